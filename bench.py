@@ -1,0 +1,499 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 relational operator pipeline (arxiv 2506.09226 hot path).
+
+One step = one pass of the plain hot path over the at-scale star workload
+(fact 600M rows x 21 B, dimension 20M rows, plus 600M (int64 key, int64
+payload) pairs), all resident in HBM:
+    qe_pipeline   join build over the dimension, then one fused pass over the
+                  fact table: date < 1278, FK join, group by (flag, attr) with
+                  SUM(price*qty), COUNT, MIN(price), MAX(price)  (3,000 groups)
+    qe_partition  stable hash partition of the pairs at fan-out 1024
+value = (fact rows + partition rows) per second of the step.  The inputs
+(12.6 GB + 9.6 GB) are larger than the 126 MB L2, so no flush is needed.
+
+Also reported on the same JSON line: the per-kernel roofline of the dominant
+kernel, the per-kernel breakdown, partition at fan-out 256 / 4096, the
+per-operator path (filter -> probe -> group-by as separate launches), the
+25K-group variant, an end-to-end number through the public API with the
+inputs copied from pinned host memory every step, the batched and served
+forms, clocks sampled during the timed region, and the CPU oracle on a
+bounded sample (cpu_baseline).
+
+--impl reference times the CPU oracle (oracle/) on a bounded sample of the
+same workload, per step, and prints the same line with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+METRIC = "scanned rows/s & % of HBM peak per pipeline; served p50/p99 vs plain launches"
+UNIT = "rows/s"
+DATE_LT = 1278
+BYTES_FACT_ROW = 21          # fk 4 + date 4 + price 8 + qty 4 + flag 1
+BYTES_PAIR_MOVE = 32         # read key+payload 16 B, write 16 B
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ---------------------------------------------------------------- peaks / clocks
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.dev = device
+        self.proc = None
+        self.path = None
+
+    def _gpu_id(self):
+        try:
+            u = str(torch.cuda.get_device_properties(self.dev).uuid)
+            return u if u.startswith("GPU-") else "GPU-" + u
+        except Exception:
+            return str(self.dev)
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self._gpu_id(), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- kernel traffic record
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2506_09226_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, units: int):
+    """DRAM bytes per launch from the committed ncu record, scaled to `units`,
+    or None when the record is missing or the kernels changed since."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    r = d.get(kernel)
+    if not r or r.get("source_hash") != kernel_source_hash():
+        return None
+    return r["dram_bytes_per_unit"] * units
+
+
+# ---------------------------------------------------------------- workload
+def make_workload(n_fact, n_dim, n_pairs, n_attr, device):
+    from paper_2506_09226_gb300 import datagen
+    t0 = time.time()
+    dim = datagen.star_dim(n_dim, n_attr, seed=1, device=device)
+    fact = datagen.star_fact(n_fact, n_dim, seed=1, device=device)
+    key, pay = datagen.key_payload_pairs(n_pairs, seed=2, device=device)
+    torch.cuda.synchronize()
+    log(f"workload generated in {time.time() - t0:.1f}s")
+    return dim, fact, key, pay
+
+
+COLS = ("fk", "date", "price", "qty", "flag")
+
+
+def star_desc(qe, fact, dim, expected_groups):
+    return qe.pipeline_desc([fact[c] for c in COLS], [(1, qe.LT, DATE_LT)], fk_col=0, dim_key=dim["key"],
+                            dim_payload=dim["attr"], key_hi_col=4, key_lo_col=qe.JOIN_PAYLOAD,
+                            aggs=[(qe.SUM, 2, 3), (qe.COUNT, -1, -1), (qe.MIN, 2, -1), (qe.MAX, 2, -1)],
+                            expected_groups=expected_groups, est_selectivity=DATE_LT / 2557)
+
+
+# ---------------------------------------------------------------- CPU oracle leg
+def oracle_sample(n_fact_sample, n_dim, n_pairs_sample, n_attr=1000):
+    """Time the oracle on a bounded sample of the same workload (CPU tensors,
+    same generator and distributions).  Returns (rows, seconds, desc)."""
+    from oracle import oracle as O
+    from paper_2506_09226_gb300 import datagen
+    dim = datagen.star_dim(n_dim, n_attr, seed=1)
+    fact = datagen.star_fact(n_fact_sample, n_dim, seed=1)
+    key, pay = datagen.key_payload_pairs(n_pairs_sample, seed=2)
+    fl = [fact[c].numpy() for c in COLS]
+    q = O.Query(preds=[O.Pred(1, O.LT, DATE_LT)], fk_col=0, key_hi_col=4, key_lo_col=O.JOIN_PAYLOAD,
+                aggs=[(O.SUM, 2, 3), (O.COUNT, -1, -1), (O.MIN, 2, -1), (O.MAX, 2, -1)])
+    dk, da, kk, pp = dim["key"].numpy(), dim["attr"].numpy(), key.numpy(), pay.numpy()
+    O.lib()
+    t0 = time.perf_counter()
+    O.pipeline(fl, q, dk, da)
+    O.partition(kk, [pp], 10)
+    dt = time.perf_counter() - t0
+    return n_fact_sample + n_pairs_sample, dt, (f"oracle (single-threaded C) on fact rows [0,{n_fact_sample}) with the "
+                                                f"full {n_dim}-row dimension, plus {n_pairs_sample} pairs at fan-out 1024")
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    n_fact_s = args.ref_sample
+    W, K = args.warmup, args.steps
+    times = []
+    desc = ""
+    for i in range(W + K):
+        rows, dt, desc = oracle_sample(n_fact_s, args.dim_rows, n_fact_s)
+        if i >= W:
+            times.append(dt)
+        log(f"reference step {i}: {dt:.2f}s")
+    t = sum(times) / len(times)
+    v = rows / t
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": K, "warmup": W,
+            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int64", "data": "synthetic", "impl": "reference",
+            "config": workload_config(args),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(args):
+    return {"workload": f"star pipeline at scale: fact {args.fact_rows} rows, dim {args.dim_rows} rows "
+                        f"(attr in [0,1000)), date<{DATE_LT}, FK join, group by (flag,attr) 3000 groups, "
+                        f"+ hash partition of {args.pairs} (int64,int64) pairs at fan-out {1 << args.log2f}",
+            "fact_rows": args.fact_rows, "dim_rows": args.dim_rows, "pairs": args.pairs,
+            "fanout": 1 << args.log2f, "l2": "inputs larger than L2 (12.6 GB + 9.6 GB vs 126 MB)",
+            "parallelism": f"replicas x{args.gpus}" if args.gpus > 1 else "1 GPU"}
+
+
+# ---------------------------------------------------------------- our arm
+def timed(fn, iters, stream):
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(iters):
+        fn()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) / iters
+
+
+def run_qe(args):
+    from paper_2506_09226_gb300 import qe
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    ctx = qe.Context(local)
+    peak, peak_kind = hbm_peak()
+
+    dim, fact, key, pay = make_workload(args.fact_rows, args.dim_rows, args.pairs, 1000, dev)
+    F = 1 << args.log2f
+    desc = star_desc(qe, fact, dim, 3000)
+    groups, gout = qe.alloc_groups(4096, 4, dev)
+    okeys, opay = torch.empty_like(key), torch.empty_like(pay)
+    offs = torch.empty(F + 1, dtype=torch.int64, device=dev)
+
+    def step():
+        qe.qe_pipeline(ctx, desc, 4096, check=False, out=(groups, gout))
+        qe.qe_partition(ctx, key, [pay], args.log2f, qe.PART_HASH, 0, okeys, [opay], offs, check=False)
+
+    for _ in range(args.warmup):
+        step()
+    ctx.sync_status()
+    # ---- timed region
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    ctx.profile_reset()
+    sampler = ClockSampler(local)
+    sampler.start()
+    l0 = ctx.launch_count()
+    ms = timed(step, args.steps, stream)
+    launches = ctx.launch_count() - l0
+    clocks = sampler.stop()
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ctx.sync_status()
+    prof = {n: ctx.profile_read(n) for n in ("build", "pipeline", "part_hist", "part_scatter")}
+    ctx.profile(False)
+    ngroups = int(groups.ngroups.item())
+    rows_step = args.fact_rows + args.pairs
+    value = rows_step * world / (ms * 1e-3)
+
+    # ---- per-kernel breakdown and the dominant kernel's roofline
+    alg_bytes = {"pipeline": BYTES_FACT_ROW * args.fact_rows,
+                 "part_scatter": BYTES_PAIR_MOVE * args.pairs,
+                 "part_hist": 8 * args.pairs,
+                 "build": 8 * args.dim_rows + 4 * args.dim_rows}
+    units = {"pipeline": args.fact_rows, "part_scatter": args.pairs, "part_hist": args.pairs,
+             "build": args.dim_rows}
+    breakdown = {}
+    for n, (cnt, tot) in prof.items():
+        if cnt:
+            avg = tot / cnt
+            gbs = alg_bytes[n] / (avg * 1e-3) / 1e9
+            breakdown[n] = {"ms": round(avg, 4), "launches_per_step": cnt / args.steps,
+                            "alg_bytes": alg_bytes[n], "gbs": round(gbs, 1), "frac": round(gbs / peak, 4)}
+    dom = max(breakdown, key=lambda n: breakdown[n]["ms"])
+    d = breakdown[dom]
+    traffic = recorded_traffic(dom, units[dom])
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": d["gbs"], "peak": peak, "unit": "GB/s",
+                "frac": d["frac"], "traffic": traffic, "peak_kind": peak_kind,
+                "alg_bytes_per_launch": d["alg_bytes"]}
+    step_bytes = alg_bytes["pipeline"] + alg_bytes["part_scatter"] + 12 * args.dim_rows
+    pipelines = {"step": {"ms": ms, "rows_per_s": value / world,
+                          "hbm_frac_of_step_alg_bytes": round(step_bytes / (ms * 1e-3) / 1e9 / peak, 4)},
+                 "fused_pipeline_call": None, "kernels": breakdown}
+
+    extras = {}
+    if "extras" in args.forms:
+        extras = run_extras(args, qe, ctx, fact, dim, key, pay, okeys, opay, dev, stream, peak)
+        pipelines["fused_pipeline_call"] = extras.pop("fused_call", None)
+
+    # ---- end to end through the public API with pinned host inputs
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, qe, ctx, fact, dim, key, pay, okeys, opay, offs, groups, gout, dev, stream)
+
+    # ---- batched and served forms
+    forms = {}
+    if "batch" in args.forms or "serve" in args.forms:
+        del okeys, opay
+        forms = run_forms(args, qe, ctx, dev, stream, fact, dim, peak)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rows, dt, desc_s = oracle_sample(args.ref_sample, args.dim_rows, args.ref_sample)
+        cpu = {"value": rows / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc_s}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "int64", "data": "synthetic", "config": workload_config(args),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": launches, "ngroups": ngroups, "pipelines": pipelines, **extras, **forms}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def run_extras(args, qe, ctx, fact, dim, key, pay, okeys, opay, dev, stream, peak):
+    out = {}
+    it = max(3, args.steps // 2)
+    # the fused pipeline call alone
+    groups, gout = qe.alloc_groups(4096, 4, dev)
+    desc = star_desc(qe, fact, dim, 3000)
+    fn = lambda: qe.qe_pipeline(ctx, desc, 4096, check=False, out=(groups, gout))  # noqa: E731
+    fn()
+    ms = timed(fn, it, stream)
+    b = BYTES_FACT_ROW * args.fact_rows + 12 * args.dim_rows
+    out["fused_call"] = {"ms": ms, "rows_per_s": args.fact_rows / (ms * 1e-3),
+                         "hbm_frac": round(b / (ms * 1e-3) / 1e9 / peak, 4)}
+    # partition at each fan-out
+    part = {}
+    for lf in (8, 10, 12):
+        offs = torch.empty((1 << lf) + 1, dtype=torch.int64, device=dev)
+        fn = lambda: qe.qe_partition(ctx, key, [pay], lf, qe.PART_HASH, 0, okeys, [opay], offs,  # noqa: E731
+                                     check=False)
+        fn()
+        ms = timed(fn, it, stream)
+        part[str(1 << lf)] = {"ms": ms, "rows_per_s": args.pairs / (ms * 1e-3),
+                              "hbm_frac": round(BYTES_PAIR_MOVE * args.pairs / (ms * 1e-3) / 1e9 / peak, 4)}
+    out["partition"] = part
+    # per-operator path: filter -> build -> probe -> group-by as separate launches
+    n = args.fact_rows
+    sel = torch.empty(n, dtype=torch.int32, device=dev)
+    cnt = torch.empty(1, dtype=torch.int64, device=dev)
+    rows = torch.empty(n, dtype=torch.int32, device=dev)
+    attr = torch.empty(n, dtype=torch.int32, device=dev)
+    jcnt = torch.empty(1, dtype=torch.int64, device=dev)
+    qe.qe_filter(ctx, [fact["date"]], [(0, qe.LT, DATE_LT)], sel, cnt)
+    nsel = int(cnt.item())
+
+    def per_op():
+        qe.qe_filter(ctx, [fact["date"]], [(0, qe.LT, DATE_LT)], sel, cnt, check=False)
+        ht = qe.qe_join_build(ctx, dim["key"], dim["attr"], check=False)
+        qe.qe_join_probe(ctx, ht, fact["fk"], sel, n=nsel, capacity=n, out_rows=rows, out_payload=attr,
+                         out_count=jcnt, check=False)
+        g = qe.qe_groupby(ctx, attr, [(qe.SUM, fact["price"], fact["qty"], True), (qe.COUNT, None, None),
+                                      (qe.MIN, fact["price"], None, True), (qe.MAX, fact["price"], None, True)],
+                          key_hi=fact["flag"], gather_hi=True, rows=rows, n=nsel, capacity=4096, check=False)
+        ht.destroy()
+        return g
+    per_op()
+    ctx.sync_status()
+    ms = timed(per_op, it, stream)
+    out["per_operator"] = {"ms": ms, "rows_per_s": n / (ms * 1e-3),
+                           "note": "filter, build, probe, group-by as separate calls; selection vector and "
+                                   "join output materialised in HBM; the filter count is read once beforehand"}
+    # 25K-group variant: attr in [0, 8334)
+    from paper_2506_09226_gb300 import datagen
+    dim25 = datagen.star_dim(args.dim_rows, 8334, seed=1, device=dev)
+    g25, gout25 = qe.alloc_groups(32768, 4, dev)
+    desc25 = star_desc(qe, fact, dim25, 25002)
+    fn = lambda: qe.qe_pipeline(ctx, desc25, 32768, check=False, out=(g25, gout25))  # noqa: E731
+    fn()
+    ms = timed(fn, it, stream)
+    out["groups_25k"] = {"ms": ms, "rows_per_s": args.fact_rows / (ms * 1e-3), "ngroups": int(g25.ngroups.item()),
+                         "hbm_frac": round((BYTES_FACT_ROW * args.fact_rows + 12 * args.dim_rows) /
+                                           (ms * 1e-3) / 1e9 / peak, 4)}
+    ctx.sync_status()
+    del sel, rows, attr, dim25
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_e2e(args, qe, ctx, fact, dim, key, pay, okeys, opay, offs, groups, gout, dev, stream):
+    """Same step through the public API with inputs copied from pinned host
+    memory and the results read back, every step."""
+    t0 = time.time()
+    hfact = {c: torch.empty(fact[c].shape, dtype=fact[c].dtype, pin_memory=True) for c in COLS}
+    hdim = {c: torch.empty(dim[c].shape, dtype=dim[c].dtype, pin_memory=True) for c in ("key", "attr")}
+    hkey = torch.empty(key.shape, dtype=key.dtype, pin_memory=True)
+    hpay = torch.empty(pay.shape, dtype=pay.dtype, pin_memory=True)
+    for c in COLS:
+        hfact[c].copy_(fact[c])
+    for c in ("key", "attr"):
+        hdim[c].copy_(dim[c])
+    hkey.copy_(key)
+    hpay.copy_(pay)
+    rk = torch.empty(4096, dtype=torch.int64, pin_memory=True)
+    ra = [torch.empty(4096, dtype=torch.int64, pin_memory=True) for _ in range(4)]
+    rn = torch.empty(1, dtype=torch.int64, pin_memory=True)
+    ro = torch.empty(offs.shape, dtype=torch.int64, pin_memory=True)
+    log(f"pinned host inputs ready in {time.time() - t0:.1f}s")
+    h2d = sum(t.numel() * t.element_size() for t in list(hfact.values()) + list(hdim.values()) + [hkey, hpay])
+    d2h = (rk.numel() + 4 * 4096 + 1 + ro.numel()) * 8
+    desc = star_desc(qe, fact, dim, 3000)
+
+    def e2e_step():
+        for c in COLS:
+            fact[c].copy_(hfact[c], non_blocking=True)
+        for c in ("key", "attr"):
+            dim[c].copy_(hdim[c], non_blocking=True)
+        key.copy_(hkey, non_blocking=True)
+        pay.copy_(hpay, non_blocking=True)
+        qe.qe_pipeline(ctx, desc, 4096, check=False, out=(groups, gout))
+        qe.qe_partition(ctx, key, [pay], args.log2f, qe.PART_HASH, 0, okeys, [opay], offs, check=False)
+        rk.copy_(groups.keys, non_blocking=True)
+        for a, b in zip(ra, groups.aggs):
+            a.copy_(b, non_blocking=True)
+        rn.copy_(groups.ngroups, non_blocking=True)
+        ro.copy_(offs, non_blocking=True)
+
+    e2e_step()
+    it = max(2, min(args.steps, 5))
+    ms = timed(e2e_step, it, stream)
+    ctx.sync_status()
+    v = (args.fact_rows + args.pairs) / (ms * 1e-3)
+    del hfact, hdim, hkey, hpay
+    return {"value": v, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms,
+            "steps": it}
+
+
+def run_forms(args, qe, ctx, dev, stream, fact, dim, peak):
+    out = {}
+    try:
+        from paper_2506_09226_gb300 import batch as B
+    except Exception as e:  # batched form not available
+        return {"batch": {"error": repr(e)}}
+    if "batch" in args.forms:
+        out["batch"] = B.bench_batch(ctx, args.batch_count, dev, stream, peak, log=log)
+    if "serve" in args.forms:
+        from paper_2506_09226_gb300 import serve as S
+        out["serve"] = S.bench_serve(ctx, dev, stream, peak, duration_s=args.serve_seconds, log=log)
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["qe", "reference"], default="qe")
+    ap.add_argument("--fact-rows", type=int, default=600_000_000)
+    ap.add_argument("--dim-rows", type=int, default=20_000_000)
+    ap.add_argument("--pairs", type=int, default=600_000_000)
+    ap.add_argument("--log2f", type=int, default=10)
+    ap.add_argument("--forms", default="extras,batch,serve")
+    ap.add_argument("--batch-count", type=int, default=10_000)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-sample", type=int, default=4_000_000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "qe":
+        log("warmup raised to 3")
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_qe(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,355 @@
+/*
+ * qe.h -- C ABI of libqe, a single-GPU relational operator library for
+ * NVIDIA GB300 (sm_103a).
+ *
+ * It implements the per-GPU operator layer of the query engine in
+ * "Terabyte-Scale Analytics in the Blink of an Eye" (arxiv 2506.09226): the
+ * paper runs relational operators over one tensor per column on each GPU
+ * (Sec. 2.1) and composes them into one program per GPU (Sec. 2.4).  The
+ * operators here are selection with stream compaction, the radix/hash
+ * partition that lays rows out per destination with start offsets (Sec. 2.2,
+ * Fig. 1; Sec. 2.3), hash-join build and probe (Sec. 2.2), hash group-by with
+ * exact SUM / COUNT / MIN / MAX (Sec. 2.3, Sec. 2.4), a fused pipeline of
+ * them, and a batched form that runs many pipelines in one persistent launch.
+ *
+ * Conventions for every call
+ *   - Memory: every column, selection vector and output buffer is a DEVICE
+ *     pointer owned by the caller; no call keeps or frees a caller pointer.
+ *     Columns may start at any address (unaligned views are read with scalar
+ *     loads).  The library owns hash tables, batch plans and per-call scratch,
+ *     which it allocates from the context's stream-ordered pool under the
+ *     context's HBM budget.
+ *   - Streams: `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *     Calls enqueue work and return; outputs, counts included, are valid once
+ *     the stream reaches that point.  Counts are written to device memory.
+ *   - Errors: argument errors are returned at once as a qe_status and leave
+ *     nothing enqueued.  Errors found by the kernels (output capacity too
+ *     small, duplicate or reserved build key, a bounded device wait that
+ *     expired) are recorded in the context; qe_sync_status() waits for the
+ *     stream and returns and clears the first one.  qe_last_error() gives a
+ *     message for the last non-OK status.
+ *   - Sizes: row counts are int64_t; selection vectors and join outputs hold
+ *     int32 row ids, so inputs that produce row ids are limited to
+ *     nrows < 2^31.  Integer aggregates wrap modulo 2^64.
+ *   - Threads: a context may be used from one host thread at a time.
+ *     Different streams may run calls of one context concurrently.
+ */
+#ifndef QE_H
+#define QE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QE_OK = 0,
+    QE_ERR_INVALID_ARG = 1,   /* bad pointer, size, type or option           */
+    QE_ERR_CAPACITY = 2,      /* output too small; required size recorded    */
+    QE_ERR_OOM = 3,           /* HBM budget of the context exceeded          */
+    QE_ERR_DUPLICATE_KEY = 4, /* join build saw a key twice                  */
+    QE_ERR_RESERVED_KEY = 5,  /* key equal to the table's empty-slot marker  */
+    QE_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up          */
+    QE_ERR_CUDA = 7,          /* a CUDA runtime call failed                  */
+    QE_ERR_NO_DEVICE = 8      /* no usable sm_103a device                     */
+} qe_status;
+
+/* Element type of a column; the value is the element size in bytes. */
+typedef enum { QE_I8 = 1, QE_I32 = 4, QE_I64 = 8 } qe_type;
+
+/* Column view: device pointer + element type.  When `gather` is nonzero the
+ * column is read through a row-id list (element i is data[rows[i]]); the
+ * calls that accept a row-id list say so. */
+typedef struct {
+    const void *data;
+    int32_t type;     /* qe_type */
+    int32_t gather;
+} qe_col;
+
+/* One comparison of a conjunctive selection predicate (Sec. 2.1).  The column
+ * value, sign-extended to int64, is compared with lo (BETWEEN: lo <= x <= hi,
+ * both inclusive). */
+typedef enum { QE_LT = 0, QE_LE, QE_GT, QE_GE, QE_EQ, QE_NE, QE_BETWEEN } qe_cmp;
+typedef struct {
+    int32_t col;      /* index into the call's column array */
+    int32_t op;       /* qe_cmp */
+    int64_t lo, hi;
+} qe_pred;
+
+#define QE_MAX_COLS 8
+#define QE_MAX_PREDS 4
+#define QE_MAX_AGGS 4
+
+/* Aggregates (Sec. 2.3 lists sum, min, max among the reduction kinds).  The
+ * value of row i is column a, or a*b (int64, wrapping) when b is given;
+ * COUNT takes no column. */
+typedef enum { QE_SUM = 0, QE_COUNT = 1, QE_MIN = 2, QE_MAX = 3 } qe_agg_op;
+
+/* Output of a group-by: one row per distinct key, in unspecified order.
+ * keys and aggs[a] (for a < the number of aggregates) are device arrays of
+ * `capacity` int64; *ngroups (device) receives the number of groups.  If the
+ * groups exceed `capacity`, QE_ERR_CAPACITY is recorded with the number of
+ * groups seen (a lower bound when the table overflowed) as the required
+ * size, and only `capacity` rows are written. */
+typedef struct {
+    int64_t capacity;
+    int64_t *keys;
+    int64_t *aggs[QE_MAX_AGGS];
+    int64_t *ngroups;
+} qe_groups_out;
+
+typedef struct qe_ctx qe_ctx;
+typedef struct qe_hash_table qe_hash_table;
+typedef struct qe_batch qe_batch;
+
+/* ------------------------------------------------------------ context */
+
+/* Create a context on CUDA device `device` (which must be sm_103a).  All
+ * library-owned device memory of the context is capped at hbm_budget_bytes
+ * (0 = no cap).  Returns QE_ERR_NO_DEVICE when the device is absent or not a
+ * GB300-class part. */
+qe_status qe_create(qe_ctx **out, int device, size_t hbm_budget_bytes);
+qe_status qe_destroy(qe_ctx *ctx);
+
+/* Message for the last non-OK status of this context (never NULL). */
+const char *qe_last_error(const qe_ctx *ctx);
+
+/* Wait for `stream`, then return and clear the first error the kernels
+ * recorded since the last call.  *required (nullable) receives the size the
+ * failing output needed (QE_ERR_CAPACITY) or 0. */
+qe_status qe_sync_status(qe_ctx *ctx, void *stream, int64_t *required);
+
+/* Device bytes currently held by library-owned objects of the context. */
+size_t qe_bytes_in_use(const qe_ctx *ctx);
+
+/* Host-side fault injection for tests: the n-th library allocation from now
+ * (1 = the next one) fails with QE_ERR_OOM; n = 0 disables. */
+void qe_debug_fail_alloc(qe_ctx *ctx, int n);
+
+/* Limit, in iterations, of every bounded device-side wait of this context's
+ * kernels (0 = the default).  Tests shorten it to make a wait expire. */
+void qe_debug_set_spin_limit(qe_ctx *ctx, int64_t iterations);
+
+/* Number of kernels this context has launched so far (host-side counter). */
+int64_t qe_launch_count(const qe_ctx *ctx);
+
+/* Per-kernel timing.  While enabled, the library brackets each launch of
+ * its main kernels with CUDA events recorded on the launch stream.
+ * qe_profile_read waits for those events and returns, for the kernel named
+ * `name` ("filter", "probe", "build", "part_hist", "part_scatter", "groupby",
+ * "pipeline", "batch"), the launches and their total device time in ms
+ * since the last reset.  Unknown names give zero launches. */
+qe_status qe_profile_enable(qe_ctx *ctx, int on);
+qe_status qe_profile_read(qe_ctx *ctx, const char *name, int64_t *launches, double *total_ms);
+qe_status qe_profile_reset(qe_ctx *ctx);
+
+/* ------------------------------------------------------------ filter */
+
+/* Selection with stable stream compaction (Sec. 2.1; the filters before a
+ * join in Sec. 2.2's example).  A row i in [0, nrows) survives when every
+ * predicate holds.  Writes the surviving row ids in ascending order to
+ * out_sel[0 .. count) and count to *out_count (device int64).
+ *   cols:   ncols column views (gather must be 0), each nrows long;
+ *   preds:  npreds (0..QE_MAX_PREDS) comparisons over those columns;
+ *   out_sel: device int32 [sel_capacity]; rows past the capacity are not
+ *            written and QE_ERR_CAPACITY is recorded (required = count).
+ * nrows must be < 2^31. */
+qe_status qe_filter(qe_ctx *ctx, const qe_col *cols, int ncols, const qe_pred *preds,
+                    int npreds, int64_t nrows, int32_t *out_sel, int64_t sel_capacity,
+                    int64_t *out_count, void *stream);
+
+/* ------------------------------------------------------------ partition */
+
+typedef enum {
+    QE_PART_HASH = 0,  /* p = top log2_fanout bits of fmix64(key)           */
+    QE_PART_RADIX = 1  /* p = (key >> shift) & (F - 1) on the key's 64 bits */
+} qe_part_mode;
+
+/* Radix / hash partition (Sec. 2.2, Fig. 1: every process applies the same
+ * partitioning function to its rows; Sec. 2.3: the data for each destination
+ * is one contiguous run per column, located by a start offset).  With
+ * F = 2^log2_fanout destinations, row i goes to destination p(key_i); rows
+ * keep their input order inside a destination (stable).  fmix64 is the
+ * MurmurHash3 64-bit finalizer.
+ *   keys:        device int64 [nrows];
+ *   payload:     npayload (0..QE_MAX_COLS-1) columns of nrows (gather = 0);
+ *   out_keys, out_payload[c]: device arrays of nrows, same types; must not
+ *                overlap the inputs;
+ *   out_offsets: device int64 [F + 1]; out_offsets[p] is the first output
+ *                row of destination p, out_offsets[F] = nrows.
+ * log2_fanout in [0, 12]; shift in [0, 63] (radix mode). */
+qe_status qe_partition(qe_ctx *ctx, const int64_t *keys, const qe_col *payload, int npayload,
+                       int64_t nrows, int log2_fanout, int mode, int shift, int64_t *out_keys,
+                       void *const *out_payload, int64_t *out_offsets, void *stream);
+
+/* ------------------------------------------------------------ join */
+
+typedef enum {
+    QE_HT_AUTO = 0,   /* dense when the key range is at most 4x the row count */
+    QE_HT_DENSE = 1,  /* direct-mapped on key - key_min (perfect hash)        */
+    QE_HT_OPEN = 2    /* open addressing, linear probing, 8-byte slots, CAS   */
+} qe_ht_layout;
+
+/* Optional build hints.  When have_range is nonzero, [key_min, key_max] is
+ * a caller-known bound on the build keys (column statistics), so the build
+ * needs no device-to-host read; a key outside it records
+ * QE_ERR_INVALID_ARG.  When have_range is zero the build reads the key range
+ * back from the device and synchronizes `stream` once. */
+typedef struct {
+    int32_t layout;       /* qe_ht_layout */
+    int32_t have_range;
+    int32_t key_min, key_max;
+} qe_build_opts;
+
+typedef struct {
+    int32_t layout;       /* QE_HT_DENSE or QE_HT_OPEN */
+    int32_t full;         /* dense table whose every slot is occupied */
+    int64_t nkeys;
+    int64_t slots;
+    int64_t bytes;
+    int32_t key_min, key_max;
+} qe_ht_info;
+
+/* Hash-join build (Sec. 2.2: the local join once both inputs are
+ * co-located; Sec. 7.2 on build sizes).  Inserts key[j] -> payload[j] for
+ * j < nrows into a library-owned table returned in *out.  Build keys must
+ * be unique (QE_ERR_DUPLICATE_KEY is recorded otherwise).  For the
+ * open-addressing layout INT32_MIN is the empty-slot marker and records
+ * QE_ERR_RESERVED_KEY.  opts may be NULL (AUTO layout, range read back). */
+qe_status qe_join_build(qe_ctx *ctx, const int32_t *keys, const int32_t *payload, int64_t nrows,
+                        const qe_build_opts *opts, qe_hash_table **out, void *stream);
+
+/* Hash-join probe (inner join).  For each probe position i < n in order,
+ * row r = sel ? sel[i] : i is looked up with key probe_keys[r]; on a match
+ * (r, payload) is appended; misses are dropped.  Output is in ascending
+ * position order (stable compaction).
+ *   out_probe_row, out_build_payload: device int32 [capacity];
+ *   *out_count (device int64): number of matches; past the capacity nothing
+ *   is written and QE_ERR_CAPACITY is recorded. */
+qe_status qe_join_probe(qe_ctx *ctx, const qe_hash_table *ht, const int32_t *probe_keys,
+                        const int32_t *sel, int64_t n, int32_t *out_probe_row,
+                        int32_t *out_build_payload, int64_t capacity, int64_t *out_count,
+                        void *stream);
+
+qe_status qe_join_info(const qe_hash_table *ht, qe_ht_info *info);
+
+/* Release the table once the work on `stream` that uses it is ordered
+ * before this call. */
+qe_status qe_join_destroy(qe_ctx *ctx, qe_hash_table *ht, void *stream);
+
+/* ------------------------------------------------------------ group-by */
+
+typedef struct {
+    int32_t op;       /* qe_agg_op */
+    int32_t pad;
+    qe_col a, b;      /* b.data == NULL: value = a; else value = a * b */
+} qe_agg;
+
+typedef enum {
+    QE_GB_AUTO = 0,   /* shared-memory tables when the capacity fits, else HBM */
+    QE_GB_SMEM = 1,   /* per-block shared-memory table, spilling to HBM       */
+    QE_GB_HBM = 2     /* HBM table only                                       */
+} qe_gb_placement;
+
+/* Hash group-by with exact aggregates (Sec. 2.3: sum, min and max as the
+ * reduction kinds; Sec. 2.4: group-by in the per-GPU program).  For i < n,
+ * the group key of row i is
+ *     (int64)key_hi[i] << 32 | (uint32)key_lo[i]   when key_hi.data != NULL,
+ *     (int64)key_lo[i]                             otherwise,
+ * and each aggregate folds its value into the group.  Columns with gather
+ * set are read at rows[i] (rows: device int32 [n], required then).
+ *   placement: qe_gb_placement (AUTO picks by group_capacity);
+ *   out: see qe_groups_out; out->capacity bounds the groups.
+ * INT64_MIN is the table's empty-key marker and records
+ * QE_ERR_RESERVED_KEY. */
+qe_status qe_groupby(qe_ctx *ctx, int64_t n, const int32_t *rows, qe_col key_hi, qe_col key_lo,
+                     const qe_agg *aggs, int naggs, int placement, const qe_groups_out *out,
+                     void *stream);
+
+/* ------------------------------------------------------------ pipeline */
+
+#define QE_JOIN_PAYLOAD (-2)
+
+typedef struct {
+    int32_t op;       /* qe_agg_op */
+    int32_t a, b;     /* fact column indices; -1 = absent */
+    int32_t pad;
+} qe_agg_spec;
+
+/* One query of the paper's per-GPU shape (Sec. 2.4): a selection on the fact
+ * table, an inner join of one fact column with a dimension table, and a
+ * group-by with aggregates -- group-by(join(filter(fact), dim)).
+ *   fact[0..n_fact_cols): fact columns, n_fact rows each (gather = 0);
+ *   preds: conjunction over fact columns;
+ *   fk_col: int32 fact column joined with the dimension keys, or -1 (no
+ *           join);
+ *   dim_key/dim_payload/n_dim: dimension columns (device int32), built into a
+ *           table by the call when ht is NULL; or a prebuilt resident table;
+ *   group key: key_hi_col (fact column or -1) and key_lo_col (fact column or
+ *           QE_JOIN_PAYLOAD), packed as in qe_groupby;
+ *   aggs: over fact columns.
+ *   expected_groups: sizing hint for the group table (0 = use the output
+ *           capacity); est_selectivity: hint in (0, 1] (0 = unknown). */
+typedef struct {
+    int64_t n_fact;
+    qe_col fact[QE_MAX_COLS];
+    int32_t n_fact_cols;
+    int32_t n_preds;
+    qe_pred preds[QE_MAX_PREDS];
+    int32_t fk_col;
+    int32_t key_hi_col;
+    int32_t key_lo_col;
+    int32_t n_aggs;
+    qe_agg_spec aggs[QE_MAX_AGGS];
+    const int32_t *dim_key;
+    const int32_t *dim_payload;
+    int64_t n_dim;
+    const qe_hash_table *ht;
+    qe_build_opts build;
+    int64_t expected_groups;
+    double est_selectivity;
+} qe_pipeline_desc;
+
+/* Run one pipeline: (build), then one fused pass over the fact table that
+ * filters, probes and aggregates each row, then the group output.  Result
+ * as in qe_groupby. */
+qe_status qe_pipeline(qe_ctx *ctx, const qe_pipeline_desc *desc, const qe_groups_out *out,
+                      void *stream);
+
+/* ------------------------------------------------------------ batch */
+
+/* Launch shape of a batch; zeros pick the tuned defaults. */
+typedef struct {
+    int32_t block_threads;   /* threads per block (multiple of 32) */
+    int32_t tile_rows;       /* fact rows per work item            */
+    int32_t smem_slots;      /* shared-memory group-table slots    */
+    int32_t use_graph;       /* capture the launch in a CUDA graph */
+} qe_batch_opts;
+
+/* Plan a batch of n pipelines that share one persistent launch: every
+ * pipeline's build, fused fact pass and group output run as work items of
+ * one kernel, ordered per pipeline by device counters (bounded waits).  The
+ * descs (dimension tables given by columns, not prebuilt tables, each with
+ * build.have_range set) and outs are copied; the pointed-to device buffers
+ * must stay valid until qe_batch_destroy.  Allocates all per-pipeline hash
+ * and group tables. */
+qe_status qe_batch_create(qe_ctx *ctx, const qe_pipeline_desc *descs, const qe_groups_out *outs,
+                          int n, const qe_batch_opts *opts, qe_batch **out, void *stream);
+
+/* Run the planned batch on `stream` (through its CUDA graph when planned
+ * with use_graph).  May be called repeatedly. */
+qe_status qe_batch_launch(qe_ctx *ctx, qe_batch *batch, void *stream);
+
+qe_status qe_batch_destroy(qe_ctx *ctx, qe_batch *batch, void *stream);
+
+/* Plan, launch once and destroy. */
+qe_status qe_batch_run(qe_ctx *ctx, const qe_pipeline_desc *descs, const qe_groups_out *outs,
+                       int n, const qe_batch_opts *opts, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QE_H */

@@ -1,0 +1,470 @@
+// qe_internal.cuh -- shared host and device pieces of libqe (sm_103a).
+//
+// Host: the context (allocation under an HBM budget, the device-side error
+// word, launch geometry).  Device: status reporting, the partition hash, the
+// join-table hash, warp scans, the decoupled look-back used by the stable
+// compaction kernels, and the hash group-table primitives.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "qe.h"
+
+// ------------------------------------------------------------------ host
+
+struct qe_dev_status {
+    int32_t code;        // first qe_status recorded by a kernel (0 = none)
+    int32_t pad;
+    int64_t required;    // size the failing output needed (max over reports)
+};
+
+struct qe_ctx {
+    int device = 0;
+    int num_sms = 0;
+    size_t budget = 0;              // 0 = unlimited
+    size_t in_use = 0;
+    int fail_after = 0;             // fault injection: n-th allocation fails
+    int64_t spin_limit = 1 << 22;   // bounded device waits (iterations)
+    size_t smem_optin = 0;          // max dynamic shared memory per block
+    qe_dev_status *dstat = nullptr; // device
+    qe_dev_status *hstat = nullptr; // pinned host mirror
+    std::string last_error;
+    std::mutex mu;
+    std::unordered_map<void *, size_t> live;
+    std::atomic<int64_t> launches{0};
+    bool profiling = false;
+    std::mutex prof_mu;
+    std::map<std::string, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>> prof;
+};
+
+// Count one kernel launch of the context.
+#define QE_LAUNCHED(ctx) ((ctx)->launches.fetch_add(1, std::memory_order_relaxed))
+
+// Brackets the launches inside its scope with profiling events when the
+// context has profiling enabled.
+struct ProfScope {
+    qe_ctx *ctx;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr, b = nullptr;
+    const char *name;
+    ProfScope(qe_ctx *c, const char *n, cudaStream_t st) : ctx(c), s(st), name(n)
+    {
+        if (!ctx->profiling) return;
+        if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+            cudaGetLastError();
+            a = b = nullptr;
+            return;
+        }
+        cudaEventRecord(a, s);
+    }
+    ~ProfScope()
+    {
+        if (!a) return;
+        cudaEventRecord(b, s);
+        std::lock_guard<std::mutex> g(ctx->prof_mu);
+        ctx->prof[name].push_back({a, b});
+    }
+};
+
+qe_status qe_fail(qe_ctx *ctx, qe_status st, const std::string &msg);
+qe_status qe_cuda_fail(qe_ctx *ctx, cudaError_t e, const char *where);
+qe_status qe_alloc(qe_ctx *ctx, void **p, size_t bytes, cudaStream_t s);
+void qe_free(qe_ctx *ctx, void *p, cudaStream_t s);
+
+#define QE_CUDA(ctx, call)                                        \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return qe_cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+#define QE_CHECK_LAUNCH(ctx) QE_CUDA(ctx, cudaGetLastError())
+
+static inline int64_t qe_ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+static inline int qe_log2_ceil(uint64_t x)
+{
+    int l = 0;
+    while ((uint64_t(1) << l) < x) l++;
+    return l;
+}
+static inline bool qe_aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+static inline bool qe_valid_type(int t) { return t == QE_I8 || t == QE_I32 || t == QE_I64; }
+
+// ------------------------------------------------------------------ device
+
+#define QE_FULL_MASK 0xffffffffu
+
+__device__ __forceinline__ void dev_report(qe_dev_status *st, int code, int64_t required)
+{
+    atomicCAS(&st->code, 0, code);
+    if (required > 0)
+        atomicMax(reinterpret_cast<unsigned long long *>(&st->required),
+                  static_cast<unsigned long long>(required));
+}
+
+// MurmurHash3 64-bit finalizer (A. Appleby, public domain), the partition
+// function: destination = top log2(F) bits.
+__device__ __forceinline__ uint64_t dev_fmix64(uint64_t k)
+{
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdULL;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ULL;
+    k ^= k >> 33;
+    return k;
+}
+
+// MurmurHash3 32-bit finalizer: slot hash of the open-addressing join table.
+__device__ __forceinline__ uint32_t dev_fmix32(uint32_t h)
+{
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+// Partition id: hash mode (top bits of fmix64) or radix mode (key bits).
+__device__ __forceinline__ uint32_t dev_part_id(int64_t key, int log2f, int mode, int shift)
+{
+    if (log2f == 0) return 0;
+    uint64_t k = static_cast<uint64_t>(key);
+    if (mode == QE_PART_HASH) return static_cast<uint32_t>(dev_fmix64(k) >> (64 - log2f));
+    return static_cast<uint32_t>((k >> shift) & ((uint64_t(1) << log2f) - 1));
+}
+
+// Read element i of a column as int64 (sign-extended).
+__device__ __forceinline__ int64_t dev_col(const void *p, int type, int64_t i)
+{
+    if (type == QE_I32) return static_cast<int64_t>(__ldg(static_cast<const int32_t *>(p) + i));
+    if (type == QE_I64) return __ldg(static_cast<const long long *>(p) + i);
+    return static_cast<int64_t>(__ldg(static_cast<const signed char *>(p) + i));
+}
+
+// Streaming read (evict-first): fact columns are read once per pass.
+__device__ __forceinline__ int64_t dev_col_stream(const void *p, int type, int64_t i)
+{
+    if (type == QE_I32) return static_cast<int64_t>(__ldcs(static_cast<const int32_t *>(p) + i));
+    if (type == QE_I64) return __ldcs(static_cast<const long long *>(p) + i);
+    return static_cast<int64_t>(__ldcs(reinterpret_cast<const signed char *>(p) + i));
+}
+
+__device__ __forceinline__ bool dev_cmp(int64_t x, int op, int64_t lo, int64_t hi)
+{
+    switch (op) {
+    case QE_LT: return x < lo;
+    case QE_LE: return x <= lo;
+    case QE_GT: return x > lo;
+    case QE_GE: return x >= lo;
+    case QE_EQ: return x == lo;
+    case QE_NE: return x != lo;
+    default: return lo <= x && x <= hi;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        T o = __shfl_up_sync(QE_FULL_MASK, v, d);
+        if (lane >= d) v += o;
+    }
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(QE_FULL_MASK, v, d);
+    return v;
+}
+
+// ---------------------------------------------- decoupled look-back scan
+// Single-pass prefix over tiles (Merrill & Garland, "Single-pass Parallel
+// Prefix Scan with Decoupled Look-back", 2016).  A status word holds a
+// 2-bit flag (0 = not ready, 1 = tile aggregate, 2 = inclusive prefix) and a
+// 62-bit count.  Tiles are claimed in order from an atomic counter, so every
+// tile a claimant waits on is already running; each wait is still bounded
+// and reports QE_ERR_TIMEOUT instead of spinning forever.
+
+#define LB_AGG (1ull << 62)
+#define LB_PRE (2ull << 62)
+#define LB_VAL ((1ull << 62) - 1)
+
+__device__ __forceinline__ void lb_store(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long lb_load(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Called by one full warp.  Publishes `agg` for `tile`, returns the exclusive
+// prefix of the tile (identical in all lanes) and publishes the inclusive one.
+__device__ __forceinline__ int64_t lb_exclusive(unsigned long long *state, int64_t tile, int64_t agg,
+                                                qe_dev_status *st, int64_t spin_limit)
+{
+    const int lane = threadIdx.x & 31;
+    if (tile == 0) {
+        if (lane == 0) lb_store(state, LB_PRE | static_cast<unsigned long long>(agg));
+        return 0;
+    }
+    if (lane == 0) lb_store(state + tile, LB_AGG | static_cast<unsigned long long>(agg));
+    int64_t excl = 0, pred = tile - 1, spins = 0;
+    while (true) {
+        int64_t t = pred - lane;
+        unsigned long long w = t >= 0 ? lb_load(state + t) : LB_PRE;
+        unsigned flag = static_cast<unsigned>(w >> 62);
+        if (__any_sync(QE_FULL_MASK, flag == 0)) {
+            if (++spins > spin_limit) {
+                if (lane == 0) dev_report(st, QE_ERR_TIMEOUT, 0);
+                break;
+            }
+            __nanosleep(32);
+            continue;
+        }
+        unsigned pm = __ballot_sync(QE_FULL_MASK, flag == 2);
+        int stop = pm ? __ffs(pm) - 1 : 31;
+        int64_t v = lane <= stop ? static_cast<int64_t>(w & LB_VAL) : 0;
+        excl += warp_sum(v);
+        if (pm) break;
+        pred -= 32;
+    }
+    if (lane == 0) lb_store(state + tile, LB_PRE | static_cast<unsigned long long>(excl + agg));
+    return excl;
+}
+
+// ---------------------------------------------- join table view
+struct HtView {
+    int32_t layout;          // QE_HT_DENSE / QE_HT_OPEN
+    int32_t full;            // dense: every slot occupied (no bitmap check)
+    int32_t key_min;
+    uint32_t range;          // dense: key_max - key_min + 1
+    uint32_t mask;           // open: slots - 1
+    const int32_t *payload;  // dense payload [range]
+    const uint32_t *bitmap;  // dense occupancy [ceil(range/32)]
+    const unsigned long long *slots;  // open: key << 32 | payload
+};
+
+#define HT_EMPTY_KEY (static_cast<int32_t>(0x80000000u))
+#define HT_EMPTY_SLOT 0x8000000080000000ull
+
+__device__ __forceinline__ bool ht_lookup(const HtView &h, int32_t key, int32_t &pay)
+{
+    if (h.layout == QE_HT_DENSE) {
+        uint32_t s = static_cast<uint32_t>(key) - static_cast<uint32_t>(h.key_min);
+        if (s >= h.range) return false;
+        int32_t p = __ldg(h.payload + s);
+        if (!h.full && !((__ldg(h.bitmap + (s >> 5)) >> (s & 31)) & 1u)) return false;
+        pay = p;
+        return true;
+    }
+    uint32_t i = dev_fmix32(static_cast<uint32_t>(key)) & h.mask;
+    for (uint32_t probes = 0; probes <= h.mask; probes++) {
+        unsigned long long w = __ldg(h.slots + i);
+        int32_t k = static_cast<int32_t>(w >> 32);
+        if (k == key) {
+            pay = static_cast<int32_t>(w & 0xffffffffu);
+            return true;
+        }
+        if (k == HT_EMPTY_KEY) return false;
+        i = (i + 1) & h.mask;
+    }
+    return false;
+}
+
+// ---------------------------------------------- group tables
+// Keys are stored as key ^ INT64_MIN so that an all-zero slot is empty
+// (INT64_MIN itself is reserved).  Aggregates are stored so that zero is
+// each one's identity and every update is an unsigned atomic:
+//   SUM   : two's-complement sum (atomicAdd)
+//   COUNT : atomicAdd 1
+//   MIN   : ~(v ^ SIGN), combined with atomicMax
+//   MAX   :  (v ^ SIGN), combined with atomicMax
+#define GB_SIGN 0x8000000000000000ull
+
+struct AggOps {
+    int n;
+    int op[QE_MAX_AGGS];
+};
+
+__device__ __forceinline__ unsigned long long agg_encode(int op, int64_t v)
+{
+    unsigned long long u = static_cast<unsigned long long>(v);
+    if (op == QE_SUM) return u;
+    if (op == QE_COUNT) return 1ull;
+    if (op == QE_MIN) return ~(u ^ GB_SIGN);
+    return u ^ GB_SIGN;
+}
+
+__device__ __forceinline__ int64_t agg_decode(int op, unsigned long long s)
+{
+    if (op == QE_MIN) return static_cast<int64_t>(~s ^ GB_SIGN);
+    if (op == QE_MAX) return static_cast<int64_t>(s ^ GB_SIGN);
+    return static_cast<int64_t>(s);
+}
+
+// Fold an encoded contribution into an aggregate cell (shared or global).
+__device__ __forceinline__ void agg_fold(unsigned long long *cell, int op, unsigned long long e)
+{
+    if (op == QE_SUM || op == QE_COUNT) {
+        if (e) atomicAdd(cell, e);
+    } else {
+        if (*reinterpret_cast<volatile unsigned long long *>(cell) < e) atomicMax(cell, e);
+    }
+}
+
+__device__ __forceinline__ uint32_t gb_hash(unsigned long long kx) { return static_cast<uint32_t>(dev_fmix64(kx)); }
+
+// Global (HBM) group table: `slots` entries of (1 + naggs) words.
+struct GTable {
+    unsigned long long *words;
+    uint64_t mask;                    // slots - 1
+    int stride;                       // 1 + naggs
+    unsigned long long *nkeys;        // distinct keys inserted
+    int64_t capacity;                 // caller's group capacity
+    qe_dev_status *st;
+};
+
+// Returns the slot index of key kx (inserting it), or -1 when the caller's
+// capacity is exhausted (QE_ERR_CAPACITY recorded) or the table is full.
+__device__ __forceinline__ int64_t gt_find_insert(const GTable &g, unsigned long long kx)
+{
+    uint64_t i = gb_hash(kx) & g.mask;
+    for (uint64_t probes = 0; probes <= g.mask; probes++) {
+        unsigned long long *cell = g.words + i * g.stride;
+        unsigned long long cur = *reinterpret_cast<volatile unsigned long long *>(cell);
+        if (cur == kx) return static_cast<int64_t>(i);
+        if (cur == 0) {
+            if (static_cast<int64_t>(*reinterpret_cast<volatile unsigned long long *>(g.nkeys)) >= g.capacity) {
+                dev_report(g.st, QE_ERR_CAPACITY, g.capacity + 1);
+                return -1;
+            }
+            unsigned long long old = atomicCAS(cell, 0ull, kx);
+            if (old == 0) {
+                unsigned long long c = atomicAdd(g.nkeys, 1ull) + 1;
+                if (static_cast<int64_t>(c) > g.capacity) dev_report(g.st, QE_ERR_CAPACITY, static_cast<int64_t>(c));
+                return static_cast<int64_t>(i);
+            }
+            if (old == kx) return static_cast<int64_t>(i);
+        }
+        i = (i + 1) & g.mask;
+    }
+    dev_report(g.st, QE_ERR_CAPACITY, g.capacity + 1);
+    return -1;
+}
+
+// Shared-memory group table: keys[S] then aggs[a][S] (S a power of two).
+// Returns the slot of kx or -1 when max_probe slots were tried (spill).
+__device__ __forceinline__ int st_find_insert(unsigned long long *keys, uint32_t mask, unsigned long long kx,
+                                              int max_probe)
+{
+    uint32_t i = gb_hash(kx) & mask;
+    for (int p = 0; p < max_probe; p++) {
+        unsigned long long cur = reinterpret_cast<volatile unsigned long long *>(keys)[i];
+        if (cur == kx) return static_cast<int>(i);
+        if (cur == 0) {
+            unsigned long long old = atomicCAS(keys + i, 0ull, kx);
+            if (old == 0 || old == kx) return static_cast<int>(i);
+        }
+        i = (i + 1) & mask;
+    }
+    return -1;
+}
+
+// Fold one row (encoded contributions e[a]) into the global table.
+__device__ __forceinline__ void gt_fold_row(const GTable &g, const AggOps &ops, unsigned long long kx,
+                                            const unsigned long long *e)
+{
+    int64_t s = gt_find_insert(g, kx);
+    if (s < 0) return;
+    unsigned long long *cell = g.words + s * g.stride + 1;
+    _Pragma("unroll") for (int a = 0; a < QE_MAX_AGGS; a++) if (a < ops.n) agg_fold(cell + a, ops.op[a], e[a]);
+}
+
+// Zero a shared-memory table of S slots (keys then naggs aggregate rows).
+__device__ __forceinline__ void st_zero(unsigned long long *sm, int S, int naggs)
+{
+    for (int i = threadIdx.x; i < S * (1 + naggs); i += blockDim.x) sm[i] = 0;
+}
+
+// Fold one row into the shared-memory table, spilling to the global table
+// when the key is not placed within max_probe slots.
+__device__ __forceinline__ void st_fold_row(unsigned long long *sm, int S, const AggOps &ops, const GTable &g,
+                                            unsigned long long kx, const unsigned long long *e, int max_probe)
+{
+    if (S) {
+        int slot = st_find_insert(sm, static_cast<uint32_t>(S - 1), kx, max_probe);
+        if (slot >= 0) {
+            _Pragma("unroll") for (int a = 0; a < QE_MAX_AGGS; a++) if (a < ops.n) agg_fold(sm + (a + 1) * S + slot, ops.op[a], e[a]);
+            return;
+        }
+    }
+    gt_fold_row(g, ops, kx, e);
+}
+
+// Merge a block's shared-memory table into the global table (after the
+// block's last update and a __syncthreads()).
+__device__ __forceinline__ void st_flush(unsigned long long *sm, int S, const AggOps &ops, const GTable &g)
+{
+    for (int slot = threadIdx.x; slot < S; slot += blockDim.x) {
+        unsigned long long kx = sm[slot];
+        if (!kx) continue;
+        unsigned long long e[QE_MAX_AGGS];
+        _Pragma("unroll") for (int a = 0; a < QE_MAX_AGGS; a++) if (a < ops.n) e[a] = sm[(a + 1) * S + slot];
+        gt_fold_row(g, ops, kx, e);
+    }
+}
+
+// Host helpers shared by group-by and pipeline.
+struct GroupTableHost {
+    unsigned long long *words = nullptr;  // device
+    uint64_t slots = 0;
+    int stride = 0;
+    size_t bytes = 0;
+};
+
+qe_status gt_create(qe_ctx *ctx, int64_t capacity, int naggs, GroupTableHost &t, cudaStream_t s);
+// Compact the table into `out` (keys + decoded aggregates + ngroups).
+qe_status gt_finalize(qe_ctx *ctx, const GroupTableHost &t, const AggOps &ops, const qe_groups_out *out,
+                      cudaStream_t s);
+qe_status gt_check_out(qe_ctx *ctx, const qe_groups_out *out, int naggs);
+
+// Smem group-table sizing: slots for `groups` at <= 75% load, 0 when the
+// table would not fit `smem_budget` bytes.
+static inline int st_slots_for(int64_t groups, int naggs, size_t smem_budget)
+{
+    uint64_t want = static_cast<uint64_t>(groups) * 4 / 3 + 1;
+    uint64_t s = 64;
+    while (s < want) s <<= 1;
+    if (s * 8 * (1 + naggs) > smem_budget) return 0;
+    return static_cast<int>(s);
+}
+
+// Largest power-of-two slot count whose table fits `smem_budget` bytes.
+static inline int st_slots_max(int naggs, size_t smem_budget)
+{
+    uint64_t s = 64;
+    if (s * 8 * (1 + naggs) > smem_budget) return 0;
+    while ((s * 2) * 8 * (1 + naggs) <= smem_budget) s <<= 1;
+    return static_cast<int>(s);
+}
+
+HtView ht_view(const qe_hash_table *ht);
+qe_status join_build_impl(qe_ctx *ctx, const int32_t *keys, const int32_t *payload, int64_t nrows,
+                          const qe_build_opts *opts, qe_hash_table **out, cudaStream_t s);

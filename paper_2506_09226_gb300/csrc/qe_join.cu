@@ -1,0 +1,329 @@
+// qe_join.cu -- hash-join build and probe (Sec. 2.2: the local join once
+// both inputs are co-located; Sec. 7.2 on large build sides).
+//
+// Two table layouts, both library-owned:
+//   DENSE  direct-mapped on key - key_min (a perfect hash for dense key
+//          domains): payload[range] plus an occupancy bitmap used to detect
+//          duplicates; when every slot is occupied the probe skips the bitmap.
+//          A 20M-key dimension takes 80 MB of payload, which stays resident in
+//          the 126 MB L2 while the fact columns stream through it.
+//   OPEN   open addressing with linear probing over 8-byte slots
+//          (key << 32 | payload), inserted with 64-bit CAS; INT32_MIN marks an
+//          empty slot.  Load factor <= 0.5.
+#include <climits>
+
+#include "qe_compact.cuh"
+
+struct qe_hash_table {
+    int32_t layout = QE_HT_DENSE;
+    int32_t full = 0;
+    int32_t key_min = 0, key_max = -1;
+    int64_t nkeys = 0;
+    int64_t slots = 0;
+    void *mem = nullptr;
+    size_t bytes = 0;
+    int32_t *payload = nullptr;
+    uint32_t *bitmap = nullptr;
+    unsigned long long *open = nullptr;
+};
+
+HtView ht_view(const qe_hash_table *ht)
+{
+    HtView v{};
+    v.layout = ht->layout;
+    v.full = ht->full;
+    v.key_min = ht->key_min;
+    v.range = ht->layout == QE_HT_DENSE ? static_cast<uint32_t>(ht->slots) : 0;
+    v.mask = ht->layout == QE_HT_OPEN ? static_cast<uint32_t>(ht->slots - 1) : 0;
+    v.payload = ht->payload;
+    v.bitmap = ht->bitmap;
+    v.slots = ht->open;
+    return v;
+}
+
+namespace {
+
+__global__ void __launch_bounds__(256) k_minmax(const int32_t *keys, int64_t n, int32_t *mm)
+{
+    int32_t lo = INT_MAX, hi = INT_MIN;
+    for (int64_t i = blockIdx.x * 256ll + threadIdx.x; i < n; i += static_cast<int64_t>(gridDim.x) * 256) {
+        int32_t k = __ldcs(keys + i);
+        lo = min(lo, k);
+        hi = max(hi, k);
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        lo = min(lo, __shfl_xor_sync(QE_FULL_MASK, lo, d));
+        hi = max(hi, __shfl_xor_sync(QE_FULL_MASK, hi, d));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(mm, lo);
+        atomicMax(mm + 1, hi);
+    }
+}
+
+__global__ void k_minmax_init(int32_t *mm)
+{
+    mm[0] = INT_MAX;
+    mm[1] = INT_MIN;
+}
+
+__global__ void __launch_bounds__(256) k_build_dense(const int32_t *keys, const int32_t *pay, int64_t n,
+                                                     int32_t key_min, uint32_t range, int32_t *payload,
+                                                     uint32_t *bitmap, qe_dev_status *st)
+{
+    for (int64_t i = blockIdx.x * 256ll + threadIdx.x; i < n; i += static_cast<int64_t>(gridDim.x) * 256) {
+        const int32_t k = __ldcs(keys + i);
+        const uint32_t s = static_cast<uint32_t>(k) - static_cast<uint32_t>(key_min);
+        if (s >= range) {
+            dev_report(st, QE_ERR_INVALID_ARG, 0);
+            continue;
+        }
+        const uint32_t bit = 1u << (s & 31);
+        const uint32_t old = atomicOr(bitmap + (s >> 5), bit);
+        if (old & bit) {
+            dev_report(st, QE_ERR_DUPLICATE_KEY, 0);
+            continue;
+        }
+        payload[s] = __ldcs(pay + i);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_fill_u64(unsigned long long *p, int64_t n, unsigned long long v)
+{
+    for (int64_t i = blockIdx.x * 256ll + threadIdx.x; i < n; i += static_cast<int64_t>(gridDim.x) * 256) p[i] = v;
+}
+
+__global__ void __launch_bounds__(256) k_build_open(const int32_t *keys, const int32_t *pay, int64_t n,
+                                                    unsigned long long *slots, uint32_t mask, qe_dev_status *st)
+{
+    for (int64_t i = blockIdx.x * 256ll + threadIdx.x; i < n; i += static_cast<int64_t>(gridDim.x) * 256) {
+        const int32_t k = __ldcs(keys + i);
+        if (k == HT_EMPTY_KEY) {
+            dev_report(st, QE_ERR_RESERVED_KEY, 0);
+            continue;
+        }
+        const unsigned long long w = (static_cast<unsigned long long>(static_cast<uint32_t>(k)) << 32) |
+                                     static_cast<uint32_t>(__ldcs(pay + i));
+        uint32_t h = dev_fmix32(static_cast<uint32_t>(k)) & mask;
+        bool done = false;
+        for (uint32_t probes = 0; probes <= mask && !done; probes++) {
+            unsigned long long old = atomicCAS(slots + h, HT_EMPTY_SLOT, w);
+            if (old == HT_EMPTY_SLOT) {
+                done = true;
+            } else if (static_cast<int32_t>(old >> 32) == k) {
+                dev_report(st, QE_ERR_DUPLICATE_KEY, 0);
+                done = true;
+            } else {
+                h = (h + 1) & mask;
+            }
+        }
+        if (!done) dev_report(st, QE_ERR_CAPACITY, n);
+    }
+}
+
+unsigned grid_for(qe_ctx *ctx, int64_t n)
+{
+    int64_t g = qe_ceil_div(n, 256);
+    int64_t cap = static_cast<int64_t>(ctx->num_sms) * 8;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return static_cast<unsigned>(g);
+}
+
+// Probe as a stable compaction: position i probes row sel[i] (or i).
+constexpr int PROBE_ITEMS = 8;
+
+struct ProbeOp {
+    HtView ht;
+    const int32_t *keys;
+    const int32_t *sel;
+    int32_t *out_row;
+    int32_t *out_pay;
+
+    struct Slot {
+        int32_t row[PROBE_ITEMS];
+        int32_t pay[PROBE_ITEMS];
+    };
+
+    template <int ITEMS>
+    __device__ __forceinline__ void eval(int64_t pos0, bool (&ok)[ITEMS], Slot &s) const
+    {
+#pragma unroll
+        for (int k = 0; k < ITEMS; k++) {
+            int64_t i = pos0 + 32 * k;
+            s.row[k] = ok[k] ? (sel ? __ldcs(sel + i) : static_cast<int32_t>(i)) : 0;
+        }
+        int32_t key[ITEMS];
+#pragma unroll
+        for (int k = 0; k < ITEMS; k++) key[k] = ok[k] ? __ldg(keys + s.row[k]) : 0;
+#pragma unroll
+        for (int k = 0; k < ITEMS; k++) {
+            int32_t p = 0;
+            if (ok[k]) ok[k] = ht_lookup(ht, key[k], p);
+            s.pay[k] = p;
+        }
+    }
+
+    __device__ __forceinline__ void emit(int64_t o, int64_t, int k, const Slot &s) const
+    {
+        __stcs(out_row + o, s.row[k]);
+        __stcs(out_pay + o, s.pay[k]);
+    }
+};
+
+}  // namespace
+
+qe_status join_build_impl(qe_ctx *ctx, const int32_t *keys, const int32_t *payload, int64_t nrows,
+                          const qe_build_opts *opts, qe_hash_table **out, cudaStream_t s)
+{
+    qe_build_opts o{};
+    if (opts) o = *opts;
+    if (o.layout < QE_HT_AUTO || o.layout > QE_HT_OPEN) return qe_fail(ctx, QE_ERR_INVALID_ARG, "build: bad layout");
+    int32_t kmin = 0, kmax = -1;
+    if (nrows > 0) {
+        if (o.have_range) {
+            kmin = o.key_min;
+            kmax = o.key_max;
+            if (kmin > kmax) return qe_fail(ctx, QE_ERR_INVALID_ARG, "build: empty key range");
+        } else {
+            void *mm = nullptr;
+            qe_status st = qe_alloc(ctx, &mm, 8, s);
+            if (st != QE_OK) return st;
+            int32_t host[2];
+            k_minmax_init<<<1, 1, 0, s>>>(static_cast<int32_t *>(mm));
+            QE_LAUNCHED(ctx);
+            k_minmax<<<grid_for(ctx, nrows), 256, 0, s>>>(keys, nrows, static_cast<int32_t *>(mm));
+            QE_LAUNCHED(ctx);
+            cudaError_t e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaMemcpyAsync(host, mm, 8, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            qe_free(ctx, mm, s);
+            if (e != cudaSuccess) return qe_cuda_fail(ctx, e, "build: key range");
+            kmin = host[0];
+            kmax = host[1];
+        }
+    }
+    const uint64_t range = nrows > 0 ? static_cast<uint64_t>(static_cast<int64_t>(kmax) - kmin + 1) : 1;
+    int layout = o.layout;
+    if (layout == QE_HT_AUTO)
+        layout = (range <= static_cast<uint64_t>(4 * (nrows > 0 ? nrows : 1)) && range < (1ull << 31)) ? QE_HT_DENSE
+                                                                                                      : QE_HT_OPEN;
+    if (layout == QE_HT_DENSE && range >= (1ull << 31))
+        return qe_fail(ctx, QE_ERR_INVALID_ARG, "build: key range too wide for a dense table");
+    qe_hash_table *ht = new qe_hash_table();
+    ht->layout = layout;
+    ht->key_min = kmin;
+    ht->key_max = kmax;
+    ht->nkeys = nrows;
+    qe_status st;
+    if (layout == QE_HT_DENSE) {
+        ht->slots = static_cast<int64_t>(range);
+        const size_t pay_bytes = ((range * 4 + 255) / 256) * 256;
+        const size_t bm_bytes = ((range + 31) / 32) * 4;
+        ht->bytes = pay_bytes + bm_bytes;
+        st = qe_alloc(ctx, &ht->mem, ht->bytes, s);
+        if (st != QE_OK) {
+            delete ht;
+            return st;
+        }
+        ht->payload = static_cast<int32_t *>(ht->mem);
+        ht->bitmap = reinterpret_cast<uint32_t *>(static_cast<char *>(ht->mem) + pay_bytes);
+        ht->full = static_cast<uint64_t>(nrows) == range ? 1 : 0;
+        cudaError_t e = cudaMemsetAsync(ht->bitmap, 0, bm_bytes, s);
+        if (e == cudaSuccess && nrows > 0) {
+            ProfScope prof(ctx, "build", s);
+            k_build_dense<<<grid_for(ctx, nrows), 256, 0, s>>>(keys, payload, nrows, kmin,
+                                                               static_cast<uint32_t>(range), ht->payload,
+                                                               ht->bitmap, ctx->dstat);
+            QE_LAUNCHED(ctx);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) {
+            qe_free(ctx, ht->mem, s);
+            delete ht;
+            return qe_cuda_fail(ctx, e, "build: dense");
+        }
+    } else {
+        uint64_t slots = 64;
+        while (slots < static_cast<uint64_t>(2 * nrows)) slots <<= 1;
+        if (slots > (1ull << 32)) return qe_fail(ctx, QE_ERR_INVALID_ARG, "build: too many keys");
+        ht->slots = static_cast<int64_t>(slots);
+        ht->bytes = slots * 8;
+        st = qe_alloc(ctx, &ht->mem, ht->bytes, s);
+        if (st != QE_OK) {
+            delete ht;
+            return st;
+        }
+        ht->open = static_cast<unsigned long long *>(ht->mem);
+        k_fill_u64<<<grid_for(ctx, static_cast<int64_t>(slots)), 256, 0, s>>>(ht->open, static_cast<int64_t>(slots),
+                                                                               HT_EMPTY_SLOT);
+        QE_LAUNCHED(ctx);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess && nrows > 0) {
+            ProfScope prof(ctx, "build", s);
+            k_build_open<<<grid_for(ctx, nrows), 256, 0, s>>>(keys, payload, nrows, ht->open,
+                                                              static_cast<uint32_t>(slots - 1), ctx->dstat);
+            QE_LAUNCHED(ctx);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) {
+            qe_free(ctx, ht->mem, s);
+            delete ht;
+            return qe_cuda_fail(ctx, e, "build: open");
+        }
+    }
+    *out = ht;
+    return QE_OK;
+}
+
+extern "C" qe_status qe_join_build(qe_ctx *ctx, const int32_t *keys, const int32_t *payload, int64_t nrows,
+                                   const qe_build_opts *opts, qe_hash_table **out, void *stream)
+{
+    if (!ctx) return QE_ERR_INVALID_ARG;
+    if (!out || nrows < 0 || nrows >= (int64_t(1) << 31) || (nrows > 0 && (!keys || !payload)) ||
+        !qe_aligned(keys, 4) || !qe_aligned(payload, 4))
+        return qe_fail(ctx, QE_ERR_INVALID_ARG, "build: bad argument");
+    cudaSetDevice(ctx->device);
+    return join_build_impl(ctx, keys, payload, nrows, opts, out, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" qe_status qe_join_probe(qe_ctx *ctx, const qe_hash_table *ht, const int32_t *probe_keys,
+                                   const int32_t *sel, int64_t n, int32_t *out_probe_row, int32_t *out_build_payload,
+                                   int64_t capacity, int64_t *out_count, void *stream)
+{
+    if (!ctx) return QE_ERR_INVALID_ARG;
+    if (!ht || n < 0 || n >= (int64_t(1) << 31) || !out_count || capacity < 0 ||
+        (capacity > 0 && (!out_probe_row || !out_build_payload)) || (n > 0 && !probe_keys))
+        return qe_fail(ctx, QE_ERR_INVALID_ARG, "probe: bad argument");
+    cudaSetDevice(ctx->device);
+    ProbeOp op{};
+    op.ht = ht_view(ht);
+    op.keys = probe_keys;
+    op.sel = sel;
+    op.out_row = out_probe_row;
+    op.out_pay = out_build_payload;
+    return launch_compact<PROBE_ITEMS>(ctx, "probe", n, capacity, out_count, op, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" qe_status qe_join_info(const qe_hash_table *ht, qe_ht_info *info)
+{
+    if (!ht || !info) return QE_ERR_INVALID_ARG;
+    info->layout = ht->layout;
+    info->full = ht->full;
+    info->nkeys = ht->nkeys;
+    info->slots = ht->slots;
+    info->bytes = static_cast<int64_t>(ht->bytes);
+    info->key_min = ht->key_min;
+    info->key_max = ht->key_max;
+    return QE_OK;
+}
+
+extern "C" qe_status qe_join_destroy(qe_ctx *ctx, qe_hash_table *ht, void *stream)
+{
+    if (!ctx || !ht) return QE_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    qe_free(ctx, ht->mem, static_cast<cudaStream_t>(stream));
+    delete ht;
+    return QE_OK;
+}
