@@ -160,6 +160,33 @@ qe_status qe_filter(qe_ctx *ctx, const qe_col *cols, int ncols, const qe_pred *p
                     int npreds, int64_t nrows, int32_t *out_sel, int64_t sel_capacity,
                     int64_t *out_count, void *stream);
 
+/* Largest nrows accepted by qe_filter_noalloc: 65,536 tiles of 4,096 rows. */
+#define QE_FILTER_NOALLOC_MAX_ROWS (65536LL * 4096LL)
+
+/* qe_filter without any device allocation.  The paper has no counterpart;
+ * this entry point exists for callers that cannot allocate device memory
+ * from inside the call: a host whose device memory is entirely owned by its
+ * own allocator (a library cudaMalloc would fail or fragment that pool), and
+ * latency-critical callers that cannot afford an allocator call, which may
+ * synchronize the device.  Arguments, result and errors are those of
+ * qe_filter, computed by the same kernel.
+ *
+ * Its scratch (a tile counter and one look-back status word per 4,096-row
+ * tile, about 512 KB) is a static device array inside libqe, which every GPU
+ * that loads the library holds until the process exits.  The call clears the
+ * part it uses before each launch, allocates and frees nothing, and rejects
+ * nrows > QE_FILTER_NOALLOC_MAX_ROWS with QE_ERR_INVALID_ARG.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it; make that
+ * first call before any stream capture.  Every call shares the one array, so
+ * calls whose work overlaps on the GPU (on different streams, or from
+ * different contexts of one device) race: order them on one stream or
+ * synchronize between them. */
+qe_status qe_filter_noalloc(qe_ctx *ctx, const qe_col *cols, int ncols, const qe_pred *preds,
+                            int npreds, int64_t nrows, int32_t *out_sel, int64_t sel_capacity,
+                            int64_t *out_count, void *stream);
+
 /* ------------------------------------------------------------ partition */
 
 typedef enum {

@@ -109,6 +109,9 @@ _SIGS = {
     "qe_filter": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(qe_col), ctypes.c_int, ctypes.POINTER(qe_pred),
                                  ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                  ctypes.c_void_p]),
+    "qe_filter_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(qe_col), ctypes.c_int,
+                                         ctypes.POINTER(qe_pred), ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
+                                         ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "qe_partition": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(qe_col), ctypes.c_int,
                                     ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                     ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_void_p]),
@@ -251,6 +254,23 @@ def qe_filter(ctx: Context, cols, preds, out_sel=None, out_count=None, stream=No
                                              for p in preds])
     ctx.check(ctx.lib.qe_filter(ctx.h, ccols, len(cols), cpreds, len(preds), n, _ptr(out_sel),
                                 out_sel.numel() if n else 0, _ptr(out_count), _stream(stream)))
+    if check:
+        ctx.sync_status(stream)
+    return out_sel, out_count
+
+
+FILTER_NOALLOC_MAX_ROWS = 65536 * 4096
+
+
+def qe_filter_noalloc(ctx: Context, cols, preds, out_sel, out_count, nrows=None, stream=None, check=True):
+    """qe_filter without device allocation inside the call; the caller
+    passes every output buffer (see qe_filter_noalloc in qe.h)."""
+    n = (cols[0].numel() if cols else 0) if nrows is None else nrows
+    ccols = (qe_col * max(1, len(cols)))(*[col(c) for c in cols])
+    cpreds = (qe_pred * max(1, len(preds)))(*[qe_pred(p[0], p[1], p[2], p[3] if len(p) > 3 else 0)
+                                             for p in preds])
+    ctx.check(ctx.lib.qe_filter_noalloc(ctx.h, ccols, len(cols), cpreds, len(preds), n, _ptr(out_sel),
+                                        out_sel.numel(), _ptr(out_count), _stream(stream)))
     if check:
         ctx.sync_status(stream)
     return out_sel, out_count
