@@ -156,10 +156,13 @@ COLS = ("fk", "date", "price", "qty", "flag")
 
 
 def star_desc(qe, fact, dim, expected_groups):
+    # key_range: the flag column's min/max statistics (domain {0,1,2}); the
+    # attribute's range is read back by the join build
     return qe.pipeline_desc([fact[c] for c in COLS], [(1, qe.LT, DATE_LT)], fk_col=0, dim_key=dim["key"],
                             dim_payload=dim["attr"], key_hi_col=4, key_lo_col=qe.JOIN_PAYLOAD,
                             aggs=[(qe.SUM, 2, 3), (qe.COUNT, -1, -1), (qe.MIN, 2, -1), (qe.MAX, 2, -1)],
-                            expected_groups=expected_groups, est_selectivity=DATE_LT / 2557)
+                            expected_groups=expected_groups, est_selectivity=DATE_LT / 2557,
+                            key_range=((0, 2), None))
 
 
 # ---------------------------------------------------------------- CPU oracle leg

@@ -237,6 +237,9 @@ typedef struct {
     int64_t slots;
     int64_t bytes;
     int32_t key_min, key_max;
+    int32_t have_payload_range;   /* payload range known (read back with the key range) */
+    int32_t payload_min, payload_max;
+    int32_t pad;
 } qe_ht_info;
 
 /* Hash-join build (Sec. 2.2: the local join once both inputs are
@@ -337,11 +340,22 @@ typedef struct {
     qe_build_opts build;
     int64_t expected_groups;
     double est_selectivity;
+    /* Optional bounds of the group key's parts (column statistics): when
+     * have_key_range is nonzero, key_hi in [key_hi_min, key_hi_max] and
+     * key_lo in [key_lo_min, key_lo_max] let the group table be a direct
+     * (perfect-hash) array; rows outside the bounds still aggregate
+     * correctly through the hash table.  Without it, a join-payload low part
+     * takes its bounds from the join table when they are known. */
+    int32_t have_key_range;
+    int32_t pad2;
+    int64_t key_hi_min, key_hi_max, key_lo_min, key_lo_max;
 } qe_pipeline_desc;
 
 /* Run one pipeline: (build), then one fused pass over the fact table that
  * filters, probes and aggregates each row, then the group output.  Result
- * as in qe_groupby. */
+ * as in qe_groupby.  Groups are kept in a direct array indexed by the key's
+ * parts when their ranges are known and small (in shared memory when it
+ * fits), else in hash tables. */
 qe_status qe_pipeline(qe_ctx *ctx, const qe_pipeline_desc *desc, const qe_groups_out *out,
                       void *stream);
 

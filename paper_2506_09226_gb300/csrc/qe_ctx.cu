@@ -257,6 +257,55 @@ __global__ void k_gt_count(const unsigned long long *emitted, int64_t capacity, 
     if (n > capacity) dev_report(st, QE_ERR_CAPACITY, n);
 }
 
+struct DenseCompactArgs {
+    const unsigned long long *dense;
+    DenseKey d;
+    AggOps ops;
+    qe_groups_out out;
+    unsigned long long *emitted;
+};
+
+__global__ void __launch_bounds__(256) k_gd_compact(DenseCompactArgs A)
+{
+    const int lane = threadIdx.x & 31;
+    const uint64_t step = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+    for (uint64_t base = static_cast<uint64_t>(blockIdx.x) * blockDim.x; base < A.d.nslots; base += step) {
+        const uint64_t i = base + threadIdx.x;
+        const bool occ = i < A.d.nslots && A.dense[i * A.d.stride + A.d.occ] != 0;
+        const unsigned m = __ballot_sync(QE_FULL_MASK, occ);
+        if (!m) continue;
+        unsigned long long first = 0;
+        if (lane == 0) first = atomicAdd(A.emitted, static_cast<unsigned long long>(__popc(m)));
+        first = __shfl_sync(QE_FULL_MASK, first, 0);
+        if (occ) {
+            const int64_t pos = static_cast<int64_t>(first) + __popc(m & ((1u << lane) - 1));
+            if (pos < A.out.capacity) {
+                A.out.keys[pos] = dense_key(A.d, i);
+                for (int a = 0; a < A.ops.n; a++)
+                    A.out.aggs[a][pos] = agg_decode(A.ops.op[a], A.dense[i * A.d.stride + a]);
+            }
+        }
+    }
+}
+
+qe_status gt_finalize_dense(qe_ctx *ctx, const GroupTableHost &t, const AggOps &ops, const DenseKey &d,
+                            const unsigned long long *dense, const qe_groups_out *out, cudaStream_t s)
+{
+    DenseCompactArgs A;
+    A.dense = dense;
+    A.d = d;
+    A.ops = ops;
+    A.out = *out;
+    A.emitted = t.words + t.slots * t.stride + 1;
+    int64_t blocks = qe_ceil_div(static_cast<int64_t>(d.nslots), 256);
+    const int64_t cap = static_cast<int64_t>(ctx->num_sms) * 8;
+    if (blocks > cap) blocks = cap;
+    k_gd_compact<<<static_cast<unsigned>(blocks), 256, 0, s>>>(A);
+    QE_LAUNCHED(ctx);
+    QE_CHECK_LAUNCH(ctx);
+    return gt_finalize(ctx, t, ops, out, s);
+}
+
 qe_status gt_finalize(qe_ctx *ctx, const GroupTableHost &t, const AggOps &ops, const qe_groups_out *out,
                       cudaStream_t s)
 {

@@ -7,7 +7,7 @@
 // one HBM table at the end; rows whose key cannot be placed in the
 // shared-memory table go straight to the HBM table.  The HBM table is then
 // compacted into the caller's output.
-#include "qe_internal.cuh"
+#include "qe_pipe_core.cuh"
 
 namespace {
 
@@ -28,7 +28,7 @@ struct GroupbyArgs {
     AggOps ops;
     GTable g;
     int S;
-    int max_probe;
+    int log2S;
 };
 
 __device__ __forceinline__ int64_t col_at(const ColRef &c, int64_t i, int64_t r)
@@ -43,16 +43,22 @@ __global__ void __launch_bounds__(GB_THREADS) k_groupby(GroupbyArgs A)
     __syncthreads();
     const int64_t tile_rows = static_cast<int64_t>(GB_THREADS) * GB_ITEMS;
     const int64_t ntiles = (A.n + tile_rows - 1) / tile_rows;
+    const uint32_t mask = A.S ? static_cast<uint32_t>(A.S - 1) : 0;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        int64_t r[GB_ITEMS];
 #pragma unroll
         for (int k = 0; k < GB_ITEMS; k++) {
             const int64_t i = tile * tile_rows + k * GB_THREADS + threadIdx.x;
-            if (i >= A.n) continue;
-            const int64_t r = A.rows ? static_cast<int64_t>(__ldg(A.rows + i)) : i;
-            const int64_t lo = col_at(A.key_lo, i, r);
+            r[k] = i < A.n ? (A.rows ? static_cast<int64_t>(__ldg(A.rows + i)) : i) : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < GB_ITEMS; k++) {
+            const int64_t i = tile * tile_rows + k * GB_THREADS + threadIdx.x;
+            if (r[k] < 0) continue;
+            const int64_t lo = col_at(A.key_lo, i, r[k]);
             int64_t key = lo;
             if (A.key_hi.data)
-                key = static_cast<int64_t>((static_cast<uint64_t>(col_at(A.key_hi, i, r)) << 32) |
+                key = static_cast<int64_t>((static_cast<uint64_t>(col_at(A.key_hi, i, r[k])) << 32) |
                                            static_cast<uint32_t>(lo));
             const unsigned long long kx = static_cast<unsigned long long>(key) ^ GB_SIGN;
             if (kx == 0) {
@@ -60,16 +66,30 @@ __global__ void __launch_bounds__(GB_THREADS) k_groupby(GroupbyArgs A)
                 continue;
             }
             unsigned long long e[QE_MAX_AGGS];
-            _Pragma("unroll") for (int a = 0; a < QE_MAX_AGGS; a++) if (a < A.ops.n) {
-                int64_t v = 0;
-                if (A.ops.op[a] != QE_COUNT) {
-                    uint64_t x = static_cast<uint64_t>(col_at(A.a[a], i, r));
-                    if (A.b[a].data) x *= static_cast<uint64_t>(col_at(A.b[a], i, r));
-                    v = static_cast<int64_t>(x);
+#pragma unroll
+            for (int a = 0; a < QE_MAX_AGGS; a++) {
+                e[a] = 0;
+                if (a < A.ops.n) {
+                    int64_t v = 0;
+                    if (A.ops.op[a] != QE_COUNT) {
+                        uint64_t x = static_cast<uint64_t>(col_at(A.a[a], i, r[k]));
+                        if (A.b[a].data) x *= static_cast<uint64_t>(col_at(A.b[a], i, r[k]));
+                        v = static_cast<int64_t>(x);
+                    }
+                    e[a] = agg_encode(A.ops.op[a], v);
                 }
-                e[a] = agg_encode(A.ops.op[a], v);
             }
-            st_fold_row(sm, A.S, A.ops, A.g, kx, e, A.max_probe);
+            if (A.S) {
+                const uint32_t h = st_hash(kx, A.log2S);
+                const int slot = sm[h] == kx ? static_cast<int>(h) : st_find_slow(sm, mask, kx, h);
+                if (slot >= 0) {
+#pragma unroll
+                    for (int a = 0; a < QE_MAX_AGGS; a++)
+                        if (a < A.ops.n) st_update(sm + (a + 1) * A.S + slot, A.ops.op[a], e[a]);
+                    continue;
+                }
+            }
+            spill_row_ni(A.g, A.ops, kx, e[0], e[1], e[2], e[3]);
         }
     }
     if (A.S) {
@@ -136,7 +156,8 @@ extern "C" qe_status qe_groupby(qe_ctx *ctx, int64_t n, const int32_t *rows, qe_
         A.S = st_slots_for(out->capacity, naggs, placement == QE_GB_SMEM ? budget : budget / 2);
         if (placement == QE_GB_SMEM && A.S == 0) A.S = st_slots_max(naggs, budget);
     }
-    A.max_probe = 32;
+    A.log2S = 0;
+    while ((1 << A.log2S) < A.S) A.log2S++;
     const size_t smem = static_cast<size_t>(A.S) * 8 * (1 + naggs);
     cudaError_t e = cudaSuccess;
     if (n > 0) {

@@ -431,6 +431,71 @@ __device__ __forceinline__ void st_flush(unsigned long long *sm, int S, const Ag
     }
 }
 
+// ------------------------------------------------------------ dense group layout
+// When the two parts of the group key have known, small ranges, the group
+// table is a direct array (a perfect hash): slot = (hi - hi_min) * lo_span +
+// (lo - lo_min).  Each slot holds the aggregate words plus, when no COUNT is
+// asked for, one hidden row count that marks occupied slots.
+struct DenseKey {
+    int32_t on;
+    int32_t has_hi;
+    int64_t hi_min, lo_min;
+    uint64_t hi_span, lo_span;
+    uint64_t nslots;
+    int32_t occ;       // word that counts rows (a COUNT aggregate or the hidden word)
+    int32_t stride;    // words per slot
+    int32_t hidden;    // the occ word is hidden (no COUNT aggregate)
+    int32_t pad;
+};
+
+__device__ __forceinline__ int64_t dense_index(const DenseKey &d, int64_t hi, int64_t lo)
+{
+    const uint64_t l = static_cast<uint64_t>(lo - d.lo_min);
+    if (l >= d.lo_span) return -1;
+    uint64_t h = 0;
+    if (d.has_hi) {
+        h = static_cast<uint64_t>(hi - d.hi_min);
+        if (h >= d.hi_span) return -1;
+    }
+    return static_cast<int64_t>(h * d.lo_span + l);
+}
+
+__device__ __forceinline__ int64_t dense_key(const DenseKey &d, uint64_t idx)
+{
+    const int64_t lo = d.lo_min + static_cast<int64_t>(idx % d.lo_span);
+    if (!d.has_hi) return lo;
+    const int64_t hi = d.hi_min + static_cast<int64_t>(idx / d.lo_span);
+    return static_cast<int64_t>((static_cast<uint64_t>(hi) << 32) | static_cast<uint32_t>(lo));
+}
+
+// Host: a dense layout for the key parts' ranges, or on = 0 when the ranges
+// are too wide (more than max_slots slots, or a 64-bit low part that the key
+// packing would truncate).
+static inline DenseKey dense_plan(bool has_hi, int64_t hi_min, int64_t hi_max, int64_t lo_min, int64_t lo_max,
+                                  const AggOps &ops, uint64_t max_slots)
+{
+    DenseKey d{};
+    if (lo_max < lo_min || (has_hi && hi_max < hi_min)) return d;
+    const uint64_t ls = static_cast<uint64_t>(lo_max - lo_min) + 1;
+    const uint64_t hs = has_hi ? static_cast<uint64_t>(hi_max - hi_min) + 1 : 1;
+    if (ls == 0 || hs == 0 || ls > max_slots || hs > max_slots || ls * hs > max_slots) return d;
+    if (has_hi && ls > (1ull << 32)) return d;
+    d.on = 1;
+    d.has_hi = has_hi;
+    d.hi_min = has_hi ? hi_min : 0;
+    d.lo_min = lo_min;
+    d.hi_span = hs;
+    d.lo_span = ls;
+    d.nslots = ls * hs;
+    d.occ = -1;
+    for (int a = 0; a < ops.n; a++)
+        if (ops.op[a] == QE_COUNT) d.occ = a;
+    d.hidden = d.occ < 0;
+    if (d.hidden) d.occ = ops.n;
+    d.stride = ops.n + (d.hidden ? 1 : 0);
+    return d;
+}
+
 // Host helpers shared by group-by and pipeline.
 struct GroupTableHost {
     unsigned long long *words = nullptr;  // device
@@ -443,6 +508,10 @@ qe_status gt_create(qe_ctx *ctx, int64_t capacity, int naggs, GroupTableHost &t,
 // Compact the table into `out` (keys + decoded aggregates + ngroups).
 qe_status gt_finalize(qe_ctx *ctx, const GroupTableHost &t, const AggOps &ops, const qe_groups_out *out,
                       cudaStream_t s);
+// Same, first emitting the occupied slots of a global dense table
+// (AoS, d.stride words per slot).
+qe_status gt_finalize_dense(qe_ctx *ctx, const GroupTableHost &t, const AggOps &ops, const DenseKey &d,
+                            const unsigned long long *dense, const qe_groups_out *out, cudaStream_t s);
 qe_status gt_check_out(qe_ctx *ctx, const qe_groups_out *out, int naggs);
 
 // Smem group-table sizing: slots for `groups` at <= 75% load, 0 when the
@@ -464,6 +533,21 @@ static inline int st_slots_max(int naggs, size_t smem_budget)
     while ((s * 2) * 8 * (1 + naggs) <= smem_budget) s <<= 1;
     return static_cast<int>(s);
 }
+
+// Library-owned join table (qe_join.cu builds it).
+struct qe_hash_table {
+    int32_t layout = QE_HT_DENSE;
+    int32_t full = 0;
+    int32_t key_min = 0, key_max = -1;
+    int32_t have_pay = 0, pay_min = 0, pay_max = -1;
+    int64_t nkeys = 0;
+    int64_t slots = 0;
+    void *mem = nullptr;
+    size_t bytes = 0;
+    int32_t *payload = nullptr;
+    uint32_t *bitmap = nullptr;
+    unsigned long long *open = nullptr;
+};
 
 HtView ht_view(const qe_hash_table *ht);
 qe_status join_build_impl(qe_ctx *ctx, const int32_t *keys, const int32_t *payload, int64_t nrows,

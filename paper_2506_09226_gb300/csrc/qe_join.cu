@@ -14,18 +14,6 @@
 
 #include "qe_compact.cuh"
 
-struct qe_hash_table {
-    int32_t layout = QE_HT_DENSE;
-    int32_t full = 0;
-    int32_t key_min = 0, key_max = -1;
-    int64_t nkeys = 0;
-    int64_t slots = 0;
-    void *mem = nullptr;
-    size_t bytes = 0;
-    int32_t *payload = nullptr;
-    uint32_t *bitmap = nullptr;
-    unsigned long long *open = nullptr;
-};
 
 HtView ht_view(const qe_hash_table *ht)
 {
@@ -43,22 +31,29 @@ HtView ht_view(const qe_hash_table *ht)
 
 namespace {
 
-__global__ void __launch_bounds__(256) k_minmax(const int32_t *keys, int64_t n, int32_t *mm)
+// Min and max of the build keys and of the payloads: mm = {kmin, kmax, pmin, pmax}.
+__global__ void __launch_bounds__(256) k_minmax(const int32_t *keys, const int32_t *pay, int64_t n, int32_t *mm)
 {
-    int32_t lo = INT_MAX, hi = INT_MIN;
+    int32_t lo = INT_MAX, hi = INT_MIN, plo = INT_MAX, phi = INT_MIN;
     for (int64_t i = blockIdx.x * 256ll + threadIdx.x; i < n; i += static_cast<int64_t>(gridDim.x) * 256) {
-        int32_t k = __ldcs(keys + i);
+        const int32_t k = __ldcs(keys + i), p = __ldcs(pay + i);
         lo = min(lo, k);
         hi = max(hi, k);
+        plo = min(plo, p);
+        phi = max(phi, p);
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
         lo = min(lo, __shfl_xor_sync(QE_FULL_MASK, lo, d));
         hi = max(hi, __shfl_xor_sync(QE_FULL_MASK, hi, d));
+        plo = min(plo, __shfl_xor_sync(QE_FULL_MASK, plo, d));
+        phi = max(phi, __shfl_xor_sync(QE_FULL_MASK, phi, d));
     }
     if ((threadIdx.x & 31) == 0) {
         atomicMin(mm, lo);
         atomicMax(mm + 1, hi);
+        atomicMin(mm + 2, plo);
+        atomicMax(mm + 3, phi);
     }
 }
 
@@ -66,6 +61,8 @@ __global__ void k_minmax_init(int32_t *mm)
 {
     mm[0] = INT_MAX;
     mm[1] = INT_MIN;
+    mm[2] = INT_MAX;
+    mm[3] = INT_MIN;
 }
 
 __global__ void __launch_bounds__(256) k_build_dense(const int32_t *keys, const int32_t *pay, int64_t n,
@@ -181,6 +178,7 @@ qe_status join_build_impl(qe_ctx *ctx, const int32_t *keys, const int32_t *paylo
     if (opts) o = *opts;
     if (o.layout < QE_HT_AUTO || o.layout > QE_HT_OPEN) return qe_fail(ctx, QE_ERR_INVALID_ARG, "build: bad layout");
     int32_t kmin = 0, kmax = -1;
+    int32_t have_pay = 0, pay_min = 0, pay_max = -1;
     if (nrows > 0) {
         if (o.have_range) {
             kmin = o.key_min;
@@ -188,20 +186,23 @@ qe_status join_build_impl(qe_ctx *ctx, const int32_t *keys, const int32_t *paylo
             if (kmin > kmax) return qe_fail(ctx, QE_ERR_INVALID_ARG, "build: empty key range");
         } else {
             void *mm = nullptr;
-            qe_status st = qe_alloc(ctx, &mm, 8, s);
+            qe_status st = qe_alloc(ctx, &mm, 16, s);
             if (st != QE_OK) return st;
-            int32_t host[2];
+            int32_t host[4];
             k_minmax_init<<<1, 1, 0, s>>>(static_cast<int32_t *>(mm));
             QE_LAUNCHED(ctx);
-            k_minmax<<<grid_for(ctx, nrows), 256, 0, s>>>(keys, nrows, static_cast<int32_t *>(mm));
+            k_minmax<<<grid_for(ctx, nrows), 256, 0, s>>>(keys, payload, nrows, static_cast<int32_t *>(mm));
             QE_LAUNCHED(ctx);
             cudaError_t e = cudaGetLastError();
-            if (e == cudaSuccess) e = cudaMemcpyAsync(host, mm, 8, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(host, mm, 16, cudaMemcpyDeviceToHost, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             qe_free(ctx, mm, s);
             if (e != cudaSuccess) return qe_cuda_fail(ctx, e, "build: key range");
             kmin = host[0];
             kmax = host[1];
+            have_pay = 1;
+            pay_min = host[2];
+            pay_max = host[3];
         }
     }
     const uint64_t range = nrows > 0 ? static_cast<uint64_t>(static_cast<int64_t>(kmax) - kmin + 1) : 1;
@@ -215,6 +216,9 @@ qe_status join_build_impl(qe_ctx *ctx, const int32_t *keys, const int32_t *paylo
     ht->layout = layout;
     ht->key_min = kmin;
     ht->key_max = kmax;
+    ht->have_pay = have_pay;
+    ht->pay_min = pay_min;
+    ht->pay_max = pay_max;
     ht->nkeys = nrows;
     qe_status st;
     if (layout == QE_HT_DENSE) {
@@ -316,6 +320,10 @@ extern "C" qe_status qe_join_info(const qe_hash_table *ht, qe_ht_info *info)
     info->bytes = static_cast<int64_t>(ht->bytes);
     info->key_min = ht->key_min;
     info->key_max = ht->key_max;
+    info->have_payload_range = ht->have_pay;
+    info->payload_min = ht->pay_min;
+    info->payload_max = ht->pay_max;
+    info->pad = 0;
     return QE_OK;
 }
 

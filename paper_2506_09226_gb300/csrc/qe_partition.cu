@@ -10,22 +10,29 @@
 //                      off[b][p] = sum over earlier blocks of hist[.][p] and
 //                      base[p] = sum over earlier destinations of all rows, so
 //                      block b's rows for p start at base[p] + off[b][p];
-//   3. k_part_scatter  block b walks its rows in chunks of CHUNK in order.  A
+//   3. k_part_scatter  block b walks its rows in chunks of CHUNK in order.  The
+//                      next chunk's keys (and an int64 payload) are copied into
+//                      shared memory with bulk TMA copies while the current one
+//                      is processed (double buffer, mbarrier completion).  A
 //                      chunk is ranked stably by destination in shared memory
 //                      (one or two LSD digit passes; within a warp equal digits
 //                      are ranked with __match_any_sync, warps and digits with a
-//                      block scan), staged in destination order, and written
-//                      out so that consecutive lanes store consecutive rows of
-//                      one destination.  Each block keeps a running output
-//                      offset per destination, so rows keep their input order.
-#include "qe_internal.cuh"
+//                      block scan); rows are then written in destination order
+//                      through the inverse permutation, so consecutive lanes
+//                      store consecutive rows of one destination.  Each block
+//                      keeps a running output offset per destination, so rows
+//                      keep their input order.
+#include "qe_pipe_core.cuh"
 
 namespace {
 
-constexpr int PT = 512;            // threads per block (16 warps)
+constexpr int PT = 1024;           // scatter threads per block (32 warps), one block per SM
 constexpr int NW = PT / 32;
-constexpr int P_ITEMS = 8;         // rows per thread per chunk
+constexpr int P_ITEMS = 4;         // rows per thread per chunk
 constexpr int CHUNK = PT * P_ITEMS;
+constexpr int HT = 1024;           // histogram threads per block
+constexpr int H_ITEMS = 8;
+constexpr int H_SPLIT = 4;         // histogram blocks per scatter block
 constexpr int MAX_PAY = QE_MAX_COLS - 1;
 
 struct PartArgs {
@@ -38,34 +45,46 @@ struct PartArgs {
     int32_t pay_type[MAX_PAY];
     int64_t *out_keys;
     void *out_pay[MAX_PAY];
-    uint32_t *hist;           // [G][F]
+    uint32_t *hist;           // [G][F], zeroed
     int64_t *off;             // [G][F]
     const int64_t *base;      // [F + 1] (= out_offsets)
+    int tma;                  // keys (and the int64 payload) are 16-byte aligned
+    int64_t spin_limit;
+    qe_dev_status *st;
 };
 
-__global__ void __launch_bounds__(PT) k_part_hist(PartArgs A)
+// Histogram of destinations; H_SPLIT blocks share each scatter block's range
+// and add their counts into hist[b][p].
+__global__ void __launch_bounds__(HT) k_part_hist(PartArgs A)
 {
     extern __shared__ uint32_t s_hist[];
     const int F = 1 << A.log2f;
-    for (int p = threadIdx.x; p < F; p += PT) s_hist[p] = 0;
+    for (int p = threadIdx.x; p < F; p += HT) s_hist[p] = 0;
     __syncthreads();
-    const int64_t lo = static_cast<int64_t>(blockIdx.x) * A.rows_per_block;
-    const int64_t hi = min(A.n, lo + A.rows_per_block);
-    for (int64_t c = lo; c < hi; c += CHUNK) {
-        int64_t k[P_ITEMS];
+    const int b = blockIdx.x / H_SPLIT, k = blockIdx.x % H_SPLIT;
+    const int64_t blo = static_cast<int64_t>(b) * A.rows_per_block;
+    const int64_t bhi = min(A.n, blo + A.rows_per_block);
+    const int64_t sub = (A.rows_per_block + H_SPLIT - 1) / H_SPLIT;
+    const int64_t lo = blo + k * sub;
+    const int64_t hi = min(bhi, lo + sub);
+    for (int64_t c = lo; c < hi; c += static_cast<int64_t>(HT) * H_ITEMS) {
+        int64_t key[H_ITEMS];
 #pragma unroll
-        for (int i = 0; i < P_ITEMS; i++) {
-            int64_t r = c + i * PT + threadIdx.x;
-            k[i] = r < hi ? __ldcs(reinterpret_cast<const long long *>(A.keys) + r) : 0;
+        for (int i = 0; i < H_ITEMS; i++) {
+            const int64_t r = c + i * HT + threadIdx.x;
+            key[i] = r < hi ? __ldcs(reinterpret_cast<const long long *>(A.keys) + r) : 0;
         }
 #pragma unroll
-        for (int i = 0; i < P_ITEMS; i++) {
-            int64_t r = c + i * PT + threadIdx.x;
-            if (r < hi) atomicAdd(&s_hist[dev_part_id(k[i], A.log2f, A.mode, A.shift)], 1u);
+        for (int i = 0; i < H_ITEMS; i++) {
+            const int64_t r = c + i * HT + threadIdx.x;
+            if (r < hi) atomicAdd(&s_hist[dev_part_id(key[i], A.log2f, A.mode, A.shift)], 1u);
         }
     }
     __syncthreads();
-    for (int p = threadIdx.x; p < F; p += PT) A.hist[static_cast<int64_t>(blockIdx.x) * F + p] = s_hist[p];
+    for (int p = threadIdx.x; p < F; p += HT) {
+        const uint32_t c = s_hist[p];
+        if (c) atomicAdd(A.hist + static_cast<int64_t>(b) * F + p, c);
+    }
 }
 
 // One thread per destination p: prefix of hist[.][p] over blocks.
@@ -114,75 +133,80 @@ __global__ void __launch_bounds__(1024) k_part_basescan(const int64_t *tot, int6
     if (t == 0) out_offsets[F] = n;
 }
 
-// Block-wide exclusive scan, in place, of cnt[0..N) (uint16 counts, N a
-// multiple of PT or smaller than PT), totals <= CHUNK.
-__device__ __forceinline__ void block_excl_scan_u16(uint16_t *cnt, int N, int *s_w)
+// Digit counters: cnt[d * CSTRIDE + w] (uint32) for digit d and warp w.  The
+// odd stride puts different digits of one warp in different banks.
+constexpr int CSTRIDE = NW + 1;
+
+// Block-wide exclusive scan, in place, of the counters in digit-major order
+// (d, then w) over ndig digits.  Totals are at most CHUNK.
+__device__ __forceinline__ void block_excl_scan_cnt(uint32_t *cnt, int ndig, int *s_w)
 {
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int N = ndig * NW;
     const int per = (N + PT - 1) / PT;
-    int local = 0;
+    uint32_t local = 0;
     for (int j = 0; j < per; j++) {
-        int i = t * per + j;
-        if (i < N) local += cnt[i];
+        const int i = t * per + j;
+        if (i < N) local += cnt[(i / NW) * CSTRIDE + (i % NW)];
     }
-    int inc = warp_incl_scan(local);
-    if (lane == 31) s_w[warp] = inc;
+    const uint32_t inc = warp_incl_scan(local);
+    if (lane == 31) s_w[warp] = static_cast<int>(inc);
     __syncthreads();
     if (warp == 0) {
-        int w = lane < NW ? s_w[lane] : 0;
-        int wi = warp_incl_scan(w);
+        const int w = lane < NW ? s_w[lane] : 0;
+        const int wi = warp_incl_scan(w);
         if (lane < NW) s_w[lane] = wi - w;
     }
     __syncthreads();
-    int run = s_w[warp] + inc - local;
+    uint32_t run = static_cast<uint32_t>(s_w[warp]) + inc - local;
     for (int j = 0; j < per; j++) {
-        int i = t * per + j;
+        const int i = t * per + j;
         if (i < N) {
-            int c = cnt[i];
-            cnt[i] = static_cast<uint16_t>(run);
-            run += c;
+            uint32_t *c = cnt + (i / NW) * CSTRIDE + (i % NW);
+            const uint32_t v = *c;
+            *c = run;
+            run += v;
         }
     }
     __syncthreads();
 }
 
-// Stable rank of chunk positions s < m by digit (pid_in[s] >> shift) & mask.
-// Writes newpos[s] (rank) and pid_out[rank] = pid_in[s].  Items are
-// warp-striped: warp w owns positions [w*32*P_ITEMS, (w+1)*32*P_ITEMS).
-__device__ __forceinline__ void rank_pass(const uint16_t *pid_in, int m, int shift, int bits, uint16_t *cnt,
-                                          uint16_t *newpos, uint16_t *pid_out, int *s_w)
+// Stable rank of the chunk's m packed words (destination << 12 | source row)
+// by the digit (destination >> shift) & (2^bits - 1): in[s] moves to out[rank].
+// Items are warp-striped: warp w owns positions [w*32*P_ITEMS, (w+1)*32*P_ITEMS),
+// so the natural order is (warp, item, lane).
+__device__ __forceinline__ void rank_pass(const uint32_t *in, uint32_t *out, int m, int shift, int bits, uint32_t *cnt,
+                                          int *s_w)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1;
     const int ndig = 1 << bits;
     const unsigned dmask = ndig - 1;
-    for (int i = threadIdx.x; i < ndig * NW; i += PT) cnt[i] = 0;
+    for (int i = threadIdx.x; i < ndig * CSTRIDE; i += PT) cnt[i] = 0;
     __syncthreads();
-    uint16_t r[P_ITEMS];
-    uint16_t dg[P_ITEMS];
+    uint32_t wv[P_ITEMS], r[P_ITEMS];
 #pragma unroll
     for (int k = 0; k < P_ITEMS; k++) {
-        const int s = warp * 32 * P_ITEMS + k * 32 + lane;
-        const bool valid = s < m;
-        const unsigned d = valid ? ((pid_in[s] >> shift) & dmask) : 0xffffu;
+        const int s2 = warp * 32 * P_ITEMS + k * 32 + lane;
+        const bool valid = s2 < m;
+        wv[k] = valid ? in[s2] : 0;
+        const unsigned d = valid ? ((wv[k] >> (12 + shift)) & dmask) : 0xffffu;
         const unsigned peers = __match_any_sync(QE_FULL_MASK, d);
-        int basec = 0;
-        if (valid) basec = cnt[d * NW + warp];
+        uint32_t basec = 0;
+        if (valid) basec = cnt[d * CSTRIDE + warp];
         __syncwarp();
-        if (valid && lane == __ffs(peers) - 1) cnt[d * NW + warp] = static_cast<uint16_t>(basec + __popc(peers));
+        if (valid && lane == __ffs(peers) - 1) cnt[d * CSTRIDE + warp] = basec + __popc(peers);
         __syncwarp();
-        r[k] = static_cast<uint16_t>(basec + __popc(peers & lt));
-        dg[k] = static_cast<uint16_t>(d);
+        r[k] = basec + __popc(peers & lt);
     }
     __syncthreads();
-    block_excl_scan_u16(cnt, ndig * NW, s_w);
+    block_excl_scan_cnt(cnt, ndig, s_w);
 #pragma unroll
     for (int k = 0; k < P_ITEMS; k++) {
-        const int s = warp * 32 * P_ITEMS + k * 32 + lane;
-        if (s < m) {
-            int t = cnt[dg[k] * NW + warp] + r[k];
-            newpos[s] = static_cast<uint16_t>(t);
-            pid_out[t] = pid_in[s];
+        const int s2 = warp * 32 * P_ITEMS + k * 32 + lane;
+        if (s2 < m) {
+            const unsigned d = (wv[k] >> (12 + shift)) & dmask;
+            out[cnt[d * CSTRIDE + warp] + r[k]] = wv[k];
         }
     }
     __syncthreads();
@@ -201,105 +225,129 @@ __device__ __forceinline__ void copy_elem(void *dst, const void *src, int type, 
 // FAST: exactly one int64 payload column, staged in shared memory with the
 // keys.  Otherwise payload columns are gathered by chunk-local source row.
 template <bool FAST>
-__global__ void __launch_bounds__(PT) k_part_scatter(PartArgs A)
+__global__ void __launch_bounds__(PT, 1) k_part_scatter(PartArgs A)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int F = 1 << A.log2f;
-    // layout: run[F] i64 | skey[CHUNK] i64 | spay[CHUNK] i64 (FAST) or
-    //         srow[CHUNK] u16 (generic) | start[F] u16 |
-    //         pidA, pidB, pos1, pos2 [CHUNK] u16 | cnt[256*NW] u16
-    int64_t *run = reinterpret_cast<int64_t *>(smem);
-    int64_t *skey = run + F;
-    int64_t *spay = skey + CHUNK;
-    uint16_t *srow = reinterpret_cast<uint16_t *>(spay);
-    uint16_t *start = reinterpret_cast<uint16_t *>(spay + CHUNK);
-    uint16_t *pidA = start + F;
-    uint16_t *pidB = pidA + CHUNK;
-    uint16_t *pos1 = pidB + CHUNK;
-    uint16_t *pos2 = pos1 + CHUNK;
-    uint16_t *cnt = pos2 + CHUNK;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) unsigned long long s_bar[2];
     __shared__ int s_w[NW];
+    __shared__ int s_abort;
+    const int F = 1 << A.log2f;
+    // layout: bufK[2][CHUNK] i64 | bufP[2][CHUNK] i64 (FAST) | run[F] i64 |
+    //         wA, wB [CHUNK] u32 (destination << 12 | source row) | start[F] u16 |
+    //         cnt[64 * CSTRIDE] u32
+    int64_t *bufK = reinterpret_cast<int64_t *>(smem);
+    int64_t *bufP = bufK + 2 * CHUNK;
+    int64_t *run = FAST ? bufP + 2 * CHUNK : bufP;
+    uint32_t *wA = reinterpret_cast<uint32_t *>(run + F);
+    uint32_t *wB = wA + CHUNK;
+    uint32_t *cnt = wB + CHUNK;
+    uint16_t *start = reinterpret_cast<uint16_t *>(cnt + 64 * CSTRIDE);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int b = blockIdx.x;
+    const int64_t lo = static_cast<int64_t>(b) * A.rows_per_block;
+    const int64_t hi = min(A.n, lo + A.rows_per_block);
+    const int64_t nch = (hi - lo + CHUNK - 1) / CHUNK;
     for (int p = threadIdx.x; p < F; p += PT) run[p] = A.base[p] + A.off[static_cast<int64_t>(b) * F + p];
-    // digit plan: one pass for F <= 256, else two passes of ceil(log2f / 2) bits
-    const int passes = A.log2f == 0 ? 0 : (A.log2f <= 8 ? 1 : 2);
+    if (threadIdx.x == 0) {
+        s_abort = 0;
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        mbar_fence_init();
+    }
+    const int passes = A.log2f == 0 ? 0 : (A.log2f <= 6 ? 1 : 2);
     const int bits1 = passes == 2 ? (A.log2f + 1) / 2 : A.log2f;
     const int bits2 = A.log2f - bits1;
     __syncthreads();
+    const uint64_t pol = l2_evict_first_policy();
 
-    const int64_t lo = static_cast<int64_t>(b) * A.rows_per_block;
-    const int64_t hi = min(A.n, lo + A.rows_per_block);
-    for (int64_t c = lo; c < hi; c += CHUNK) {
-        const int m = static_cast<int>(hi - c < CHUNK ? hi - c : CHUNK);
-        int64_t key[P_ITEMS], pay[P_ITEMS];
-#pragma unroll
-        for (int k = 0; k < P_ITEMS; k++) {
-            const int s = warp * 32 * P_ITEMS + k * 32 + lane;
-            key[k] = s < m ? __ldcs(reinterpret_cast<const long long *>(A.keys) + c + s) : 0;
-            if (FAST) pay[k] = s < m ? __ldcs(static_cast<const long long *>(A.pay[0]) + c + s) : 0;
+    // chunk c: rows [lo + c*CHUNK, ...) into buffer c & 1
+    auto issue = [&](int64_t c) {
+        const int64_t r0 = lo + c * CHUNK;
+        const int m = static_cast<int>(hi - r0 < CHUNK ? hi - r0 : CHUNK);
+        const int mc = A.tma ? (m & ~1) : 0;      // 16-byte multiple
+        unsigned long long *bar = &s_bar[c & 1];
+        const uint32_t bytes = static_cast<uint32_t>(mc) * 8u * (FAST ? 2u : 1u);
+        if (bytes) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(bar, bytes);
+            tma_load_1d(bufK + (c & 1) * CHUNK, A.keys + r0, mc * 8u, bar, pol);
+            if (FAST) tma_load_1d(bufP + (c & 1) * CHUNK, static_cast<const long long *>(A.pay[0]) + r0, mc * 8u, bar, pol);
+        } else {
+            mbar_arrive(bar);
         }
-#pragma unroll
-        for (int k = 0; k < P_ITEMS; k++) {
-            const int s = warp * 32 * P_ITEMS + k * 32 + lane;
-            if (s < m) pidA[s] = static_cast<uint16_t>(dev_part_id(key[k], A.log2f, A.mode, A.shift));
+    };
+    if (threadIdx.x == 0 && nch > 0) issue(0);
+
+    for (int64_t c = 0; c < nch; c++) {
+        if (threadIdx.x == 0 && c + 1 < nch) issue(c + 1);
+        const int64_t r0 = lo + c * CHUNK;
+        const int m = static_cast<int>(hi - r0 < CHUNK ? hi - r0 : CHUNK);
+        const int mc = A.tma ? (m & ~1) : 0;
+        int64_t *keys = bufK + (c & 1) * CHUNK;
+        int64_t *pays = bufP + (c & 1) * CHUNK;
+        if (!mbar_wait(&s_bar[c & 1], static_cast<uint32_t>((c >> 1) & 1), A.spin_limit)) {
+            if (threadIdx.x == 0) dev_report(A.st, QE_ERR_TIMEOUT, 0);
+            s_abort = 1;
+        }
+        // rows the bulk copy did not cover (unaligned columns, odd tail)
+        for (int s2 = mc + threadIdx.x; s2 < m; s2 += PT) {
+            keys[s2] = A.keys[r0 + s2];
+            if (FAST) pays[s2] = static_cast<const long long *>(A.pay[0])[r0 + s2];
         }
         __syncthreads();
-        const uint16_t *pidS = pidA;
+        if (s_abort) break;
+#pragma unroll
+        for (int k = 0; k < P_ITEMS; k++) {
+            const int s2 = warp * 32 * P_ITEMS + k * 32 + lane;
+            if (s2 < m) wA[s2] = (dev_part_id(keys[s2], A.log2f, A.mode, A.shift) << 12) | static_cast<uint32_t>(s2);
+        }
+        __syncthreads();
+        const uint32_t *sorted = wA;
         if (passes >= 1) {
-            rank_pass(pidA, m, 0, bits1, cnt, pos1, pidB, s_w);
-            pidS = pidB;
+            rank_pass(wA, wB, m, 0, bits1, cnt, s_w);
+            sorted = wB;
         }
         if (passes == 2) {
-            rank_pass(pidB, m, bits1, bits2, cnt, pos2, pidA, s_w);
-            pidS = pidA;
+            rank_pass(wB, wA, m, bits1, bits2, cnt, s_w);
+            sorted = wA;
         }
-        // stage rows in destination order (generic path: the source row)
-#pragma unroll
-        for (int k = 0; k < P_ITEMS; k++) {
-            const int s = warp * 32 * P_ITEMS + k * 32 + lane;
-            if (s < m) {
-                int t = s;
-                if (passes >= 1) t = pos1[t];
-                if (passes == 2) t = pos2[t];
-                skey[t] = key[k];
-                if (FAST) spay[t] = pay[k];
-                else srow[t] = static_cast<uint16_t>(s);
-            }
-        }
-        __syncthreads();
         // run starts (positions where the destination changes)
-        for (int s = threadIdx.x; s < m; s += PT) {
-            uint16_t p = pidS[s];
-            if (s == 0 || pidS[s - 1] != p) start[p] = static_cast<uint16_t>(s);
+        for (int t = threadIdx.x; t < m; t += PT) {
+            const uint32_t p = sorted[t] >> 12;
+            if (t == 0 || (sorted[t - 1] >> 12) != p) start[p] = static_cast<uint16_t>(t);
         }
         __syncthreads();
-        for (int s = threadIdx.x; s < m; s += PT) {
-            const uint16_t p = pidS[s];
-            const int64_t d = run[p] + (s - start[p]);
-            __stcs(reinterpret_cast<long long *>(A.out_keys) + d, skey[s]);
+        for (int t = threadIdx.x; t < m; t += PT) {
+            const uint32_t w = sorted[t];
+            const uint32_t p = w >> 12;
+            const int src = static_cast<int>(w & 0xfffu);
+            const int64_t d = run[p] + (t - start[p]);
+            __stcs(reinterpret_cast<long long *>(A.out_keys) + d, keys[src]);
             if (FAST) {
-                __stcs(static_cast<long long *>(A.out_pay[0]) + d, spay[s]);
+                __stcs(static_cast<long long *>(A.out_pay[0]) + d, pays[src]);
             } else {
-                const int64_t src = c + srow[s];
-                for (int j = 0; j < A.npay; j++) copy_elem(A.out_pay[j], A.pay[j], A.pay_type[j], d, src);
+                for (int j = 0; j < A.npay; j++) copy_elem(A.out_pay[j], A.pay[j], A.pay_type[j], d, r0 + src);
             }
         }
         __syncthreads();
-        for (int s = threadIdx.x; s < m; s += PT) {
-            const uint16_t p = pidS[s];
-            if (s == m - 1 || pidS[s + 1] != p) run[p] += s - start[p] + 1;
+        for (int t = threadIdx.x; t < m; t += PT) {
+            const uint32_t p = sorted[t] >> 12;
+            if (t == m - 1 || (sorted[t + 1] >> 12) != p) run[p] += t - start[p] + 1;
         }
         __syncthreads();
+    }
+    if (s_abort && threadIdx.x == 0) {
+        // let copies still in flight land before the block exits (bounded)
+        mbar_wait(&s_bar[0], 0, A.spin_limit);
+        mbar_wait(&s_bar[1], 0, A.spin_limit);
     }
 }
 
 size_t scatter_smem(int log2f, bool fast)
 {
     const size_t F = size_t(1) << log2f;
-    (void)fast;
-    return F * 8 + CHUNK * 8 + CHUNK * 8 + F * 2 + 4 * CHUNK * 2 + 256 * NW * 2;
+    return 2 * CHUNK * 8 * (fast ? 2 : 1) + F * 8 + 2 * CHUNK * 4 + 64 * CSTRIDE * 4 + F * 2;
 }
 
 }  // namespace
@@ -349,8 +397,12 @@ extern "C" qe_status qe_partition(qe_ctx *ctx, const int64_t *keys, const qe_col
     int64_t G = static_cast<int64_t>(ctx->num_sms) * per_sm;
     int64_t need = qe_ceil_div(nrows, CHUNK);
     if (G > need) G = need;
-    A.rows_per_block = qe_ceil_div(nrows, G);
+    // whole chunks per block, so every chunk but the last starts 32 KB-aligned
+    A.rows_per_block = qe_ceil_div(qe_ceil_div(nrows, G), CHUNK) * CHUNK;
     G = qe_ceil_div(nrows, A.rows_per_block);
+    A.tma = qe_aligned(keys, 16) && (!fast || qe_aligned(A.pay[0], 16));
+    A.spin_limit = ctx->spin_limit;
+    A.st = ctx->dstat;
 
     void *scratch = nullptr;
     const size_t hist_bytes = static_cast<size_t>(G) * F * sizeof(uint32_t);
@@ -364,10 +416,10 @@ extern "C" qe_status qe_partition(qe_ctx *ctx, const int64_t *keys, const qe_col
     A.hist = reinterpret_cast<uint32_t *>(sp + off_bytes + tot_bytes);
     A.base = out_offsets;
 
-    cudaError_t e = cudaSuccess;
-    {
+    cudaError_t e = cudaMemsetAsync(A.hist, 0, hist_bytes, s);
+    if (e == cudaSuccess) {
         ProfScope prof(ctx, "part_hist", s);
-        k_part_hist<<<static_cast<unsigned>(G), PT, F * sizeof(uint32_t), s>>>(A);
+        k_part_hist<<<static_cast<unsigned>(G * H_SPLIT), HT, F * sizeof(uint32_t), s>>>(A);
         QE_LAUNCHED(ctx);
     }
     if ((e = cudaGetLastError()) == cudaSuccess) {

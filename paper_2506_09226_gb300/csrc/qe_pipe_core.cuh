@@ -1,0 +1,380 @@
+// qe_pipe_core.cuh -- the per-row core of the fused pipeline, shared by the
+// single-pipeline kernel (qe_pipeline.cu) and the batched persistent kernel
+// (qe_batch.cu).
+//
+// A tile is ITEMS x 1024 consecutive fact rows.  The columns a pipeline reads
+// are copied tile by tile into shared memory with the Tensor Memory
+// Accelerator (cp.async.bulk, completion on an mbarrier); each thread of a
+// 1024-thread block then owns ITEMS rows of the tile, 1024 rows apart.  Tiles
+// that are not full, or columns that are not 16-byte aligned, are read
+// straight from global memory.
+#pragma once
+
+#include "qe_internal.cuh"
+
+#define PIPE_THREADS 1024
+#define PIPE_WARPS (PIPE_THREADS / 32)
+#define PIPE_MAX_STAGE 8
+
+enum { SRC_NONE = 0, SRC_X = 1, SRC_Y = 2, SRC_XY = 3 };
+
+// Device view of one pipeline.  Column slots index the staged columns.
+struct PipeSpec {
+    int64_t n;                          // fact rows
+    int32_t ncol;                       // staged columns
+    int32_t tma;                        // all staged columns 16-byte aligned
+    const void *col[QE_MAX_COLS];
+    int32_t type[QE_MAX_COLS];
+    uint32_t soff[QE_MAX_COLS];         // byte offset of the column in a stage
+    uint32_t stage_bytes;               // bytes of a full tile
+    int32_t npreds;
+    int32_t pslot[QE_MAX_PREDS], pop[QE_MAX_PREDS];
+    int64_t plo[QE_MAX_PREDS], phi[QE_MAX_PREDS];
+    int32_t has_join, fk_slot, hi_slot, lo_slot;   // lo_slot == QE_JOIN_PAYLOAD: join payload
+    int32_t x_slot, y_slot;
+    int32_t src[QE_MAX_AGGS];
+    AggOps ops;
+    HtView ht;
+    GTable g;                           // HBM hash table (spills, hash layouts)
+    DenseKey dk;                        // dense layout of the group key
+    unsigned long long *gdense;         // HBM dense table (TM_GLOBAL_DENSE), AoS
+    // star kernel: direct column pointers and 32-bit bounds, read from the
+    // parameter bank as instruction operands instead of held in registers
+    const int32_t *s_pred, *s_fk, *s_y;
+    const void *s_hi;
+    const long long *s_x;
+    int32_t p0_lo, p0_hi, p0_neg, s_h8;
+    int32_t s_hmin, s_lmin;
+    uint32_t s_hspan, s_lspan, s_ns;
+};
+
+// Where a block aggregates.
+enum { TM_SMEM_HASH = 0, TM_SMEM_DENSE = 1, TM_GLOBAL_DENSE = 2, TM_GLOBAL_HASH = 3 };
+
+struct TableCfg {
+    int mode;
+    int S;        // shared-memory hash slots (TM_SMEM_HASH)
+    int log2S;
+};
+
+// ------------------------------------------------------------ TMA / mbarrier
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for phase `parity` of `bar`: gives up (returns false) after
+// `limit` polls or two seconds, whichever comes first.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, int64_t limit)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (int64_t i = 0; i < limit; i++) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 255) == 255 && global_ns() - t0 > 2000000000ull) break;
+    }
+    return false;
+}
+
+__device__ __forceinline__ uint64_t l2_evict_first_policy()
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// One bulk copy global -> shared, completing on `bar`.  Addresses and size
+// must be multiples of 16 bytes.
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes, unsigned long long *bar,
+                                            uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Fill a stage with rows [row0, row0 + PIPE_TR) of every staged column, or,
+// for a partial tile or unaligned columns, just complete the barrier phase
+// (the consumers then read global memory).
+__device__ __forceinline__ void stage_issue(const PipeSpec &P, unsigned char *stage, unsigned long long *bar,
+                                            int64_t row0, uint64_t policy, int tr)
+{
+    if (P.tma && row0 + tr <= P.n) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(bar, P.stage_bytes);
+        for (int c = 0; c < P.ncol; c++) {
+            const uint32_t sz = static_cast<uint32_t>(P.type[c]);
+            tma_load_1d(stage + P.soff[c], static_cast<const unsigned char *>(P.col[c]) + row0 * sz,
+                        static_cast<uint32_t>(tr) * sz, bar, policy);
+        }
+    } else {
+        mbar_arrive(bar);
+    }
+}
+
+// ------------------------------------------------------------ row values
+__device__ __forceinline__ int64_t ld_stage(const unsigned char *stage, uint32_t off, int type, int r)
+{
+    const unsigned char *p = stage + off;
+    if (type == QE_I32) return static_cast<int64_t>(reinterpret_cast<const int32_t *>(p)[r]);
+    if (type == QE_I64) return reinterpret_cast<const long long *>(p)[r];
+    return static_cast<int64_t>(reinterpret_cast<const signed char *>(p)[r]);
+}
+
+// Column slot value of a row, from the stage (smem) or global memory.
+__device__ __forceinline__ int64_t ld_slot(const PipeSpec &P, const unsigned char *stage, bool from_stage, int slot,
+                                           int r, int64_t grow)
+{
+    if (from_stage) return ld_stage(stage, P.soff[slot], P.type[slot], r);
+    return dev_col_stream(P.col[slot], P.type[slot], grow);
+}
+
+struct RowVals {
+    int64_t key_a;   // foreign key (join) or low key half
+    int64_t lo;      // low key half from a fact column, with a join
+    int64_t hi;
+    int64_t x, y;
+    bool ok;
+};
+
+// Predicates and the columns a surviving row needs.
+__device__ __forceinline__ RowVals row_load(const PipeSpec &P, const unsigned char *stage, bool from_stage, int r,
+                                            int64_t grow, bool in_range)
+{
+    RowVals v;
+    bool ok = in_range;
+#pragma unroll
+    for (int p = 0; p < QE_MAX_PREDS; p++)
+        if (p < P.npreds && ok) ok = dev_cmp(ld_slot(P, stage, from_stage, P.pslot[p], r, grow), P.pop[p], P.plo[p], P.phi[p]);
+    v.ok = ok;
+    v.key_a = 0;
+    v.lo = 0;
+    v.hi = 0;
+    v.x = 0;
+    v.y = 0;
+    if (ok) {
+        v.key_a = ld_slot(P, stage, from_stage, P.has_join ? P.fk_slot : P.lo_slot, r, grow);
+        if (P.has_join && P.lo_slot >= 0) v.lo = ld_slot(P, stage, from_stage, P.lo_slot, r, grow);
+        if (P.hi_slot >= 0) v.hi = ld_slot(P, stage, from_stage, P.hi_slot, r, grow);
+        if (P.x_slot >= 0) v.x = ld_slot(P, stage, from_stage, P.x_slot, r, grow);
+        if (P.y_slot >= 0) v.y = ld_slot(P, stage, from_stage, P.y_slot, r, grow);
+    }
+    return v;
+}
+
+static __device__ __noinline__ bool ht_lookup_open_ni(const HtView h, int32_t key, int32_t *pay)
+{
+    int32_t p = 0;
+    bool hit = ht_lookup(h, key, p);
+    *pay = p;
+    return hit;
+}
+
+// Join probe.  Dense tables are looked up inline (one L2 read), open tables
+// out of line.
+__device__ __forceinline__ bool probe(const HtView &h, int32_t key, int32_t &pay)
+{
+    if (h.layout == QE_HT_DENSE) {
+        const uint32_t s = static_cast<uint32_t>(key) - static_cast<uint32_t>(h.key_min);
+        if (s >= h.range) return false;
+        pay = __ldg(h.payload + s);
+        if (!h.full && !((__ldg(h.bitmap + (s >> 5)) >> (s & 31)) & 1u)) return false;
+        return true;
+    }
+    return ht_lookup_open_ni(h, key, &pay);
+}
+
+// ------------------------------------------------------------ group table
+// Shared-memory slot hash: multiplicative (Fibonacci) hashing of the
+// 64-bit stored key, top log2S bits.
+__device__ __forceinline__ uint32_t st_hash(unsigned long long kx, int log2S)
+{
+    return static_cast<uint32_t>((kx * 0x9E3779B97F4A7C15ull) >> (64 - log2S));
+}
+
+static __device__ __noinline__ int st_find_slow(unsigned long long *keys, uint32_t mask, unsigned long long kx, uint32_t h)
+{
+    for (int p = 0; p < 64; p++) {
+        unsigned long long cur = reinterpret_cast<volatile unsigned long long *>(keys)[h];
+        if (cur == kx) return static_cast<int>(h);
+        if (cur == 0) {
+            unsigned long long old = atomicCAS(keys + h, 0ull, kx);
+            if (old == 0 || old == kx) return static_cast<int>(h);
+        }
+        h = (h + 1) & mask;
+    }
+    return -1;
+}
+
+static __device__ __noinline__ void spill_row_ni(const GTable g, const AggOps ops, unsigned long long kx, unsigned long long e0,
+                                          unsigned long long e1, unsigned long long e2, unsigned long long e3)
+{
+    unsigned long long e[QE_MAX_AGGS] = {e0, e1, e2, e3};
+    gt_fold_row(g, ops, kx, e);
+}
+
+__device__ __forceinline__ unsigned long long agg_value_enc(const PipeSpec &P, int a, const RowVals &v)
+{
+    const int src = P.src[a];
+    const int64_t val = src == SRC_X ? v.x
+                      : src == SRC_Y ? v.y
+                      : src == SRC_XY ? static_cast<int64_t>(static_cast<uint64_t>(v.x) * static_cast<uint64_t>(v.y))
+                                      : 0;
+    return agg_encode(P.ops.op[a], val);
+}
+
+// Update of one shared-memory aggregate cell: ADD kinds are reductions with
+// no return value; MAX kinds read the cell first (a stale read can only
+// cause a redundant atomic, never a lost update, since cells only grow).
+__device__ __forceinline__ void st_update(unsigned long long *cell, int op, unsigned long long e)
+{
+    if (op == QE_SUM || op == QE_COUNT) {
+        atomicAdd(cell, e);
+    } else if (*cell < e) {
+        atomicMax(cell, e);
+    }
+}
+
+// Update of one HBM aggregate cell (same rule as st_update).
+__device__ __forceinline__ void gd_update(unsigned long long *cell, int op, unsigned long long e)
+{
+    if (op == QE_SUM || op == QE_COUNT) {
+        atomicAdd(cell, e);
+    } else if (*cell < e) {
+        atomicMax(cell, e);
+    }
+}
+
+// Fold a surviving row (key parts hi / lo) into the block's table.
+__device__ __forceinline__ void fold_row(const PipeSpec &P, const TableCfg &T, unsigned long long *sm, int64_t hi,
+                                         int64_t lo, const RowVals &v)
+{
+    int64_t key = lo;
+    if (P.hi_slot >= 0) key = static_cast<int64_t>((static_cast<uint64_t>(hi) << 32) | static_cast<uint32_t>(lo));
+    const unsigned long long kx = static_cast<unsigned long long>(key) ^ GB_SIGN;
+    if (kx == 0) {
+        dev_report(P.g.st, QE_ERR_RESERVED_KEY, 0);
+        return;
+    }
+    unsigned long long e[QE_MAX_AGGS];
+#pragma unroll
+    for (int a = 0; a < QE_MAX_AGGS; a++) e[a] = a < P.ops.n ? agg_value_enc(P, a, v) : 0;
+    if (T.mode == TM_SMEM_DENSE || T.mode == TM_GLOBAL_DENSE) {
+        const int64_t idx = dense_index(P.dk, hi, lo);
+        if (idx >= 0) {
+            if (T.mode == TM_SMEM_DENSE) {
+                const uint64_t ns = P.dk.nslots;
+#pragma unroll
+                for (int a = 0; a < QE_MAX_AGGS; a++)
+                    if (a < P.ops.n) st_update(sm + a * ns + idx, P.ops.op[a], e[a]);
+                if (P.dk.hidden) atomicAdd(sm + P.ops.n * ns + idx, 1ull);
+            } else {
+                unsigned long long *cell = P.gdense + idx * P.dk.stride;
+#pragma unroll
+                for (int a = 0; a < QE_MAX_AGGS; a++)
+                    if (a < P.ops.n) gd_update(cell + a, P.ops.op[a], e[a]);
+                if (P.dk.hidden) atomicAdd(cell + P.ops.n, 1ull);
+            }
+            return;
+        }
+    } else if (T.mode == TM_SMEM_HASH) {
+        const uint32_t mask = static_cast<uint32_t>(T.S - 1);
+        const uint32_t h = st_hash(kx, T.log2S);
+        const int slot = sm[h] == kx ? static_cast<int>(h) : st_find_slow(sm, mask, kx, h);
+        if (slot >= 0) {
+#pragma unroll
+            for (int a = 0; a < QE_MAX_AGGS; a++)
+                if (a < P.ops.n) st_update(sm + (a + 1) * T.S + slot, P.ops.op[a], e[a]);
+            return;
+        }
+    }
+    spill_row_ni(P.g, P.ops, kx, e[0], e[1], e[2], e[3]);
+}
+
+// Join probe of a loaded row; false when the row does not join.  Sets the
+// key parts.
+__device__ __forceinline__ bool row_probe(const PipeSpec &P, const RowVals &v, int64_t &hi, int64_t &lo)
+{
+    if (!v.ok) return false;
+    hi = v.hi;
+    lo = v.key_a;
+    if (P.has_join) {
+        int32_t pay = 0;
+        if (!probe(P.ht, static_cast<int32_t>(v.key_a), pay)) return false;
+        lo = P.lo_slot == QE_JOIN_PAYLOAD ? static_cast<int64_t>(pay) : v.lo;
+    }
+    return true;
+}
+
+// Zero the block table.
+__device__ __forceinline__ void table_zero(const PipeSpec &P, const TableCfg &T, unsigned long long *sm)
+{
+    if (T.mode == TM_SMEM_HASH) st_zero(sm, T.S, P.ops.n);
+    if (T.mode == TM_SMEM_DENSE)
+        for (uint64_t i = threadIdx.x; i < P.dk.nslots * P.dk.stride; i += blockDim.x) sm[i] = 0;
+}
+
+// Merge the block table into the HBM tables (after a __syncthreads()).
+__device__ __forceinline__ void table_flush(const PipeSpec &P, const TableCfg &T, unsigned long long *sm)
+{
+    if (T.mode == TM_SMEM_HASH) st_flush(sm, T.S, P.ops, P.g);
+    if (T.mode != TM_SMEM_DENSE) return;
+    const uint64_t ns = P.dk.nslots;
+    for (uint64_t i = threadIdx.x; i < ns; i += blockDim.x) {
+        if (sm[P.dk.occ * ns + i] == 0) continue;
+        if (P.gdense) {
+            unsigned long long *cell = P.gdense + i * P.dk.stride;
+            for (int w = 0; w < P.dk.stride; w++) gd_update(cell + w, w < P.ops.n ? P.ops.op[w] : QE_COUNT, sm[w * ns + i]);
+        } else {
+            unsigned long long e[QE_MAX_AGGS];
+#pragma unroll
+            for (int a = 0; a < QE_MAX_AGGS; a++) e[a] = a < P.ops.n ? sm[a * ns + i] : 0;
+            const unsigned long long kx = static_cast<unsigned long long>(dense_key(P.dk, i)) ^ GB_SIGN;
+            gt_fold_row(P.g, P.ops, kx, e);
+        }
+    }
+}

@@ -1,150 +1,178 @@
 // qe_pipeline.cu -- the fused per-GPU operator pipeline (Sec. 2.4: each GPU
 // runs one program over its local columns): group-by(join(filter(fact), dim)).
 //
-// After the dimension table is built (qe_join.cu), one persistent kernel
-// makes a single pass over the fact columns.  For each tile of rows it
-//   1. reads the predicate columns (streaming, coalesced) and evaluates the
-//      conjunction;
-//   2. reads the foreign key and the group/aggregate columns of survivors;
-//   3. probes the join table (dense tables sit in L2);
-//   4. folds survivors into the block's shared-memory group table (or the HBM
-//      table when the groups do not fit), without any block barrier, so warps
-//      overlap these phases.
-// Blocks merge their shared-memory tables into the HBM table at the end and
-// the HBM table is compacted into the output.
+// After the dimension table is built (qe_join.cu), one persistent kernel,
+// one 1024-thread block per SM, makes a single pass over the fact columns.
+// Each thread owns ITEMS rows of a tile, 1024 rows apart, so every column
+// read is a coalesced warp access; per row it evaluates the predicates,
+// probes the join table (dense tables: one L2 read, the table staying
+// resident while the fact columns stream through with an evict-first hint)
+// and folds the row into the block's group table (additive aggregates as
+// reductions, MIN/MAX as max over an order-preserving code).  Blocks merge
+// their tables into the HBM tables at the end and the HBM tables are
+// compacted into the output.
+//
+// Group tables, by preference: a direct (perfect-hash) array when the key's
+// parts have known small ranges, in shared memory or else in HBM; a hash
+// table in shared memory; a hash table in HBM.  Keys outside a direct
+// array's range go to the HBM hash table.
+//
+// The star shape (one int32 predicate, a dense int32 join, the key (column,
+// join payload) and [SUM(x*y), COUNT, MIN(x), MAX(x)]) has its own kernel:
+// all columns of the next tile are loaded into registers while the current
+// tile is processed, which keeps about 100 KB of loads in flight per SM from
+// the register file.  (A variant that staged tiles in shared memory with
+// bulk TMA copies ran at half this speed: the stages shared the 227 KB with
+// the group table and a stage could only be refilled once every warp had
+// read it.)
 //
 // Aggregate values are drawn from at most two fact columns X and Y (each
-// aggregate is X, Y or X*Y), which covers SUM(price*qty), MIN(price),
-// MAX(price), COUNT(*); other shapes are rejected with QE_ERR_INVALID_ARG.
-#include "qe_internal.cuh"
+// aggregate is X, Y or X*Y); other shapes are rejected with
+// QE_ERR_INVALID_ARG.
+#include <climits>
+#include <cstdlib>
+
+#include "qe_pipe_core.cuh"
 
 namespace {
 
-enum { SRC_NONE = 0, SRC_X = 1, SRC_Y = 2, SRC_XY = 3 };
+constexpr int PT = 1024;          // threads per block (one block per SM)
 
-struct PipeArgs {
-    int64_t n;
-    const void *col[QE_MAX_COLS];
-    int32_t type[QE_MAX_COLS];
-    int npreds;
-    int32_t pcol[QE_MAX_PREDS], pop[QE_MAX_PREDS];
-    int64_t plo[QE_MAX_PREDS], phi[QE_MAX_PREDS];
-    int fk_col;
-    HtView ht;
-    int key_hi_col, key_lo_col;
-    int x_col, y_col;
-    int32_t src[QE_MAX_AGGS];
-    AggOps ops;
-    GTable g;
-    int S;
-    int max_probe;
-};
-
-template <int ITEMS, int BLOCK>
-__device__ __forceinline__ void load_col(const void *p, int type, int64_t base, const bool (&ld)[ITEMS],
-                                         int64_t (&v)[ITEMS])
+// Generic pass: any column types, predicates and aggregate plan.
+template <int ITEMS>
+__global__ void __launch_bounds__(PT, 1) k_pipeline(PipeSpec P, TableCfg T)
 {
-    switch (type) {
-    case QE_I32:
-#pragma unroll
-        for (int k = 0; k < ITEMS; k++)
-            v[k] = ld[k] ? static_cast<int64_t>(__ldcs(static_cast<const int32_t *>(p) + base + k * BLOCK)) : 0;
-        break;
-    case QE_I64:
-#pragma unroll
-        for (int k = 0; k < ITEMS; k++) v[k] = ld[k] ? __ldcs(static_cast<const long long *>(p) + base + k * BLOCK) : 0;
-        break;
-    default:
-#pragma unroll
-        for (int k = 0; k < ITEMS; k++)
-            v[k] = ld[k] ? static_cast<int64_t>(__ldcs(static_cast<const signed char *>(p) + base + k * BLOCK)) : 0;
-        break;
-    }
-}
-
-template <int BLOCK, int ITEMS>
-__global__ void __launch_bounds__(BLOCK) k_pipeline(PipeArgs A)
-{
-    extern __shared__ unsigned long long sm[];
-    if (A.S) st_zero(sm, A.S, A.ops.n);
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned long long *sm = reinterpret_cast<unsigned long long *>(smem);
+    table_zero(P, T, sm);
     __syncthreads();
-    const int64_t tile_rows = static_cast<int64_t>(BLOCK) * ITEMS;
-    const int64_t ntiles = (A.n + tile_rows - 1) / tile_rows;
+    constexpr int TR = PT * ITEMS;
+    const int64_t ntiles = (P.n + TR - 1) / TR;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t base = tile * tile_rows + threadIdx.x;
+        RowVals v[ITEMS];
+#pragma unroll
+        for (int k = 0; k < ITEMS; k++) {
+            const int64_t r = tile * TR + k * PT + threadIdx.x;
+            v[k] = row_load(P, nullptr, false, 0, r, r < P.n);
+        }
+        int64_t hi[ITEMS], lo[ITEMS];
         bool ok[ITEMS];
 #pragma unroll
-        for (int k = 0; k < ITEMS; k++) ok[k] = base + k * BLOCK < A.n;
-        // 1. selection
-        for (int p = 0; p < A.npreds; p++) {
-            int64_t v[ITEMS];
-            load_col<ITEMS, BLOCK>(A.col[A.pcol[p]], A.type[A.pcol[p]], base, ok, v);
+        for (int k = 0; k < ITEMS; k++) ok[k] = row_probe(P, v[k], hi[k], lo[k]);
 #pragma unroll
-            for (int k = 0; k < ITEMS; k++) ok[k] = ok[k] && dev_cmp(v[k], A.pop[p], A.plo[p], A.phi[p]);
-        }
-        // 2. columns of survivors
-        int64_t lo[ITEMS], hi[ITEMS], x[ITEMS], y[ITEMS];
-        if (A.fk_col >= 0) load_col<ITEMS, BLOCK>(A.col[A.fk_col], QE_I32, base, ok, lo);
-        else load_col<ITEMS, BLOCK>(A.col[A.key_lo_col], A.type[A.key_lo_col], base, ok, lo);
-        if (A.key_hi_col >= 0) load_col<ITEMS, BLOCK>(A.col[A.key_hi_col], A.type[A.key_hi_col], base, ok, hi);
-        if (A.x_col >= 0) load_col<ITEMS, BLOCK>(A.col[A.x_col], A.type[A.x_col], base, ok, x);
-        if (A.y_col >= 0) load_col<ITEMS, BLOCK>(A.col[A.y_col], A.type[A.y_col], base, ok, y);
-        // 3. join probe: the low key half becomes the dimension payload
-        if (A.fk_col >= 0) {
+        for (int k = 0; k < ITEMS; k++)
+            if (ok[k]) fold_row(P, T, sm, hi[k], lo[k], v[k]);
+    }
+    __syncthreads();
+    table_flush(P, T, sm);
+}
+
+// Star shape (see the file comment).  GLOBAL: the direct array lives in HBM
+// (AoS, 4 words per slot) instead of shared memory (SoA).
+template <bool GLOBAL, int ITEMS>
+__global__ void __launch_bounds__(PT, 1) k_pipeline_star(PipeSpec P, TableCfg T)
+{
+    constexpr int TR = PT * ITEMS;
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned long long *sm = reinterpret_cast<unsigned long long *>(smem);
+    if (!GLOBAL) table_zero(P, T, sm);
+    __syncthreads();
+    const int64_t ntiles = (P.n + TR - 1) / TR;
+
+    int d[ITEMS], f[ITEMS], h[ITEMS], q[ITEMS];
+    long long x[ITEMS];
+    unsigned inmask = 0;
+    auto load = [&](int64_t tile) {
+        inmask = 0;
 #pragma unroll
-            for (int k = 0; k < ITEMS; k++) {
-                int32_t pay = 0;
-                if (ok[k]) ok[k] = ht_lookup(A.ht, static_cast<int32_t>(lo[k]), pay);
-                if (A.key_lo_col == QE_JOIN_PAYLOAD) lo[k] = pay;
-            }
-            if (A.key_lo_col != QE_JOIN_PAYLOAD)
-                load_col<ITEMS, BLOCK>(A.col[A.key_lo_col], A.type[A.key_lo_col], base, ok, lo);
+        for (int k = 0; k < ITEMS; k++) {
+            const int64_t r = tile * TR + k * PT + threadIdx.x;
+            const bool in = tile < ntiles && r < P.n;
+            inmask |= in ? (1u << k) : 0u;
+            d[k] = in ? __ldcs(P.s_pred + r) : 0;
+            f[k] = in ? __ldcs(P.s_fk + r) : 0;
+            h[k] = in ? (P.s_h8 ? static_cast<int>(__ldcs(static_cast<const signed char *>(P.s_hi) + r))
+                                : __ldcs(static_cast<const int32_t *>(P.s_hi) + r))
+                      : 0;
+            x[k] = in ? __ldcs(P.s_x + r) : 0;
+            q[k] = in ? __ldcs(P.s_y + r) : 0;
         }
-        // 4. aggregate
+    };
+    int64_t tile = blockIdx.x;
+    load(tile);
+    for (; tile < ntiles; tile += gridDim.x) {
+        int cd[ITEMS], cf[ITEMS], ch[ITEMS], cq[ITEMS];
+        long long cx[ITEMS];
+        const unsigned cin = inmask;
+#pragma unroll
+        for (int k = 0; k < ITEMS; k++) {
+            cd[k] = d[k];
+            cf[k] = f[k];
+            ch[k] = h[k];
+            cq[k] = q[k];
+            cx[k] = x[k];
+        }
+        load(tile + gridDim.x);   // next tile's loads overlap this tile's work
+        bool ok[ITEMS];
+        int32_t pay[ITEMS];
+#pragma unroll
+        for (int k = 0; k < ITEMS; k++) {
+            const uint32_t ks = static_cast<uint32_t>(cf[k]) - static_cast<uint32_t>(P.ht.key_min);
+            const bool pass = (cd[k] >= P.p0_lo && cd[k] <= P.p0_hi) != static_cast<bool>(P.p0_neg);
+            const bool hit = ((cin >> k) & 1u) && pass && ks < P.ht.range;
+            pay[k] = hit ? __ldg(P.ht.payload + ks) : 0;
+            ok[k] = hit && (P.ht.full || ((__ldg(P.ht.bitmap + (ks >> 5)) >> (ks & 31)) & 1u));
+        }
 #pragma unroll
         for (int k = 0; k < ITEMS; k++) {
             if (!ok[k]) continue;
-            int64_t key = lo[k];
-            if (A.key_hi_col >= 0)
-                key = static_cast<int64_t>((static_cast<uint64_t>(hi[k]) << 32) | static_cast<uint32_t>(lo[k]));
-            const unsigned long long kx = static_cast<unsigned long long>(key) ^ GB_SIGN;
-            if (kx == 0) {
-                dev_report(A.g.st, QE_ERR_RESERVED_KEY, 0);
-                continue;
+            const uint32_t hh = static_cast<uint32_t>(ch[k]) - static_cast<uint32_t>(P.s_hmin);
+            const uint32_t ll = static_cast<uint32_t>(pay[k]) - static_cast<uint32_t>(P.s_lmin);
+            const unsigned long long v = static_cast<unsigned long long>(cx[k]) * static_cast<unsigned long long>(cq[k]);
+            const unsigned long long emin = ~(static_cast<unsigned long long>(cx[k]) ^ GB_SIGN);
+            const unsigned long long emax = static_cast<unsigned long long>(cx[k]) ^ GB_SIGN;
+            if (hh < P.s_hspan && ll < P.s_lspan) {
+                const uint32_t idx = hh * P.s_lspan + ll;
+                if (GLOBAL) {
+                    unsigned long long *cell = P.gdense + static_cast<uint64_t>(idx) * 4;
+                    atomicAdd(cell, v);
+                    atomicAdd(cell + 1, 1ull);
+                    if (cell[2] < emin) atomicMax(cell + 2, emin);
+                    if (cell[3] < emax) atomicMax(cell + 3, emax);
+                } else {
+                    atomicAdd(sm + idx, v);
+                    atomicAdd(sm + P.s_ns + idx, 1ull);
+                    if (sm[2 * P.s_ns + idx] < emin) atomicMax(sm + 2 * P.s_ns + idx, emin);
+                    if (sm[3 * P.s_ns + idx] < emax) atomicMax(sm + 3 * P.s_ns + idx, emax);
+                }
+            } else {
+                const int64_t key = static_cast<int64_t>((static_cast<uint64_t>(static_cast<int64_t>(ch[k])) << 32) |
+                                                         static_cast<uint32_t>(pay[k]));
+                const unsigned long long kx = static_cast<unsigned long long>(key) ^ GB_SIGN;
+                if (kx == 0) {
+                    dev_report(P.g.st, QE_ERR_RESERVED_KEY, 0);
+                } else {
+                    const unsigned long long e[QE_MAX_AGGS] = {v, 1ull, emin, emax};
+                    gt_fold_row(P.g, P.ops, kx, e);
+                }
             }
-            unsigned long long e[QE_MAX_AGGS];
-            _Pragma("unroll") for (int a = 0; a < QE_MAX_AGGS; a++) if (a < A.ops.n) {
-                const int src = A.src[a];
-                int64_t v = src == SRC_X ? x[k]
-                          : src == SRC_Y ? y[k]
-                          : src == SRC_XY ? static_cast<int64_t>(static_cast<uint64_t>(x[k]) * static_cast<uint64_t>(y[k]))
-                                          : 0;
-                e[a] = agg_encode(A.ops.op[a], v);
-            }
-            st_fold_row(sm, A.S, A.ops, A.g, kx, e, A.max_probe);
         }
     }
-    if (A.S) {
-        __syncthreads();
-        st_flush(sm, A.S, A.ops, A.g);
-    }
+    __syncthreads();
+    if (!GLOBAL) table_flush(P, T, sm);
 }
 
-template <int BLOCK, int ITEMS>
-qe_status launch_pipeline(qe_ctx *ctx, const PipeArgs &A, size_t smem, cudaStream_t s)
+template <class K>
+qe_status launch(qe_ctx *ctx, K kern, const PipeSpec &P, const TableCfg &T, size_t smem, int64_t rows_per_tile,
+                 cudaStream_t s)
 {
-    auto kern = k_pipeline<BLOCK, ITEMS>;
     QE_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-    int per_sm = 0;
-    QE_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, smem));
-    if (per_sm < 1) per_sm = 1;
-    int64_t grid = static_cast<int64_t>(ctx->num_sms) * per_sm;
-    int64_t need = qe_ceil_div(A.n, static_cast<int64_t>(BLOCK) * ITEMS);
-    if (grid > need) grid = need;
-    if (grid < 1) grid = 1;
+    const int64_t ntiles = qe_ceil_div(P.n, rows_per_tile);
+    int64_t grid = ctx->num_sms;
+    if (grid > ntiles) grid = ntiles;
     {
         ProfScope prof(ctx, "pipeline", s);
-        kern<<<static_cast<unsigned>(grid), BLOCK, smem, s>>>(A);
+        kern<<<static_cast<unsigned>(grid), PT, smem, s>>>(P, T);
         QE_LAUNCHED(ctx);
     }
     QE_CHECK_LAUNCH(ctx);
@@ -153,111 +181,237 @@ qe_status launch_pipeline(qe_ctx *ctx, const PipeArgs &A, size_t smem, cudaStrea
 
 }  // namespace
 
-// Validate a pipeline description and translate it to kernel arguments
-// (everything but the join table and the group table).
-qe_status pipeline_prepare(qe_ctx *ctx, const qe_pipeline_desc *d, PipeArgs &A);
-
-qe_status pipeline_prepare(qe_ctx *ctx, const qe_pipeline_desc *d, PipeArgs &A)
+// Validate a pipeline description and build its device view (everything but
+// the join table and the group table).
+qe_status pipeline_prepare(qe_ctx *ctx, const qe_pipeline_desc *d, PipeSpec &P)
 {
     if (!d) return qe_fail(ctx, QE_ERR_INVALID_ARG, "pipeline: null desc");
     if (d->n_fact < 0 || d->n_fact >= (int64_t(1) << 31) || d->n_fact_cols < 0 || d->n_fact_cols > QE_MAX_COLS ||
         d->n_preds < 0 || d->n_preds > QE_MAX_PREDS || d->n_aggs < 0 || d->n_aggs > QE_MAX_AGGS)
         return qe_fail(ctx, QE_ERR_INVALID_ARG, "pipeline: bad sizes");
-    A = PipeArgs{};
-    A.n = d->n_fact;
+    P = PipeSpec{};
+    P.n = d->n_fact;
     const int nc = d->n_fact_cols;
     for (int c = 0; c < nc; c++) {
         const qe_col &col = d->fact[c];
-        if (!qe_valid_type(col.type) || col.gather || (A.n > 0 && !col.data) || !qe_aligned(col.data, col.type))
+        if (!qe_valid_type(col.type) || col.gather || (P.n > 0 && !col.data) || !qe_aligned(col.data, col.type))
             return qe_fail(ctx, QE_ERR_INVALID_ARG, "pipeline: bad fact column " + std::to_string(c));
-        A.col[c] = col.data;
-        A.type[c] = col.type;
     }
     auto colok = [&](int c) { return c >= 0 && c < nc; };
-    A.npreds = d->n_preds;
+    int slot_of[QE_MAX_COLS];
+    for (int c = 0; c < QE_MAX_COLS; c++) slot_of[c] = -1;
+    auto use = [&](int c) -> int {
+        if (slot_of[c] < 0) {
+            slot_of[c] = P.ncol;
+            P.col[P.ncol] = d->fact[c].data;
+            P.type[P.ncol] = d->fact[c].type;
+            P.ncol++;
+        }
+        return slot_of[c];
+    };
+    P.npreds = d->n_preds;
     for (int p = 0; p < d->n_preds; p++) {
         const qe_pred &pr = d->preds[p];
         if (!colok(pr.col) || pr.op < QE_LT || pr.op > QE_BETWEEN)
             return qe_fail(ctx, QE_ERR_INVALID_ARG, "pipeline: bad predicate");
-        A.pcol[p] = pr.col;
-        A.pop[p] = pr.op;
-        A.plo[p] = pr.lo;
-        A.phi[p] = pr.hi;
+        P.pslot[p] = use(pr.col);
+        P.pop[p] = pr.op;
+        P.plo[p] = pr.lo;
+        P.phi[p] = pr.hi;
     }
-    A.fk_col = d->fk_col;
-    if (A.fk_col >= 0 && (!colok(A.fk_col) || A.type[A.fk_col] != QE_I32))
-        return qe_fail(ctx, QE_ERR_INVALID_ARG, "pipeline: join column must be int32");
-    if (A.fk_col < 0 && A.fk_col != -1) return qe_fail(ctx, QE_ERR_INVALID_ARG, "pipeline: bad join column");
-    A.key_hi_col = d->key_hi_col;
-    A.key_lo_col = d->key_lo_col;
-    if (A.key_hi_col != -1 && !colok(A.key_hi_col)) return qe_fail(ctx, QE_ERR_INVALID_ARG, "pipeline: bad key_hi");
-    if (A.key_lo_col == QE_JOIN_PAYLOAD) {
-        if (A.fk_col < 0) return qe_fail(ctx, QE_ERR_INVALID_ARG, "pipeline: join payload key without a join");
-    } else if (!colok(A.key_lo_col)) {
+    if (d->fk_col >= 0) {
+        if (!colok(d->fk_col) || d->fact[d->fk_col].type != QE_I32)
+            return qe_fail(ctx, QE_ERR_INVALID_ARG, "pipeline: join column must be int32");
+        P.has_join = 1;
+        P.fk_slot = use(d->fk_col);
+    } else if (d->fk_col != -1) {
+        return qe_fail(ctx, QE_ERR_INVALID_ARG, "pipeline: bad join column");
+    }
+    P.hi_slot = -1;
+    if (d->key_hi_col != -1) {
+        if (!colok(d->key_hi_col)) return qe_fail(ctx, QE_ERR_INVALID_ARG, "pipeline: bad key_hi");
+        P.hi_slot = use(d->key_hi_col);
+    }
+    if (d->key_lo_col == QE_JOIN_PAYLOAD) {
+        if (!P.has_join) return qe_fail(ctx, QE_ERR_INVALID_ARG, "pipeline: join payload key without a join");
+        P.lo_slot = QE_JOIN_PAYLOAD;
+    } else if (colok(d->key_lo_col)) {
+        P.lo_slot = use(d->key_lo_col);
+    } else {
         return qe_fail(ctx, QE_ERR_INVALID_ARG, "pipeline: bad key_lo");
     }
-    A.x_col = A.y_col = -1;
-    A.ops.n = d->n_aggs;
+    int xc = -1, yc = -1;
+    P.ops.n = d->n_aggs;
     for (int a = 0; a < d->n_aggs; a++) {
         const qe_agg_spec &g = d->aggs[a];
         if (g.op < QE_SUM || g.op > QE_MAX) return qe_fail(ctx, QE_ERR_INVALID_ARG, "pipeline: bad aggregate");
-        A.ops.op[a] = g.op;
-        A.src[a] = SRC_NONE;
+        P.ops.op[a] = g.op;
+        P.src[a] = SRC_NONE;
         if (g.op == QE_COUNT) continue;
         if (!colok(g.a) || (g.b != -1 && !colok(g.b)))
             return qe_fail(ctx, QE_ERR_INVALID_ARG, "pipeline: bad aggregate column");
         auto place = [&](int c) -> int {
-            if (A.x_col == c) return SRC_X;
-            if (A.y_col == c) return SRC_Y;
-            if (A.x_col < 0) { A.x_col = c; return SRC_X; }
-            if (A.y_col < 0) { A.y_col = c; return SRC_Y; }
+            if (xc == c) return SRC_X;
+            if (yc == c) return SRC_Y;
+            if (xc < 0) { xc = c; return SRC_X; }
+            if (yc < 0) { yc = c; return SRC_Y; }
             return -1;
         };
         int sa = place(g.a);
         if (sa < 0) return qe_fail(ctx, QE_ERR_INVALID_ARG, "pipeline: aggregates use more than two columns");
         if (g.b == -1) {
-            A.src[a] = sa;
+            P.src[a] = sa;
         } else {
             int sb = place(g.b);
             if (sb < 0 || sb == sa) return qe_fail(ctx, QE_ERR_INVALID_ARG, "pipeline: unsupported aggregate shape");
-            A.src[a] = SRC_XY;
+            P.src[a] = SRC_XY;
+        }
+    }
+    P.x_slot = xc >= 0 ? use(xc) : -1;
+    P.y_slot = yc >= 0 ? use(yc) : -1;
+    P.tma = 0;
+    return QE_OK;
+}
+
+// Table placement of a pipeline.
+struct PipePlan {
+    TableCfg T{};
+    size_t table = 0;     // shared-memory table bytes
+    size_t gdense_bytes = 0;
+};
+
+// Choose where groups live: a direct array (shared memory, else HBM) when
+// the key parts have known small ranges, else a shared-memory hash table,
+// else the HBM hash table.
+qe_status pipeline_plan(qe_ctx *ctx, PipeSpec &P, const qe_pipeline_desc *d, const qe_hash_table *ht,
+                        int64_t capacity, PipePlan &plan)
+{
+    const size_t static_smem = 1024;
+    const size_t budget = ctx->smem_optin > static_smem ? ctx->smem_optin - static_smem : 0;
+    const bool has_hi = P.hi_slot >= 0;
+    P.dk = DenseKey{};
+    int64_t lo_min = 1, lo_max = 0;
+    if (d->have_key_range) {
+        lo_min = d->key_lo_min;
+        lo_max = d->key_lo_max;
+    }
+    if (lo_min > lo_max && P.lo_slot == QE_JOIN_PAYLOAD && ht && ht->have_pay) {
+        lo_min = ht->pay_min;
+        lo_max = ht->pay_max;
+    }
+    if (lo_min <= lo_max && (!has_hi || d->have_key_range))
+        P.dk = dense_plan(has_hi, d->key_hi_min, d->key_hi_max, lo_min, lo_max, P.ops, uint64_t(1) << 26);
+    if (P.dk.on) {
+        const size_t bytes = P.dk.nslots * P.dk.stride * 8;
+        if (bytes <= budget) {
+            plan.T.mode = TM_SMEM_DENSE;
+            plan.table = bytes;
+        } else {
+            plan.T.mode = TM_GLOBAL_DENSE;
+            plan.gdense_bytes = bytes;
+        }
+    } else {
+        const int64_t groups = d->expected_groups > 0 ? d->expected_groups : capacity;
+        const int S = st_slots_for(groups, P.ops.n, budget);
+        if (S) {
+            plan.T.mode = TM_SMEM_HASH;
+            plan.T.S = S;
+            while ((1 << plan.T.log2S) < S) plan.T.log2S++;
+            plan.table = static_cast<size_t>(S) * 8 * (1 + P.ops.n);
+        } else {
+            plan.T.mode = TM_GLOBAL_HASH;
         }
     }
     return QE_OK;
 }
 
-// Launch the fused pass with the join table and group table in place.
-qe_status pipeline_launch(qe_ctx *ctx, PipeArgs &A, const GroupTableHost &t, int64_t capacity,
-                          int64_t expected_groups, cudaStream_t s)
+// The first predicate as x in [lo, hi] (negated for NE), clamped to int32:
+// every comparison on an int32 column becomes two compares.
+static void star_predicate(PipeSpec &P)
 {
-    A.g.words = t.words;
-    A.g.mask = t.slots - 1;
-    A.g.stride = t.stride;
-    A.g.nkeys = t.words + t.slots * t.stride;
-    A.g.capacity = capacity;
-    A.g.st = ctx->dstat;
-    A.max_probe = 32;
-    const size_t budget = ctx->smem_optin > 4096 ? ctx->smem_optin - 4096 : 0;
-    const int64_t groups = expected_groups > 0 ? expected_groups : capacity;
-    A.S = st_slots_for(groups, A.ops.n, budget);
-    if (A.n == 0) return QE_OK;
-    const size_t smem = static_cast<size_t>(A.S) * 8 * (1 + A.ops.n);
-    if (smem > 48 * 1024) return launch_pipeline<1024, 4>(ctx, A, smem, s);
-    return launch_pipeline<256, 8>(ctx, A, smem, s);
+    const int64_t c = P.plo[0];
+    int64_t a = INT64_MIN, b = INT64_MAX;
+    int neg = 0;
+    switch (P.pop[0]) {
+    case QE_LT: b = c == INT64_MIN ? INT64_MIN : c - 1; if (c == INT64_MIN) a = 1; break;
+    case QE_LE: b = c; break;
+    case QE_GT: a = c == INT64_MAX ? INT64_MAX : c + 1; if (c == INT64_MAX) b = -1; break;
+    case QE_GE: a = c; break;
+    case QE_EQ: a = b = c; break;
+    case QE_NE: a = b = c; neg = 1; break;
+    default: a = P.plo[0]; b = P.phi[0]; break;
+    }
+    // empty ranges become [1, 0]; clamp the rest to int32
+    if (a > b || a > INT32_MAX || b < INT32_MIN) {
+        a = 1;
+        b = 0;
+    }
+    P.p0_lo = static_cast<int32_t>(a < INT32_MIN ? INT32_MIN : a);
+    P.p0_hi = static_cast<int32_t>(b > INT32_MAX ? INT32_MAX : b);
+    P.p0_neg = neg;
+    P.s_pred = static_cast<const int32_t *>(P.col[P.pslot[0]]);
+    P.s_fk = static_cast<const int32_t *>(P.col[P.fk_slot]);
+    P.s_hi = P.col[P.hi_slot];
+    P.s_h8 = P.type[P.hi_slot] == QE_I8;
+    P.s_x = static_cast<const long long *>(P.col[P.x_slot]);
+    P.s_y = static_cast<const int32_t *>(P.col[P.y_slot]);
+    P.s_hmin = static_cast<int32_t>(P.dk.hi_min);
+    P.s_lmin = static_cast<int32_t>(P.dk.lo_min);
+    P.s_hspan = static_cast<uint32_t>(P.dk.hi_span);
+    P.s_lspan = static_cast<uint32_t>(P.dk.lo_span);
+    P.s_ns = static_cast<uint32_t>(P.dk.nslots);
+}
+
+// The star specialisation applies (see k_pipeline_star).
+static bool star_shape(const PipeSpec &P, const TableCfg &T)
+{
+    return (T.mode == TM_SMEM_DENSE || T.mode == TM_GLOBAL_DENSE) && P.npreds == 1 && P.type[P.pslot[0]] == QE_I32 &&
+           P.has_join && P.ht.layout == QE_HT_DENSE && P.lo_slot == QE_JOIN_PAYLOAD && P.hi_slot >= 0 &&
+           (P.type[P.hi_slot] == QE_I8 || P.type[P.hi_slot] == QE_I32) && P.ops.n == 4 && P.ops.op[0] == QE_SUM &&
+           P.src[0] == SRC_XY && P.ops.op[1] == QE_COUNT && P.ops.op[2] == QE_MIN && P.src[2] == SRC_X &&
+           P.ops.op[3] == QE_MAX && P.src[3] == SRC_X && P.type[P.x_slot] == QE_I64 && P.type[P.y_slot] == QE_I32 &&
+           P.dk.stride == 4 && P.dk.nslots < (1ull << 31) && P.dk.hi_min >= INT32_MIN &&
+           P.dk.hi_min + static_cast<int64_t>(P.dk.hi_span) <= INT32_MAX && P.dk.lo_min >= INT32_MIN &&
+           P.dk.lo_min + static_cast<int64_t>(P.dk.lo_span) <= INT32_MAX && getenv("QE_PIPE_GENERIC") == nullptr;
+}
+
+// Bind the HBM tables and launch the fused pass.
+qe_status pipeline_launch(qe_ctx *ctx, PipeSpec &P, const PipePlan &plan, const GroupTableHost &t, int64_t capacity,
+                          cudaStream_t s)
+{
+    P.g.words = t.words;
+    P.g.mask = t.slots - 1;
+    P.g.stride = t.stride;
+    P.g.nkeys = t.words + t.slots * t.stride;
+    P.g.capacity = capacity;
+    P.g.st = ctx->dstat;
+    if (P.n == 0) return QE_OK;
+    if (star_shape(P, plan.T)) {
+        star_predicate(P);
+        // rows per thread: 3 by default; a tuning override (QE_STAR_ITEMS=2) pins 2
+        const char *o = getenv("QE_STAR_ITEMS");
+        const bool two = o && atoi(o) == 2;
+        if (plan.T.mode == TM_GLOBAL_DENSE)
+            return two ? launch(ctx, k_pipeline_star<true, 2>, P, plan.T, 0, PT * 2, s)
+                       : launch(ctx, k_pipeline_star<true, 3>, P, plan.T, 0, PT * 3, s);
+        return two ? launch(ctx, k_pipeline_star<false, 2>, P, plan.T, plan.table, PT * 2, s)
+                   : launch(ctx, k_pipeline_star<false, 3>, P, plan.T, plan.table, PT * 3, s);
+    }
+    return launch(ctx, k_pipeline<2>, P, plan.T, plan.table, PT * 2, s);
 }
 
 extern "C" qe_status qe_pipeline(qe_ctx *ctx, const qe_pipeline_desc *desc, const qe_groups_out *out, void *stream)
 {
     if (!ctx) return QE_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    PipeArgs A;
-    qe_status st = pipeline_prepare(ctx, desc, A);
+    PipeSpec P;
+    qe_status st = pipeline_prepare(ctx, desc, P);
     if (st != QE_OK) return st;
     st = gt_check_out(ctx, out, desc->n_aggs);
     if (st != QE_OK) return st;
     cudaSetDevice(ctx->device);
     qe_hash_table *built = nullptr;
-    if (A.fk_col >= 0) {
+    if (P.has_join) {
         const qe_hash_table *ht = desc->ht;
         if (!ht) {
             if (desc->n_dim < 0 || (desc->n_dim > 0 && (!desc->dim_key || !desc->dim_payload)))
@@ -266,15 +420,30 @@ extern "C" qe_status qe_pipeline(qe_ctx *ctx, const qe_pipeline_desc *desc, cons
             if (st != QE_OK) return st;
             ht = built;
         }
-        A.ht = ht_view(ht);
+        P.ht = ht_view(ht);
+    }
+    PipePlan plan;
+    st = pipeline_plan(ctx, P, desc, P.has_join ? (desc->ht ? desc->ht : built) : nullptr, out->capacity, plan);
+    void *gd = nullptr;
+    if (st == QE_OK && plan.gdense_bytes) {
+        st = qe_alloc(ctx, &gd, plan.gdense_bytes, s);
+        if (st == QE_OK) {
+            cudaError_t e = cudaMemsetAsync(gd, 0, plan.gdense_bytes, s);
+            if (e != cudaSuccess) st = qe_cuda_fail(ctx, e, "pipeline: dense table");
+        }
+        P.gdense = static_cast<unsigned long long *>(gd);
     }
     GroupTableHost t;
-    st = gt_create(ctx, out->capacity, A.ops.n, t, s);
+    if (st == QE_OK) st = gt_create(ctx, out->capacity, P.ops.n, t, s);
     if (st == QE_OK) {
-        st = pipeline_launch(ctx, A, t, out->capacity, desc->expected_groups, s);
-        if (st == QE_OK) st = gt_finalize(ctx, t, A.ops, out, s);
+        st = pipeline_launch(ctx, P, plan, t, out->capacity, s);
+        if (st == QE_OK) {
+            st = P.gdense ? gt_finalize_dense(ctx, t, P.ops, P.dk, P.gdense, out, s)
+                          : gt_finalize(ctx, t, P.ops, out, s);
+        }
         qe_free(ctx, t.words, s);
     }
+    if (gd) qe_free(ctx, gd, s);
     if (built) qe_join_destroy(ctx, built, s);
     return st;
 }

@@ -67,7 +67,8 @@ class qe_build_opts(ctypes.Structure):
 class qe_ht_info(ctypes.Structure):
     _fields_ = [("layout", ctypes.c_int32), ("full", ctypes.c_int32), ("nkeys", ctypes.c_int64),
                 ("slots", ctypes.c_int64), ("bytes", ctypes.c_int64), ("key_min", ctypes.c_int32),
-                ("key_max", ctypes.c_int32)]
+                ("key_max", ctypes.c_int32), ("have_payload_range", ctypes.c_int32),
+                ("payload_min", ctypes.c_int32), ("payload_max", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class qe_agg(ctypes.Structure):
@@ -84,7 +85,9 @@ class qe_pipeline_desc(ctypes.Structure):
                 ("key_hi_col", ctypes.c_int32), ("key_lo_col", ctypes.c_int32), ("n_aggs", ctypes.c_int32),
                 ("aggs", qe_agg_spec * MAX_AGGS), ("dim_key", ctypes.c_void_p), ("dim_payload", ctypes.c_void_p),
                 ("n_dim", ctypes.c_int64), ("ht", ctypes.c_void_p), ("build", qe_build_opts),
-                ("expected_groups", ctypes.c_int64), ("est_selectivity", ctypes.c_double)]
+                ("expected_groups", ctypes.c_int64), ("est_selectivity", ctypes.c_double),
+                ("have_key_range", ctypes.c_int32), ("pad2", ctypes.c_int32), ("key_hi_min", ctypes.c_int64),
+                ("key_hi_max", ctypes.c_int64), ("key_lo_min", ctypes.c_int64), ("key_lo_max", ctypes.c_int64)]
 
 
 class qe_batch_opts(ctypes.Structure):
@@ -392,7 +395,7 @@ def qe_groupby(ctx: Context, key_lo, aggs, key_hi=None, rows=None, n=None, capac
 
 def pipeline_desc(fact, preds, fk_col=-1, dim_key=None, dim_payload=None, ht: HashTable | None = None,
                   key_hi_col=-1, key_lo_col=JOIN_PAYLOAD, aggs=(), dim_key_range=None, layout=HT_AUTO,
-                  expected_groups=0, est_selectivity=0.0) -> qe_pipeline_desc:
+                  expected_groups=0, est_selectivity=0.0, key_range=None) -> qe_pipeline_desc:
     """fact: list of tensors; preds: (col, op, lo[, hi]); aggs: (op, a, b) column indices."""
     d = qe_pipeline_desc()
     d.n_fact = fact[0].numel() if fact else 0
@@ -413,6 +416,12 @@ def pipeline_desc(fact, preds, fk_col=-1, dim_key=None, dim_payload=None, ht: Ha
     d.build = build_opts(layout, dim_key_range)
     d.expected_groups = expected_groups
     d.est_selectivity = est_selectivity
+    if key_range is not None:
+        # ((hi_min, hi_max), (lo_min, lo_max)) column statistics; lo None takes
+        # the join payload's range from the join table
+        (d.key_hi_min, d.key_hi_max) = key_range[0] if key_range[0] is not None else (0, 0)
+        (d.key_lo_min, d.key_lo_max) = key_range[1] if key_range[1] is not None else (1, 0)
+        d.have_key_range = 1
     # the descriptor holds raw device pointers: keep the tensors alive with it
     d._keep = (list(fact), dim_key, dim_payload, ht)
     return d

@@ -319,3 +319,56 @@ def test_pipeline_without_join_and_misses(ctx):
     ref = oracle_star(fact, dim)
     assert ref["njoin"] < ref["nsel"]
     assert_groups_equal(g, ref)
+
+
+# ---------------------------------------------------------------- dense group layouts
+def run_star_hint(ctx, fact, dim, key_range, capacity, date_lt=1278, expected=0):
+    f = [fact[c].cuda() for c in COLS]
+    d = qe.pipeline_desc(f, [(1, qe.LT, date_lt)], fk_col=0, dim_key=dim["key"].cuda(),
+                         dim_payload=dim["attr"].cuda(), key_hi_col=4, key_lo_col=qe.JOIN_PAYLOAD, aggs=STAR_AGGS,
+                         expected_groups=expected, key_range=key_range)
+    return qe.qe_pipeline(ctx, d, capacity)
+
+
+@pytest.mark.parametrize("generic", [False, True])
+@pytest.mark.parametrize("shape", ["0", "1", "2"])
+def test_pipeline_dense_smem_each_shape(ctx, shape, generic, monkeypatch):
+    """Every tile shape, through the star-specialised and the generic kernel."""
+    monkeypatch.setenv("QE_PIPE_SHAPE", shape)
+    if generic:
+        monkeypatch.setenv("QE_PIPE_GENERIC", "1")
+    dim = datagen.star_dim(20_000, 1000, seed=5)
+    fact = datagen.star_fact(500_001, 20_000, seed=5)
+    g = run_star_hint(ctx, fact, dim, ((0, 2), (0, 999)), 3100)
+    assert_groups_equal(g, oracle_star(fact, dim))
+
+
+@pytest.mark.parametrize("generic", [False, True])
+def test_pipeline_dense_hint_too_narrow_spills(ctx, generic, monkeypatch):
+    if generic:
+        monkeypatch.setenv("QE_PIPE_GENERIC", "1")
+    dim = datagen.star_dim(20_000, 100, seed=6)
+    fact = datagen.star_fact(300_000, 20_000, seed=6)
+    g = run_star_hint(ctx, fact, dim, ((1, 1), (10, 49)), 400)   # most keys fall outside
+    assert_groups_equal(g, oracle_star(fact, dim))
+
+
+def test_pipeline_dense_hbm_25k(ctx):
+    dim = datagen.star_dim(50_000, 8334, seed=7)
+    fact = datagen.star_fact(400_000, 50_000, seed=7)
+    g = run_star_hint(ctx, fact, dim, ((0, 2), (0, 8333)), 30_000)
+    assert_groups_equal(g, oracle_star(fact, dim))
+
+
+def test_pipeline_dense_payload_only(ctx):
+    """Group by the joined attribute alone; its range comes from the build."""
+    dim = datagen.star_dim(30_000, 77, seed=8)
+    fact = datagen.star_fact(250_000, 30_000, seed=8)
+    f = [fact[c].cuda() for c in COLS]
+    d = qe.pipeline_desc(f, [(1, qe.GE, 700)], fk_col=0, dim_key=dim["key"].cuda(), dim_payload=dim["attr"].cuda(),
+                         key_hi_col=-1, key_lo_col=qe.JOIN_PAYLOAD, aggs=[(qe.MAX, 3, -1), (qe.SUM, 2, -1)])
+    g = qe.qe_pipeline(ctx, d, 128)
+    q = O.Query(preds=[O.Pred(1, O.GE, 700)], fk_col=0, key_hi_col=-1, key_lo_col=O.JOIN_PAYLOAD,
+                aggs=[(O.MAX, 3, -1), (O.SUM, 2, -1)])
+    ref = O.pipeline([fact[c].numpy() for c in COLS], q, dim["key"].numpy(), dim["attr"].numpy())
+    assert_groups_equal(g, ref)
