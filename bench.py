@@ -324,8 +324,9 @@ def run_qe(args):
     # ---- batched and served forms
     forms = {}
     if "batch" in args.forms or "serve" in args.forms:
-        del okeys, opay
-        forms = run_forms(args, qe, ctx, dev, stream, fact, dim, peak)
+        del okeys, opay, dim, fact, key, pay, desc, groups, gout
+        torch.cuda.empty_cache()
+        forms = run_forms(args, qe, ctx, dev, stream, None, None, peak)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -460,16 +461,14 @@ def run_e2e(args, qe, ctx, fact, dim, key, pay, okeys, opay, offs, groups, gout,
 
 
 def run_forms(args, qe, ctx, dev, stream, fact, dim, peak):
+    from paper_2506_09226_gb300 import batch as B
     out = {}
-    try:
-        from paper_2506_09226_gb300 import batch as B
-    except Exception as e:  # batched form not available
-        return {"batch": {"error": repr(e)}}
     if "batch" in args.forms:
         out["batch"] = B.bench_batch(ctx, args.batch_count, dev, stream, peak, log=log)
     if "serve" in args.forms:
         from paper_2506_09226_gb300 import serve as S
-        out["serve"] = S.bench_serve(ctx, dev, stream, peak, duration_s=args.serve_seconds, log=log)
+        out["serve"] = S.bench_serve(ctx, dev, stream, peak, duration_s=args.serve_seconds, log=log,
+                                     scale=args.serve_scale)
     return out
 
 
@@ -486,6 +485,7 @@ def main():
     ap.add_argument("--forms", default="extras,batch,serve")
     ap.add_argument("--batch-count", type=int, default=10_000)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-scale", type=float, default=1.0)
     ap.add_argument("--ref-sample", type=int, default=4_000_000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

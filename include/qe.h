@@ -132,6 +132,13 @@ void qe_debug_fail_alloc(qe_ctx *ctx, int n);
  * kernels (0 = the default).  Tests shorten it to make a wait expire. */
 void qe_debug_set_spin_limit(qe_ctx *ctx, int64_t iterations);
 
+/* Tuning knobs of the context (the autotuner sets them):
+ *   "star_items"    rows per thread of the star-shape pipeline kernel: 2 or 3
+ *                   (0 = default 3);
+ *   "force_generic" nonzero: run every pipeline through the generic kernel.
+ * Unknown names return QE_ERR_INVALID_ARG. */
+qe_status qe_set_tuning(qe_ctx *ctx, const char *name, int64_t value);
+
 /* Number of kernels this context has launched so far (host-side counter). */
 int64_t qe_launch_count(const qe_ctx *ctx);
 
@@ -371,11 +378,12 @@ typedef struct {
 
 /* Plan a batch of n pipelines that share one persistent launch: every
  * pipeline's build, fused fact pass and group output run as work items of
- * one kernel, ordered per pipeline by device counters (bounded waits).  The
- * descs (dimension tables given by columns, not prebuilt tables, each with
- * build.have_range set) and outs are copied; the pointed-to device buffers
- * must stay valid until qe_batch_destroy.  Allocates all per-pipeline hash
- * and group tables. */
+ * one kernel, ordered per pipeline by device counters (bounded waits).  A
+ * pipeline joins either a prebuilt resident table (desc.ht) or dimension
+ * columns with build.have_range set (built inside the kernel, dense).  The
+ * descs and outs are copied; the pointed-to device buffers must stay valid
+ * until qe_batch_destroy.  Allocates all per-pipeline tables on `stream`
+ * without synchronizing the host. */
 qe_status qe_batch_create(qe_ctx *ctx, const qe_pipeline_desc *descs, const qe_groups_out *outs,
                           int n, const qe_batch_opts *opts, qe_batch **out, void *stream);
 
@@ -383,6 +391,7 @@ qe_status qe_batch_create(qe_ctx *ctx, const qe_pipeline_desc *descs, const qe_g
  * with use_graph).  May be called repeatedly. */
 qe_status qe_batch_launch(qe_ctx *ctx, qe_batch *batch, void *stream);
 
+/* Synchronizes `stream`, then frees the batch. */
 qe_status qe_batch_destroy(qe_ctx *ctx, qe_batch *batch, void *stream);
 
 /* Plan, launch once and destroy. */

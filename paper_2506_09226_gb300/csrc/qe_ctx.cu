@@ -101,6 +101,21 @@ extern "C" qe_status qe_destroy(qe_ctx *ctx)
     return QE_OK;
 }
 
+extern "C" qe_status qe_set_tuning(qe_ctx *ctx, const char *name, int64_t value)
+{
+    if (!ctx || !name) return QE_ERR_INVALID_ARG;
+    const std::string n(name);
+    if (n == "star_items") {
+        if (value != 0 && value != 2 && value != 3) return qe_fail(ctx, QE_ERR_INVALID_ARG, "star_items must be 0, 2 or 3");
+        ctx->tune_star_items = static_cast<int>(value);
+    } else if (n == "force_generic") {
+        ctx->tune_force_generic = value != 0;
+    } else {
+        return qe_fail(ctx, QE_ERR_INVALID_ARG, "unknown tuning knob " + n);
+    }
+    return QE_OK;
+}
+
 extern "C" int64_t qe_launch_count(const qe_ctx *ctx) { return ctx ? ctx->launches.load() : 0; }
 
 extern "C" qe_status qe_profile_enable(qe_ctx *ctx, int on)

@@ -40,6 +40,8 @@ struct qe_ctx {
     std::mutex mu;
     std::unordered_map<void *, size_t> live;
     std::atomic<int64_t> launches{0};
+    int tune_star_items = 0;        // 0: default
+    int tune_force_generic = 0;
     bool profiling = false;
     std::mutex prof_mu;
     std::map<std::string, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>> prof;
@@ -259,7 +261,18 @@ struct HtView {
     const int32_t *payload;  // dense payload [range]
     const uint32_t *bitmap;  // dense occupancy [ceil(range/32)]
     const unsigned long long *slots;  // open: key << 32 | payload
+    int32_t coherent;        // built by the same kernel: read through L2 only
+    int32_t pad;
 };
+
+// Read a join-table word: the read-only path for tables built before the
+// kernel, L2-only (coherent) loads for tables built earlier in the same
+// kernel by other blocks.
+template <typename T>
+__device__ __forceinline__ T ht_ld(const HtView &h, const T *p)
+{
+    return h.coherent ? __ldcg(p) : __ldg(p);
+}
 
 #define HT_EMPTY_KEY (static_cast<int32_t>(0x80000000u))
 #define HT_EMPTY_SLOT 0x8000000080000000ull
@@ -269,14 +282,14 @@ __device__ __forceinline__ bool ht_lookup(const HtView &h, int32_t key, int32_t 
     if (h.layout == QE_HT_DENSE) {
         uint32_t s = static_cast<uint32_t>(key) - static_cast<uint32_t>(h.key_min);
         if (s >= h.range) return false;
-        int32_t p = __ldg(h.payload + s);
-        if (!h.full && !((__ldg(h.bitmap + (s >> 5)) >> (s & 31)) & 1u)) return false;
+        int32_t p = ht_ld(h, h.payload + s);
+        if (!h.full && !((ht_ld(h, h.bitmap + (s >> 5)) >> (s & 31)) & 1u)) return false;
         pay = p;
         return true;
     }
     uint32_t i = dev_fmix32(static_cast<uint32_t>(key)) & h.mask;
     for (uint32_t probes = 0; probes <= h.mask; probes++) {
-        unsigned long long w = __ldg(h.slots + i);
+        unsigned long long w = ht_ld(h, h.slots + i);
         int32_t k = static_cast<int32_t>(w >> 32);
         if (k == key) {
             pay = static_cast<int32_t>(w & 0xffffffffu);

@@ -10,6 +10,9 @@
 // straight from global memory.
 #pragma once
 
+#include <climits>
+#include <cstdlib>
+
 #include "qe_internal.cuh"
 
 #define PIPE_THREADS 1024
@@ -221,8 +224,8 @@ __device__ __forceinline__ bool probe(const HtView &h, int32_t key, int32_t &pay
     if (h.layout == QE_HT_DENSE) {
         const uint32_t s = static_cast<uint32_t>(key) - static_cast<uint32_t>(h.key_min);
         if (s >= h.range) return false;
-        pay = __ldg(h.payload + s);
-        if (!h.full && !((__ldg(h.bitmap + (s >> 5)) >> (s & 31)) & 1u)) return false;
+        pay = ht_ld(h, h.payload + s);
+        if (!h.full && !((ht_ld(h, h.bitmap + (s >> 5)) >> (s & 31)) & 1u)) return false;
         return true;
     }
     return ht_lookup_open_ni(h, key, &pay);
@@ -378,3 +381,146 @@ __device__ __forceinline__ void table_flush(const PipeSpec &P, const TableCfg &T
         }
     }
 }
+
+// ------------------------------------------------------------ star shape
+// One int32 predicate column, an int32 foreign key joined through a dense
+// table, the group key (hi column, join payload) in a direct array and the
+// aggregates [SUM(x*y), COUNT, MIN(x), MAX(x)] with x int64, y int32.  Rows
+// [r0, r1) are processed by one block in tiles of THREADS x ITEMS rows; all
+// columns of the next tile are loaded into registers while the current tile
+// is processed, so the register file holds the loads in flight.
+template <bool GLOBAL, int ITEMS, int THREADS>
+__device__ __forceinline__ void star_range(const PipeSpec &P, unsigned long long *sm, int64_t r0, int64_t r1)
+{
+    constexpr int TR = THREADS * ITEMS;
+    int d[ITEMS], f[ITEMS], h[ITEMS], q[ITEMS];
+    long long x[ITEMS];
+    unsigned inmask = 0;
+    auto load = [&](int64_t t0) {
+        inmask = 0;
+#pragma unroll
+        for (int k = 0; k < ITEMS; k++) {
+            const int64_t r = t0 + k * THREADS + threadIdx.x;
+            const bool in = r < r1;
+            inmask |= in ? (1u << k) : 0u;
+            d[k] = in ? __ldcs(P.s_pred + r) : 0;
+            f[k] = in ? __ldcs(P.s_fk + r) : 0;
+            h[k] = in ? (P.s_h8 ? static_cast<int>(__ldcs(static_cast<const signed char *>(P.s_hi) + r))
+                                : __ldcs(static_cast<const int32_t *>(P.s_hi) + r))
+                      : 0;
+            x[k] = in ? __ldcs(P.s_x + r) : 0;
+            q[k] = in ? __ldcs(P.s_y + r) : 0;
+        }
+    };
+    if (r0 >= r1) return;
+    load(r0);
+    for (int64_t t0 = r0; t0 < r1; t0 += TR) {
+        int cd[ITEMS], cf[ITEMS], ch[ITEMS], cq[ITEMS];
+        long long cx[ITEMS];
+        const unsigned cin = inmask;
+#pragma unroll
+        for (int k = 0; k < ITEMS; k++) {
+            cd[k] = d[k];
+            cf[k] = f[k];
+            ch[k] = h[k];
+            cq[k] = q[k];
+            cx[k] = x[k];
+        }
+        load(t0 + TR);   // next tile's loads overlap this tile's work
+        bool ok[ITEMS];
+        int32_t pay[ITEMS];
+#pragma unroll
+        for (int k = 0; k < ITEMS; k++) {
+            const uint32_t ks = static_cast<uint32_t>(cf[k]) - static_cast<uint32_t>(P.ht.key_min);
+            const bool pass = (cd[k] >= P.p0_lo && cd[k] <= P.p0_hi) != static_cast<bool>(P.p0_neg);
+            const bool hit = ((cin >> k) & 1u) && pass && ks < P.ht.range;
+            pay[k] = hit ? ht_ld(P.ht, P.ht.payload + ks) : 0;
+            ok[k] = hit && (P.ht.full || ((ht_ld(P.ht, P.ht.bitmap + (ks >> 5)) >> (ks & 31)) & 1u));
+        }
+#pragma unroll
+        for (int k = 0; k < ITEMS; k++) {
+            if (!ok[k]) continue;
+            const uint32_t hh = static_cast<uint32_t>(ch[k]) - static_cast<uint32_t>(P.s_hmin);
+            const uint32_t ll = static_cast<uint32_t>(pay[k]) - static_cast<uint32_t>(P.s_lmin);
+            const unsigned long long v = static_cast<unsigned long long>(cx[k]) * static_cast<unsigned long long>(cq[k]);
+            const unsigned long long emin = ~(static_cast<unsigned long long>(cx[k]) ^ GB_SIGN);
+            const unsigned long long emax = static_cast<unsigned long long>(cx[k]) ^ GB_SIGN;
+            if (hh < P.s_hspan && ll < P.s_lspan) {
+                const uint32_t idx = hh * P.s_lspan + ll;
+                if (GLOBAL) {
+                    unsigned long long *cell = P.gdense + static_cast<uint64_t>(idx) * 4;
+                    atomicAdd(cell, v);
+                    atomicAdd(cell + 1, 1ull);
+                    if (cell[2] < emin) atomicMax(cell + 2, emin);
+                    if (cell[3] < emax) atomicMax(cell + 3, emax);
+                } else {
+                    atomicAdd(sm + idx, v);
+                    atomicAdd(sm + P.s_ns + idx, 1ull);
+                    if (sm[2 * P.s_ns + idx] < emin) atomicMax(sm + 2 * P.s_ns + idx, emin);
+                    if (sm[3 * P.s_ns + idx] < emax) atomicMax(sm + 3 * P.s_ns + idx, emax);
+                }
+            } else {
+                const int64_t key = static_cast<int64_t>((static_cast<uint64_t>(static_cast<int64_t>(ch[k])) << 32) |
+                                                         static_cast<uint32_t>(pay[k]));
+                const unsigned long long kx = static_cast<unsigned long long>(key) ^ GB_SIGN;
+                if (kx == 0) {
+                    dev_report(P.g.st, QE_ERR_RESERVED_KEY, 0);
+                } else {
+                    const unsigned long long e[QE_MAX_AGGS] = {v, 1ull, emin, emax};
+                    gt_fold_row(P.g, P.ops, kx, e);
+                }
+            }
+        }
+    }
+}
+
+// The first predicate as x in [lo, hi] (negated for NE), clamped to int32:
+// every comparison on an int32 column becomes two compares.
+static inline void star_predicate(PipeSpec &P)
+{
+    const int64_t c = P.plo[0];
+    int64_t a = INT64_MIN, b = INT64_MAX;
+    int neg = 0;
+    switch (P.pop[0]) {
+    case QE_LT: b = c == INT64_MIN ? INT64_MIN : c - 1; if (c == INT64_MIN) a = 1; break;
+    case QE_LE: b = c; break;
+    case QE_GT: a = c == INT64_MAX ? INT64_MAX : c + 1; if (c == INT64_MAX) b = -1; break;
+    case QE_GE: a = c; break;
+    case QE_EQ: a = b = c; break;
+    case QE_NE: a = b = c; neg = 1; break;
+    default: a = P.plo[0]; b = P.phi[0]; break;
+    }
+    // empty ranges become [1, 0]; clamp the rest to int32
+    if (a > b || a > INT32_MAX || b < INT32_MIN) {
+        a = 1;
+        b = 0;
+    }
+    P.p0_lo = static_cast<int32_t>(a < INT32_MIN ? INT32_MIN : a);
+    P.p0_hi = static_cast<int32_t>(b > INT32_MAX ? INT32_MAX : b);
+    P.p0_neg = neg;
+    P.s_pred = static_cast<const int32_t *>(P.col[P.pslot[0]]);
+    P.s_fk = static_cast<const int32_t *>(P.col[P.fk_slot]);
+    P.s_hi = P.col[P.hi_slot];
+    P.s_h8 = P.type[P.hi_slot] == QE_I8;
+    P.s_x = static_cast<const long long *>(P.col[P.x_slot]);
+    P.s_y = static_cast<const int32_t *>(P.col[P.y_slot]);
+    P.s_hmin = static_cast<int32_t>(P.dk.hi_min);
+    P.s_lmin = static_cast<int32_t>(P.dk.lo_min);
+    P.s_hspan = static_cast<uint32_t>(P.dk.hi_span);
+    P.s_lspan = static_cast<uint32_t>(P.dk.lo_span);
+    P.s_ns = static_cast<uint32_t>(P.dk.nslots);
+}
+
+// The star specialisation applies (see k_pipeline_star).
+static inline bool star_shape(const PipeSpec &P, const TableCfg &T)
+{
+    return (T.mode == TM_SMEM_DENSE || T.mode == TM_GLOBAL_DENSE) && P.npreds == 1 && P.type[P.pslot[0]] == QE_I32 &&
+           P.has_join && P.ht.layout == QE_HT_DENSE && P.lo_slot == QE_JOIN_PAYLOAD && P.hi_slot >= 0 &&
+           (P.type[P.hi_slot] == QE_I8 || P.type[P.hi_slot] == QE_I32) && P.ops.n == 4 && P.ops.op[0] == QE_SUM &&
+           P.src[0] == SRC_XY && P.ops.op[1] == QE_COUNT && P.ops.op[2] == QE_MIN && P.src[2] == SRC_X &&
+           P.ops.op[3] == QE_MAX && P.src[3] == SRC_X && P.type[P.x_slot] == QE_I64 && P.type[P.y_slot] == QE_I32 &&
+           P.dk.stride == 4 && P.dk.nslots < (1ull << 31) && P.dk.hi_min >= INT32_MIN &&
+           P.dk.hi_min + static_cast<int64_t>(P.dk.hi_span) <= INT32_MAX && P.dk.lo_min >= INT32_MIN &&
+           P.dk.lo_min + static_cast<int64_t>(P.dk.lo_span) <= INT32_MAX;
+}
+

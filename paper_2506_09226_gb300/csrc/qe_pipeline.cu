@@ -67,97 +67,19 @@ __global__ void __launch_bounds__(PT, 1) k_pipeline(PipeSpec P, TableCfg T)
     table_flush(P, T, sm);
 }
 
-// Star shape (see the file comment).  GLOBAL: the direct array lives in HBM
-// (AoS, 4 words per slot) instead of shared memory (SoA).
+// Star shape (see the file comment): each block takes a contiguous range of
+// rows.  GLOBAL: the direct array lives in HBM (AoS, 4 words per slot)
+// instead of shared memory (SoA).
 template <bool GLOBAL, int ITEMS>
 __global__ void __launch_bounds__(PT, 1) k_pipeline_star(PipeSpec P, TableCfg T)
 {
-    constexpr int TR = PT * ITEMS;
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long *sm = reinterpret_cast<unsigned long long *>(smem);
     if (!GLOBAL) table_zero(P, T, sm);
     __syncthreads();
-    const int64_t ntiles = (P.n + TR - 1) / TR;
-
-    int d[ITEMS], f[ITEMS], h[ITEMS], q[ITEMS];
-    long long x[ITEMS];
-    unsigned inmask = 0;
-    auto load = [&](int64_t tile) {
-        inmask = 0;
-#pragma unroll
-        for (int k = 0; k < ITEMS; k++) {
-            const int64_t r = tile * TR + k * PT + threadIdx.x;
-            const bool in = tile < ntiles && r < P.n;
-            inmask |= in ? (1u << k) : 0u;
-            d[k] = in ? __ldcs(P.s_pred + r) : 0;
-            f[k] = in ? __ldcs(P.s_fk + r) : 0;
-            h[k] = in ? (P.s_h8 ? static_cast<int>(__ldcs(static_cast<const signed char *>(P.s_hi) + r))
-                                : __ldcs(static_cast<const int32_t *>(P.s_hi) + r))
-                      : 0;
-            x[k] = in ? __ldcs(P.s_x + r) : 0;
-            q[k] = in ? __ldcs(P.s_y + r) : 0;
-        }
-    };
-    int64_t tile = blockIdx.x;
-    load(tile);
-    for (; tile < ntiles; tile += gridDim.x) {
-        int cd[ITEMS], cf[ITEMS], ch[ITEMS], cq[ITEMS];
-        long long cx[ITEMS];
-        const unsigned cin = inmask;
-#pragma unroll
-        for (int k = 0; k < ITEMS; k++) {
-            cd[k] = d[k];
-            cf[k] = f[k];
-            ch[k] = h[k];
-            cq[k] = q[k];
-            cx[k] = x[k];
-        }
-        load(tile + gridDim.x);   // next tile's loads overlap this tile's work
-        bool ok[ITEMS];
-        int32_t pay[ITEMS];
-#pragma unroll
-        for (int k = 0; k < ITEMS; k++) {
-            const uint32_t ks = static_cast<uint32_t>(cf[k]) - static_cast<uint32_t>(P.ht.key_min);
-            const bool pass = (cd[k] >= P.p0_lo && cd[k] <= P.p0_hi) != static_cast<bool>(P.p0_neg);
-            const bool hit = ((cin >> k) & 1u) && pass && ks < P.ht.range;
-            pay[k] = hit ? __ldg(P.ht.payload + ks) : 0;
-            ok[k] = hit && (P.ht.full || ((__ldg(P.ht.bitmap + (ks >> 5)) >> (ks & 31)) & 1u));
-        }
-#pragma unroll
-        for (int k = 0; k < ITEMS; k++) {
-            if (!ok[k]) continue;
-            const uint32_t hh = static_cast<uint32_t>(ch[k]) - static_cast<uint32_t>(P.s_hmin);
-            const uint32_t ll = static_cast<uint32_t>(pay[k]) - static_cast<uint32_t>(P.s_lmin);
-            const unsigned long long v = static_cast<unsigned long long>(cx[k]) * static_cast<unsigned long long>(cq[k]);
-            const unsigned long long emin = ~(static_cast<unsigned long long>(cx[k]) ^ GB_SIGN);
-            const unsigned long long emax = static_cast<unsigned long long>(cx[k]) ^ GB_SIGN;
-            if (hh < P.s_hspan && ll < P.s_lspan) {
-                const uint32_t idx = hh * P.s_lspan + ll;
-                if (GLOBAL) {
-                    unsigned long long *cell = P.gdense + static_cast<uint64_t>(idx) * 4;
-                    atomicAdd(cell, v);
-                    atomicAdd(cell + 1, 1ull);
-                    if (cell[2] < emin) atomicMax(cell + 2, emin);
-                    if (cell[3] < emax) atomicMax(cell + 3, emax);
-                } else {
-                    atomicAdd(sm + idx, v);
-                    atomicAdd(sm + P.s_ns + idx, 1ull);
-                    if (sm[2 * P.s_ns + idx] < emin) atomicMax(sm + 2 * P.s_ns + idx, emin);
-                    if (sm[3 * P.s_ns + idx] < emax) atomicMax(sm + 3 * P.s_ns + idx, emax);
-                }
-            } else {
-                const int64_t key = static_cast<int64_t>((static_cast<uint64_t>(static_cast<int64_t>(ch[k])) << 32) |
-                                                         static_cast<uint32_t>(pay[k]));
-                const unsigned long long kx = static_cast<unsigned long long>(key) ^ GB_SIGN;
-                if (kx == 0) {
-                    dev_report(P.g.st, QE_ERR_RESERVED_KEY, 0);
-                } else {
-                    const unsigned long long e[QE_MAX_AGGS] = {v, 1ull, emin, emax};
-                    gt_fold_row(P.g, P.ops, kx, e);
-                }
-            }
-        }
-    }
+    const int64_t per = (P.n + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = static_cast<int64_t>(blockIdx.x) * per;
+    star_range<GLOBAL, ITEMS, PT>(P, sm, r0, r0 + per < P.n ? r0 + per : P.n);
     __syncthreads();
     if (!GLOBAL) table_flush(P, T, sm);
 }
@@ -325,56 +247,6 @@ qe_status pipeline_plan(qe_ctx *ctx, PipeSpec &P, const qe_pipeline_desc *d, con
     return QE_OK;
 }
 
-// The first predicate as x in [lo, hi] (negated for NE), clamped to int32:
-// every comparison on an int32 column becomes two compares.
-static void star_predicate(PipeSpec &P)
-{
-    const int64_t c = P.plo[0];
-    int64_t a = INT64_MIN, b = INT64_MAX;
-    int neg = 0;
-    switch (P.pop[0]) {
-    case QE_LT: b = c == INT64_MIN ? INT64_MIN : c - 1; if (c == INT64_MIN) a = 1; break;
-    case QE_LE: b = c; break;
-    case QE_GT: a = c == INT64_MAX ? INT64_MAX : c + 1; if (c == INT64_MAX) b = -1; break;
-    case QE_GE: a = c; break;
-    case QE_EQ: a = b = c; break;
-    case QE_NE: a = b = c; neg = 1; break;
-    default: a = P.plo[0]; b = P.phi[0]; break;
-    }
-    // empty ranges become [1, 0]; clamp the rest to int32
-    if (a > b || a > INT32_MAX || b < INT32_MIN) {
-        a = 1;
-        b = 0;
-    }
-    P.p0_lo = static_cast<int32_t>(a < INT32_MIN ? INT32_MIN : a);
-    P.p0_hi = static_cast<int32_t>(b > INT32_MAX ? INT32_MAX : b);
-    P.p0_neg = neg;
-    P.s_pred = static_cast<const int32_t *>(P.col[P.pslot[0]]);
-    P.s_fk = static_cast<const int32_t *>(P.col[P.fk_slot]);
-    P.s_hi = P.col[P.hi_slot];
-    P.s_h8 = P.type[P.hi_slot] == QE_I8;
-    P.s_x = static_cast<const long long *>(P.col[P.x_slot]);
-    P.s_y = static_cast<const int32_t *>(P.col[P.y_slot]);
-    P.s_hmin = static_cast<int32_t>(P.dk.hi_min);
-    P.s_lmin = static_cast<int32_t>(P.dk.lo_min);
-    P.s_hspan = static_cast<uint32_t>(P.dk.hi_span);
-    P.s_lspan = static_cast<uint32_t>(P.dk.lo_span);
-    P.s_ns = static_cast<uint32_t>(P.dk.nslots);
-}
-
-// The star specialisation applies (see k_pipeline_star).
-static bool star_shape(const PipeSpec &P, const TableCfg &T)
-{
-    return (T.mode == TM_SMEM_DENSE || T.mode == TM_GLOBAL_DENSE) && P.npreds == 1 && P.type[P.pslot[0]] == QE_I32 &&
-           P.has_join && P.ht.layout == QE_HT_DENSE && P.lo_slot == QE_JOIN_PAYLOAD && P.hi_slot >= 0 &&
-           (P.type[P.hi_slot] == QE_I8 || P.type[P.hi_slot] == QE_I32) && P.ops.n == 4 && P.ops.op[0] == QE_SUM &&
-           P.src[0] == SRC_XY && P.ops.op[1] == QE_COUNT && P.ops.op[2] == QE_MIN && P.src[2] == SRC_X &&
-           P.ops.op[3] == QE_MAX && P.src[3] == SRC_X && P.type[P.x_slot] == QE_I64 && P.type[P.y_slot] == QE_I32 &&
-           P.dk.stride == 4 && P.dk.nslots < (1ull << 31) && P.dk.hi_min >= INT32_MIN &&
-           P.dk.hi_min + static_cast<int64_t>(P.dk.hi_span) <= INT32_MAX && P.dk.lo_min >= INT32_MIN &&
-           P.dk.lo_min + static_cast<int64_t>(P.dk.lo_span) <= INT32_MAX && getenv("QE_PIPE_GENERIC") == nullptr;
-}
-
 // Bind the HBM tables and launch the fused pass.
 qe_status pipeline_launch(qe_ctx *ctx, PipeSpec &P, const PipePlan &plan, const GroupTableHost &t, int64_t capacity,
                           cudaStream_t s)
@@ -386,11 +258,10 @@ qe_status pipeline_launch(qe_ctx *ctx, PipeSpec &P, const PipePlan &plan, const 
     P.g.capacity = capacity;
     P.g.st = ctx->dstat;
     if (P.n == 0) return QE_OK;
-    if (star_shape(P, plan.T)) {
+    if (!ctx->tune_force_generic && star_shape(P, plan.T)) {
         star_predicate(P);
-        // rows per thread: 3 by default; a tuning override (QE_STAR_ITEMS=2) pins 2
-        const char *o = getenv("QE_STAR_ITEMS");
-        const bool two = o && atoi(o) == 2;
+        // rows per thread: 3 by default, 2 when tuned so
+        const bool two = ctx->tune_star_items == 2;
         if (plan.T.mode == TM_GLOBAL_DENSE)
             return two ? launch(ctx, k_pipeline_star<true, 2>, P, plan.T, 0, PT * 2, s)
                        : launch(ctx, k_pipeline_star<true, 3>, P, plan.T, 0, PT * 3, s);

@@ -151,3 +151,33 @@ def poisson_trace(duration_s: float, rate: float, table_rows: list, *, seed: int
         sel = rng.uniform(0.01, 0.90)
         out.append(Arrival(t, shape, off, n, int(round(sel * DATE_SPAN))))
     return out
+
+
+def batch_star(sizes, n_attr: int, *, seed: int, device="cpu") -> dict:
+    """Many independent star pipelines stored back to back: pipeline i owns
+    fact rows [fact_off[i], fact_off[i] + n_i) and dimension rows
+    [dim_off[i], dim_off[i] + n_i // 10) (at least one).  Each dimension's
+    keys are a permutation of 0..nd_i-1 and each pipeline's foreign keys are
+    uniform over them; the other columns follow star_fact."""
+    sizes = [int(x) for x in sizes]
+    nds = [max(1, n // 10) for n in sizes]
+    fact_off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    dim_off = np.concatenate([[0], np.cumsum(nds)]).astype(np.int64)
+    total, dtotal = int(fact_off[-1]), int(dim_off[-1])
+    g = _gen(seed * 1000 + 5, device)
+    cols = {
+        "fk": torch.empty(total, dtype=torch.int32, device=device),
+        "date": _randint(0, DATE_SPAN - 1, total, torch.int32, g, device),
+        "price": _randint(PRICE_LO, PRICE_HI, total, torch.int64, g, device),
+        "qty": _randint(QTY_LO, QTY_HI, total, torch.int32, g, device),
+        "flag": _randint(0, N_FLAGS - 1, total, torch.int8, g, device),
+    }
+    key = torch.empty(dtotal, dtype=torch.int32, device=device)
+    for i, (n, nd) in enumerate(zip(sizes, nds)):
+        a, b = int(fact_off[i]), int(dim_off[i])
+        if n:
+            cols["fk"][a:a + n] = torch.randint(0, nd, (n,), generator=g, device=device, dtype=torch.int32)
+        key[b:b + nd] = torch.randperm(nd, generator=g, device=device, dtype=torch.int32)
+    attr = _randint(0, n_attr - 1, dtotal, torch.int32, g, device)
+    return {"fact": cols, "dim": {"key": key, "attr": attr}, "fact_off": fact_off, "dim_off": dim_off,
+            "sizes": np.asarray(sizes, np.int64), "dim_sizes": np.asarray(nds, np.int64)}

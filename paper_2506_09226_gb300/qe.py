@@ -105,6 +105,7 @@ _SIGS = {
     "qe_debug_fail_alloc": (None, [ctypes.c_void_p, ctypes.c_int]),
     "qe_debug_set_spin_limit": (None, [ctypes.c_void_p, ctypes.c_int64]),
     "qe_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
+    "qe_set_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int64]),
     "qe_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "qe_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(ctypes.c_double)]),
@@ -218,6 +219,9 @@ class Context:
 
     def bytes_in_use(self) -> int:
         return int(self.lib.qe_bytes_in_use(self.h))
+
+    def set_tuning(self, name: str, value: int):
+        self.check(self.lib.qe_set_tuning(self.h, name.encode(), int(value)))
 
     def launch_count(self) -> int:
         return int(self.lib.qe_launch_count(self.h))

@@ -330,27 +330,31 @@ def run_star_hint(ctx, fact, dim, key_range, capacity, date_lt=1278, expected=0)
     return qe.qe_pipeline(ctx, d, capacity)
 
 
-@pytest.mark.parametrize("generic", [False, True])
-@pytest.mark.parametrize("shape", ["0", "1", "2"])
-def test_pipeline_dense_smem_each_shape(ctx, shape, generic, monkeypatch):
-    """Every tile shape, through the star-specialised and the generic kernel."""
-    monkeypatch.setenv("QE_PIPE_SHAPE", shape)
-    if generic:
-        monkeypatch.setenv("QE_PIPE_GENERIC", "1")
-    dim = datagen.star_dim(20_000, 1000, seed=5)
-    fact = datagen.star_fact(500_001, 20_000, seed=5)
-    g = run_star_hint(ctx, fact, dim, ((0, 2), (0, 999)), 3100)
-    assert_groups_equal(g, oracle_star(fact, dim))
+@pytest.mark.parametrize("generic,items", [(False, 2), (False, 3), (True, 0)])
+def test_pipeline_dense_smem_each_shape(ctx, generic, items):
+    """The star-specialised kernel at 2 and 3 rows per thread, and the generic kernel."""
+    ctx.set_tuning("force_generic", int(generic))
+    ctx.set_tuning("star_items", items)
+    try:
+        dim = datagen.star_dim(20_000, 1000, seed=5)
+        fact = datagen.star_fact(500_001, 20_000, seed=5)
+        g = run_star_hint(ctx, fact, dim, ((0, 2), (0, 999)), 3100)
+        assert_groups_equal(g, oracle_star(fact, dim))
+    finally:
+        ctx.set_tuning("force_generic", 0)
+        ctx.set_tuning("star_items", 0)
 
 
 @pytest.mark.parametrize("generic", [False, True])
-def test_pipeline_dense_hint_too_narrow_spills(ctx, generic, monkeypatch):
-    if generic:
-        monkeypatch.setenv("QE_PIPE_GENERIC", "1")
-    dim = datagen.star_dim(20_000, 100, seed=6)
-    fact = datagen.star_fact(300_000, 20_000, seed=6)
-    g = run_star_hint(ctx, fact, dim, ((1, 1), (10, 49)), 400)   # most keys fall outside
-    assert_groups_equal(g, oracle_star(fact, dim))
+def test_pipeline_dense_hint_too_narrow_spills(ctx, generic):
+    ctx.set_tuning("force_generic", int(generic))
+    try:
+        dim = datagen.star_dim(20_000, 100, seed=6)
+        fact = datagen.star_fact(300_000, 20_000, seed=6)
+        g = run_star_hint(ctx, fact, dim, ((1, 1), (10, 49)), 400)   # most keys fall outside
+        assert_groups_equal(g, oracle_star(fact, dim))
+    finally:
+        ctx.set_tuning("force_generic", 0)
 
 
 def test_pipeline_dense_hbm_25k(ctx):
@@ -372,3 +376,67 @@ def test_pipeline_dense_payload_only(ctx):
                 aggs=[(O.MAX, 3, -1), (O.SUM, 2, -1)])
     ref = O.pipeline([fact[c].numpy() for c in COLS], q, dim["key"].numpy(), dim["attr"].numpy())
     assert_groups_equal(g, ref)
+
+
+# ---------------------------------------------------------------- batched form
+def _batch_inputs(sizes, seed, prebuilt=None, ctx=None, hint=True):
+    """Config-0-schema pipelines (attr in [0,25)); returns descs, outs, refs."""
+    descs, outs, groups, refs, keep = [], [], [], [], []
+    for i, n in enumerate(sizes):
+        nd = max(1, n // 10)
+        dim = datagen.star_dim(nd, 25, seed=seed * 1000 + i)
+        fact = datagen.star_fact(n, nd, seed=seed * 1000 + i)
+        f = [fact[c].cuda() for c in COLS]
+        dk, da = dim["key"].cuda(), dim["attr"].cuda()
+        ht = None
+        if prebuilt is not None and prebuilt(i):
+            ht = qe.qe_join_build(ctx, dk, da)
+        d = qe.pipeline_desc(f, [(1, qe.LT, 1278)], fk_col=0, dim_key=dk, dim_payload=da, ht=ht, key_hi_col=4,
+                             key_lo_col=qe.JOIN_PAYLOAD, aggs=STAR_AGGS, dim_key_range=(0, nd - 1),
+                             key_range=((0, 2), (0, 24)) if hint else None, expected_groups=75)
+        g, o = qe.alloc_groups(128, 4, torch.device("cuda"))
+        descs.append(d)
+        outs.append(o)
+        groups.append(g)
+        refs.append(oracle_star(fact, dim))
+        keep.append((f, dk, da, ht))
+    return descs, outs, groups, refs, keep
+
+
+@pytest.mark.parametrize("hint", [True, False])
+def test_batch_run_matches_oracle(ctx, hint):
+    sizes = [0, 1, 999, 2048, 5000, 70_001, 200_000, 33]
+    descs, outs, groups, refs, keep = _batch_inputs(sizes, seed=9, hint=hint)
+    qe.qe_batch_run(ctx, descs, outs, opts=qe.qe_batch_opts(0, 1 << 16, 0, 0))
+    for g, r in zip(groups, refs):
+        assert_groups_equal(g, r)
+
+
+def test_batch_graph_relaunch_prebuilt_and_solo_equivalence(ctx):
+    sizes = [4096, 123_457, 1, 60_000, 0, 300_000]
+    descs, outs, groups, refs, keep = _batch_inputs(sizes, seed=10, prebuilt=lambda i: i % 2 == 0, ctx=ctx)
+    b = qe.Batch(ctx, descs, outs, qe.qe_batch_opts(0, 1 << 15, 0, 1))
+    for _ in range(2):                      # the graph clears its tables each launch
+        for g in groups:
+            g.ngroups.fill_(-1)
+        b.launch()
+        ctx.sync_status()
+        for g, r in zip(groups, refs):
+            assert_groups_equal(g, r)
+    b.destroy()
+    # each pipeline alone gives the same result as in the batch
+    for d, g in zip(descs, groups):
+        solo = qe.qe_pipeline(ctx, d, 128)
+        a, bb = _sorted_groups(solo), _sorted_groups(g)
+        assert np.array_equal(a[0], bb[0]) and all(np.array_equal(x, y) for x, y in zip(a[1], bb[1]))
+    for k in keep:
+        if k[3] is not None:
+            k[3].destroy()
+
+
+def test_batch_hbm_tables_only(ctx):
+    sizes = [50_000, 7, 90_000]
+    descs, outs, groups, refs, keep = _batch_inputs(sizes, seed=11)
+    qe.qe_batch_run(ctx, descs, outs, opts=qe.qe_batch_opts(0, 1 << 16, -1, 0))
+    for g, r in zip(groups, refs):
+        assert_groups_equal(g, r)
