@@ -46,6 +46,8 @@ struct BatchPipe {
     int32_t star, pad;                 // star shape: the specialised row loop
 };
 
+static_assert(sizeof(PipeSpec) % 4 == 0, "the spec is copied to shared memory in 4-byte words");
+
 struct BatchArgs {
     const BatchPipe *pipes;
     const BatchItem *items;
@@ -130,12 +132,12 @@ __device__ void batch_finalize(const BatchPipe &B, qe_dev_status *st)
 // register allocation.
 __device__ __noinline__ void item_star_smem(const PipeSpec &P, unsigned long long *sm, int64_t r0, int64_t r1)
 {
-    star_range<false, 3, BT>(P, sm, r0, r1);
+    star_range<false, 3, BT>(P, sm, r0, r1, BT * 3);
 }
 
 __device__ __noinline__ void item_star_global(const PipeSpec &P, unsigned long long *sm, int64_t r0, int64_t r1)
 {
-    star_range<true, 3, BT>(P, sm, r0, r1);
+    star_range<true, 3, BT>(P, sm, r0, r1, BT * 3);
 }
 
 __device__ __noinline__ void item_generic(const PipeSpec &P, const TableCfg T, unsigned long long *sm, int64_t r0,
@@ -165,6 +167,10 @@ __global__ void __launch_bounds__(BT, 1) k_batch(BatchArgs A)
     unsigned long long *sm = reinterpret_cast<unsigned long long *>(smem);
     __shared__ long long s_item;
     __shared__ int s_flag;
+    // the current item's pipeline spec, read by the row loop as shared-memory
+    // broadcasts instead of global loads
+    __shared__ __align__(16) unsigned char s_spec_raw[sizeof(PipeSpec)];
+    const PipeSpec &SP = *reinterpret_cast<const PipeSpec *>(s_spec_raw);
     while (true) {
         if (threadIdx.x == 0) s_item = static_cast<long long>(atomicAdd(A.counter, 1ull));
         __syncthreads();
@@ -196,8 +202,13 @@ __global__ void __launch_bounds__(BT, 1) k_batch(BatchArgs A)
                 __threadfence();
             }
         }
+        {
+            const unsigned *src = reinterpret_cast<const unsigned *>(&B.P);
+            unsigned *dst = reinterpret_cast<unsigned *>(s_spec_raw);
+            for (int i = threadIdx.x; i < static_cast<int>(sizeof(PipeSpec) / 4); i += BT) dst[i] = src[i];
+        }
         __syncthreads();
-        const PipeSpec &P = B.P;
+        const PipeSpec &P = SP;
         const TableCfg T = B.T;
         if (!s_flag) {
             table_zero(P, T, sm);

@@ -385,12 +385,14 @@ __device__ __forceinline__ void table_flush(const PipeSpec &P, const TableCfg &T
 // ------------------------------------------------------------ star shape
 // One int32 predicate column, an int32 foreign key joined through a dense
 // table, the group key (hi column, join payload) in a direct array and the
-// aggregates [SUM(x*y), COUNT, MIN(x), MAX(x)] with x int64, y int32.  Rows
-// [r0, r1) are processed by one block in tiles of THREADS x ITEMS rows; all
-// columns of the next tile are loaded into registers while the current tile
-// is processed, so the register file holds the loads in flight.
+// aggregates [SUM(x*y), COUNT, MIN(x), MAX(x)] with x int64, y int32.  One
+// block processes the tiles of THREADS x ITEMS rows starting at r0, r0 +
+// stride, ... below r1; all columns of the next tile are loaded into
+// registers while the current tile is processed, so the register file holds
+// the loads in flight.
 template <bool GLOBAL, int ITEMS, int THREADS>
-__device__ __forceinline__ void star_range(const PipeSpec &P, unsigned long long *sm, int64_t r0, int64_t r1)
+__device__ __forceinline__ void star_range(const PipeSpec &P, unsigned long long *sm, int64_t r0, int64_t r1,
+                                           int64_t stride)
 {
     constexpr int TR = THREADS * ITEMS;
     int d[ITEMS], f[ITEMS], h[ITEMS], q[ITEMS];
@@ -414,7 +416,7 @@ __device__ __forceinline__ void star_range(const PipeSpec &P, unsigned long long
     };
     if (r0 >= r1) return;
     load(r0);
-    for (int64_t t0 = r0; t0 < r1; t0 += TR) {
+    for (int64_t t0 = r0; t0 < r1; t0 += stride) {
         int cd[ITEMS], cf[ITEMS], ch[ITEMS], cq[ITEMS];
         long long cx[ITEMS];
         const unsigned cin = inmask;
@@ -426,7 +428,7 @@ __device__ __forceinline__ void star_range(const PipeSpec &P, unsigned long long
             cq[k] = q[k];
             cx[k] = x[k];
         }
-        load(t0 + TR);   // next tile's loads overlap this tile's work
+        load(t0 + stride);   // next tile's loads overlap this tile's work
         bool ok[ITEMS];
         int32_t pay[ITEMS];
 #pragma unroll

@@ -67,8 +67,7 @@ __global__ void __launch_bounds__(PT, 1) k_pipeline(PipeSpec P, TableCfg T)
     table_flush(P, T, sm);
 }
 
-// Star shape (see the file comment): each block takes a contiguous range of
-// rows.  GLOBAL: the direct array lives in HBM (AoS, 4 words per slot)
+// Star shape (see the file comment).  GLOBAL: the direct array lives in HBM (AoS, 4 words per slot)
 // instead of shared memory (SoA).
 template <bool GLOBAL, int ITEMS>
 __global__ void __launch_bounds__(PT, 1) k_pipeline_star(PipeSpec P, TableCfg T)
@@ -77,9 +76,9 @@ __global__ void __launch_bounds__(PT, 1) k_pipeline_star(PipeSpec P, TableCfg T)
     unsigned long long *sm = reinterpret_cast<unsigned long long *>(smem);
     if (!GLOBAL) table_zero(P, T, sm);
     __syncthreads();
-    const int64_t per = (P.n + gridDim.x - 1) / gridDim.x;
-    const int64_t r0 = static_cast<int64_t>(blockIdx.x) * per;
-    star_range<GLOBAL, ITEMS, PT>(P, sm, r0, r0 + per < P.n ? r0 + per : P.n);
+    // grid-stride tiles: at any moment the blocks read neighbouring tiles
+    constexpr int64_t TR = static_cast<int64_t>(PT) * ITEMS;
+    star_range<GLOBAL, ITEMS, PT>(P, sm, static_cast<int64_t>(blockIdx.x) * TR, P.n, TR * gridDim.x);
     __syncthreads();
     if (!GLOBAL) table_flush(P, T, sm);
 }

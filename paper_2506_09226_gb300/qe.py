@@ -432,6 +432,7 @@ def pipeline_desc(fact, preds, fk_col=-1, dim_key=None, dim_payload=None, ht: Ha
 
 
 def qe_pipeline(ctx: Context, desc: qe_pipeline_desc, capacity: int, stream=None, check=True, out=None):
+    """out: (Groups or None, qe_groups_out) to write into existing buffers."""
     if out is None:
         groups, cout = alloc_groups(capacity, desc.n_aggs, torch.device("cuda", ctx.device))
     else:

@@ -28,6 +28,7 @@ STAR_COLS = ("fk", "date", "price", "qty", "flag")
 STAR_AGGS = [(qe.SUM, 2, 3), (qe.COUNT, -1, -1), (qe.MIN, 2, -1), (qe.MAX, 2, -1)]
 CAPACITY = 3072           # output groups per request (3 flags x up to 1000 attributes)
 REQ_BYTES = 560_000       # HBM a request holds while in flight: output slot + batch tables
+ROW_CAP = 100_000_000     # fact rows per batched round
 
 
 def percentile(xs, p: float) -> float:
@@ -91,9 +92,12 @@ class ServeStats:
 
 
 def serve_loop(trace, executor, admission: Admission, max_round: int = 4096, clock=time.perf_counter,
-               idle_sleep: float = 20e-6) -> ServeStats:
+               idle_sleep: float = 20e-6, row_cap: int | None = None) -> ServeStats:
     """Continuous batching over `trace` (Arrival list sorted by t).
 
+    A round takes the oldest admitted requests until it holds max_round of
+    them or row_cap fact rows (a request larger than row_cap goes alone), so
+    rounds stay short and small requests are not held behind a large one.
     executor.launch(reqs) -> handle with .done() and .close(); executor.cost(req)
     is the request's HBM share.  Works with any clock/executor (tests use fakes)."""
     reqs = [Request(i, a.t, a.shape, a.offset, a.n, a.date_hi) for i, a in enumerate(trace)]
@@ -126,7 +130,11 @@ def serve_loop(trace, executor, admission: Admission, max_round: int = 4096, clo
             ready.append(r)
         st.max_inflight = max(st.max_inflight, admission.busy)
         if ready and executor.can_launch():
-            batch, ready = ready[:max_round], ready[max_round:]
+            k, rows = 0, 0
+            while k < len(ready) and k < max_round and (k == 0 or row_cap is None or rows + ready[k].n <= row_cap):
+                rows += ready[k].n
+                k += 1
+            batch, ready = ready[:k], ready[k:]
             inflight.append((executor.launch(batch), batch))
             st.rounds += 1
             st.max_round = max(st.max_round, len(batch))
@@ -210,16 +218,32 @@ class _Round:
         self.free.append(self.stream)
 
 
+class _Single:
+    """A one-request round run as a fused single-pipeline launch."""
+
+    def __init__(self, event, stream, streams_free):
+        self.event, self.stream, self.free = event, stream, streams_free
+
+    def done(self) -> bool:
+        return self.event.query()
+
+    def close(self):
+        self.free.append(self.stream)
+
+
 class BatchExecutor:
-    """Runs a round of requests as one batched launch on a free stream."""
+    """Runs a round of requests as one batched launch on a free stream; a
+    round of one request of at least `single_rows` rows runs as a fused
+    single-pipeline launch instead."""
 
     def __init__(self, ctx, tables: ResidentTables, outs: OutputSlots, n_streams: int = 4,
-                 opts: qe.qe_batch_opts | None = None, on_round=None):
+                 opts: qe.qe_batch_opts | None = None, on_round=None, single_rows: int = 50_000_000):
         self.ctx, self.tables, self.outs = ctx, tables, outs
         self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
         self.free = list(self.streams)
         self.opts = opts if opts is not None else qe.qe_batch_opts(0, 1 << 16, 0, 0)
         self.on_round = on_round
+        self.single_rows = single_rows
 
     def cost(self, r: Request) -> int:
         return REQ_BYTES
@@ -229,14 +253,21 @@ class BatchExecutor:
 
     def launch(self, reqs):
         s = self.free.pop()
+        if self.on_round:
+            self.on_round(reqs)
+        if len(reqs) == 1 and reqs[0].n >= self.single_rows:
+            r = reqs[0]
+            qe.qe_pipeline(self.ctx, self.tables.desc(r), CAPACITY, stream=s, check=False,
+                           out=(None, self.outs.structs[r.slot]))
+            ev = torch.cuda.Event()
+            ev.record(s)
+            return _Single(ev, s, self.free)
         descs = [self.tables.desc(r) for r in reqs]
         outs = [self.outs.structs[r.slot] for r in reqs]
         b = qe.Batch(self.ctx, descs, outs, self.opts, s)
         b.launch(s)
         ev = torch.cuda.Event()
         ev.record(s)
-        if self.on_round:
-            self.on_round(reqs)
         return _Round(b, ev, s, self.free)
 
 
@@ -297,16 +328,16 @@ def bench_serve(ctx, device, stream, peak_gbs: float, duration_s: float = 10.0, 
     adm = Admission(budget_bytes=slots * REQ_BYTES, slots=slots)
     ex = BatchExecutor(ctx, tables, outs, n_streams=4)
     # warm-up round (module load, first launch)
-    warm = serve_loop(trace[:8], ex, Admission(slots * REQ_BYTES, slots))
+    warm = serve_loop(trace[:8], ex, Admission(slots * REQ_BYTES, slots), row_cap=ROW_CAP)
     torch.cuda.synchronize()
     log(f"serve: {len(trace)} requests over {duration_s}s, resident {resident / 1e9:.1f} GB")
-    st = serve_loop(trace, ex, adm)
+    st = serve_loop(trace, ex, adm, row_cap=ROW_CAP)
     ctx.sync_status()
     served = st.summary()
     del warm
     # serial replays on the first serial_s seconds of the same trace
     prefix = [a for a in trace if a.t < serial_s]
-    st_pre = serve_loop(prefix, ex, Admission(slots * REQ_BYTES, slots)).summary()
+    st_pre = serve_loop(prefix, ex, Admission(slots * REQ_BYTES, slots), row_cap=ROW_CAP).summary()
     mx = max(a.n for a in prefix) if prefix else 1
     scratch = {"sel": torch.empty(mx, dtype=torch.int32, device=device),
                "cnt": torch.empty(1, dtype=torch.int64, device=device),

@@ -23,9 +23,11 @@ def test_served_mix_equals_solo_and_oracle():
     tables = serve.ResidentTables(ctx, shapes, dev, log=lambda *a: None)
     trace = datagen.poisson_trace(0.15, 2000.0, tables.rows, seed=1, n_lo=1e3, n_hi=2e6)
     assert len(trace) > 100
+    reqs_n = [a.n for a in trace]
     outs = serve.OutputSlots(len(trace) + 8, dev)
     rounds = []
-    ex = serve.BatchExecutor(ctx, tables, outs, n_streams=3, on_round=lambda rs: rounds.append([r.rid for r in rs]))
+    ex = serve.BatchExecutor(ctx, tables, outs, n_streams=3, on_round=lambda rs: rounds.append([r.rid for r in rs]),
+                             single_rows=1_000_000)
     adm = serve.Admission(budget_bytes=(len(trace) + 8) * serve.REQ_BYTES, slots=len(trace) + 8)
     reqs = []
     orig = ex.launch
@@ -34,10 +36,11 @@ def test_served_mix_equals_solo_and_oracle():
         reqs.extend(rs)
         return orig(rs)
     ex.launch = launch
-    st = serve.serve_loop(trace, ex, adm)
+    st = serve.serve_loop(trace, ex, adm, row_cap=3_000_000)
     ctx.sync_status()
     assert len(st.latencies_ms) == len(trace) and st.rounds == len(rounds)
     assert max(len(r) for r in rounds) > 1                 # requests were batched together
+    assert any(len(r) == 1 and reqs_n[r[0]] >= 1_000_000 for r in rounds)   # and large ones ran alone
     g1, o1 = qe.alloc_groups(serve.CAPACITY, 4, dev)
     for r in reqs:
         k, a = outs.groups(r.slot)

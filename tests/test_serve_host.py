@@ -96,3 +96,13 @@ def test_poisson_trace_rate_and_ranges():
     assert all(0 <= a.offset and a.offset + a.n <= (10 ** 9 if a.shape == 0 else 5 * 10 ** 8) for a in tr)
     assert all(int(0.01 * 2557) - 1 <= a.date_hi <= int(0.9 * 2557) + 1 for a in tr)
     assert all(tr[i].t <= tr[i + 1].t for i in range(len(tr) - 1))
+
+
+def test_row_cap_keeps_rounds_short():
+    clock = FakeClock()
+    sizes = [10, 10, 500, 10, 10, 10]
+    trace = [datagen.Arrival(0.0, 0, 0, n, 100) for n in sizes]
+    ex = FakeExecutor(clock, dur=0.01)
+    adm = serve.Admission(budget_bytes=10 ** 9, slots=100)
+    serve.serve_loop(trace, ex, adm, clock=clock, idle_sleep=0, row_cap=100)
+    assert ex.rounds == [[0, 1], [2], [3, 4, 5]]        # oldest first; the big one alone
