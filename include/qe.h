@@ -136,6 +136,9 @@ void qe_debug_set_spin_limit(qe_ctx *ctx, int64_t iterations);
  *   "star_items"    rows per thread of the star-shape pipeline kernel: 2 or 3
  *                   (0 = default 3);
  *   "force_generic" nonzero: run every pipeline through the generic kernel.
+ *   "part_general"  nonzero: qe_partition always uses its general scatter
+ *                   kernel (two-pass chunk ranking, any payload types)
+ *                   instead of the write-combining one.
  * Unknown names return QE_ERR_INVALID_ARG. */
 qe_status qe_set_tuning(qe_ctx *ctx, const char *name, int64_t value);
 

@@ -110,6 +110,8 @@ extern "C" qe_status qe_set_tuning(qe_ctx *ctx, const char *name, int64_t value)
         ctx->tune_star_items = static_cast<int>(value);
     } else if (n == "force_generic") {
         ctx->tune_force_generic = value != 0;
+    } else if (n == "part_general") {
+        ctx->tune_part_general = value != 0;
     } else {
         return qe_fail(ctx, QE_ERR_INVALID_ARG, "unknown tuning knob " + n);
     }

@@ -42,6 +42,7 @@ struct qe_ctx {
     std::atomic<int64_t> launches{0};
     int tune_star_items = 0;        // 0: default
     int tune_force_generic = 0;
+    int tune_part_general = 0;      // partition: skip the write-combining scatter
     bool profiling = false;
     std::mutex prof_mu;
     std::map<std::string, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>> prof;

@@ -10,26 +10,22 @@
 //                      off[b][p] = sum over earlier blocks of hist[.][p] and
 //                      base[p] = sum over earlier destinations of all rows, so
 //                      block b's rows for p start at base[p] + off[b][p];
-//   3. k_part_scatter  block b walks its rows in chunks of CHUNK in order.  The
-//                      next chunk's keys (and an int64 payload) are copied into
-//                      shared memory with bulk TMA copies while the current one
-//                      is processed (double buffer, mbarrier completion).  A
-//                      chunk is ranked stably by destination in shared memory
-//                      (one or two LSD digit passes; within a warp equal digits
-//                      are ranked with __match_any_sync, warps and digits with a
-//                      block scan); rows are then written in destination order
-//                      through the inverse permutation, so consecutive lanes
-//                      store consecutive rows of one destination.  Each block
-//                      keeps a running output offset per destination, so rows
-//                      keep their input order.
+//   3. scatter        block b walks its rows in chunks, in order, ranks each
+//                      chunk stably by destination in shared memory and writes
+//                      the rows in destination order, keeping a running output
+//                      offset per destination so rows keep their input order.
+//                      Two kernels:
+//                      k_part_scatter_wc (one int64 payload or none, F <= 512):
+//                        register-prefetched chunks, one-pass ranking with
+//                        per-warp counters, and write-combining of 32-byte
+//                        sectors (see below);
+//                      k_part_scatter (qe_part_general.cuh; any payloads, any
+//                        fan-out): bulk-copy (TMA) double-buffered chunks and
+//                        a one- or two-digit LSD ranking.
 #include "qe_pipe_core.cuh"
 
 namespace {
 
-constexpr int PT = 1024;           // scatter threads per block (32 warps), one block per SM
-constexpr int NW = PT / 32;
-constexpr int P_ITEMS = 4;         // rows per thread per chunk
-constexpr int CHUNK = PT * P_ITEMS;
 constexpr int HT = 1024;           // histogram threads per block
 constexpr int H_ITEMS = 8;
 constexpr int H_SPLIT = 4;         // histogram blocks per scatter block
@@ -133,222 +129,330 @@ __global__ void __launch_bounds__(1024) k_part_basescan(const int64_t *tot, int6
     if (t == 0) out_offsets[F] = n;
 }
 
-// Digit counters: cnt[d * CSTRIDE + w] (uint32) for digit d and warp w.  The
-// odd stride puts different digits of one warp in different banks.
-constexpr int CSTRIDE = NW + 1;
+// ---------------------------------------------------------------------------
+// Write-combining scatter: int64 keys with no payload or one int64 payload,
+// fan-out F <= 512.  A block walks its rows in chunks of T * W_ITEMS;
+// the next chunk is loaded into registers while the current one is ranked.
+//
+// Ranking is one pass: each warp counts destinations in its own row of the
+// counter matrix cnt[warp][p] (equal destinations within a warp found with
+// bit-wise ballots, in lane order), the matrix is scanned over warps per
+// destination and then over destinations, and every row moves to its stable
+// sorted position in shared memory.
+//
+// A DRAM sector is 32 bytes (four 8-byte rows).  With F destinations a chunk
+// adds only CHUNK/F rows to each, so writing every chunk's rows at once would
+// leave most sectors half written and complete them a chunk later, after L2
+// may have evicted them (a read-modify-write in DRAM).  Instead the rows of a
+// destination's last, incomplete sector stay in shared memory ("pending", at
+// most three) until a later chunk fills the sector; only whole sectors are
+// written, except the first and last sector of the block's range, which it
+// shares with the neighbouring blocks.
+constexpr int W_ITEMS = 8;                    // rows per thread per chunk
+constexpr int WC_MAX_LOG2F = 9;
 
-// Block-wide exclusive scan, in place, of the counters in digit-major order
-// (d, then w) over ndig digits.  Totals are at most CHUNK.
-__device__ __forceinline__ void block_excl_scan_cnt(uint32_t *cnt, int ndig, int *s_w)
+// Shared-memory layout of a block of T threads (chunks of T * W_ITEMS rows).
+struct WcLayout {
+    size_t sK, sP, pK, pP, ob, qt, rq, hist, start, cnt, sD, total;
+    int FC;                                       // counter row width (even)
+    __host__ __device__ WcLayout(int F, bool pay, int T)
+    {
+        const size_t f = static_cast<size_t>(F), ch = static_cast<size_t>(T) * W_ITEMS;
+        FC = F < 2 ? 2 : F;
+        sK = 0;
+        sP = sK + ch * 8;
+        pK = sP + (pay ? ch * 8 : 0);
+        pP = pK + 24 * f;
+        ob = pP + (pay ? 24 * f : 0);
+        qt = ob + 8 * f;
+        rq = qt + 8 * f;
+        hist = rq + 4 * f;
+        start = hist + 4 * f;
+        cnt = (start + 4 * f + 15) & ~size_t(15);
+        sD = cnt + 2 * static_cast<size_t>(T / 32) * FC;
+        total = sD + 2 * ch;
+    }
+};
+
+template <bool PAY, int T>
+__device__ __forceinline__ void wc_load(const PartArgs &A, int64_t r0, int64_t hi, long long (&k)[W_ITEMS],
+                                        long long (&v)[W_ITEMS])
 {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < W_ITEMS; i++) {
+        const int64_t r = r0 + warp * 32 * W_ITEMS + i * 32 + lane;
+        k[i] = r < hi ? __ldcs(reinterpret_cast<const long long *>(A.keys) + r) : 0;
+        if (PAY) v[i] = r < hi ? __ldcs(static_cast<const long long *>(A.pay[0]) + r) : 0;
+    }
+}
+
+// Lanes holding the same BITS-bit label d, among the lanes in `valid`.
+template <int BITS>
+__device__ __forceinline__ unsigned match_label(uint32_t d, unsigned valid)
+{
+#ifdef QE_WC_MATCH_ANY
+    return __match_any_sync(QE_FULL_MASK, d) & valid;
+#endif
+    unsigned peers = valid;
+#pragma unroll
+    for (int bit = 0; bit < BITS; bit++) {
+        const bool on = (d >> bit) & 1u;
+        const unsigned set = __ballot_sync(QE_FULL_MASK, on);
+        peers &= on ? set : ~set;
+    }
+    return peers;
+}
+
+// Exclusive scan of a[0..N) into out[0..N) by a block of T threads.
+template <int T>
+__device__ __forceinline__ void wc_block_scan(const uint32_t *a, uint32_t *out, int N, int *s_w)
+{
+    constexpr int NWARP = T / 32;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int N = ndig * NW;
-    const int per = (N + PT - 1) / PT;
+    const int per = (N + T - 1) / T;
     uint32_t local = 0;
     for (int j = 0; j < per; j++) {
         const int i = t * per + j;
-        if (i < N) local += cnt[(i / NW) * CSTRIDE + (i % NW)];
+        if (i < N) local += a[i];
     }
     const uint32_t inc = warp_incl_scan(local);
+    if (N <= 32 * per) {                          // one warp holds everything
+        if (warp == 0) {
+            uint32_t run = inc - local;
+            for (int j = 0; j < per; j++) {
+                const int i = t * per + j;
+                if (i < N) {
+                    out[i] = run;
+                    run += a[i];
+                }
+            }
+        }
+        return;
+    }
     if (lane == 31) s_w[warp] = static_cast<int>(inc);
     __syncthreads();
     if (warp == 0) {
-        const int w = lane < NW ? s_w[lane] : 0;
+        const int w = lane < NWARP ? s_w[lane] : 0;
         const int wi = warp_incl_scan(w);
-        if (lane < NW) s_w[lane] = wi - w;
+        if (lane < NWARP) s_w[lane] = wi - w;
     }
     __syncthreads();
     uint32_t run = static_cast<uint32_t>(s_w[warp]) + inc - local;
     for (int j = 0; j < per; j++) {
         const int i = t * per + j;
         if (i < N) {
-            uint32_t *c = cnt + (i / NW) * CSTRIDE + (i % NW);
-            const uint32_t v = *c;
-            *c = run;
-            run += v;
+            out[i] = run;
+            run += a[i];
         }
     }
-    __syncthreads();
 }
 
-// Stable rank of the chunk's m packed words (destination << 12 | source row)
-// by the digit (destination >> shift) & (2^bits - 1): in[s] moves to out[rank].
-// Items are warp-striped: warp w owns positions [w*32*P_ITEMS, (w+1)*32*P_ITEMS),
-// so the natural order is (warp, item, lane).
-__device__ __forceinline__ void rank_pass(const uint32_t *in, uint32_t *out, int m, int shift, int bits, uint32_t *cnt,
-                                          int *s_w)
+template <bool PAY, int BITS, int T>
+__global__ void __launch_bounds__(T, T <= 256 ? 2 : 1) k_part_scatter_wc(PartArgs A)
 {
+    constexpr int NWARP = T / 32;
+    constexpr int CH = T * W_ITEMS;
+    static_assert(CH < 65536, "counters are 16-bit");
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int s_w[NWARP];
+    const int F = 1 << A.log2f;
+    const WcLayout L(F, PAY, T);
+    const int FC = L.FC;
+    long long *sK = reinterpret_cast<long long *>(smem + L.sK);     // sorted chunk keys
+    long long *sP = reinterpret_cast<long long *>(smem + L.sP);     // sorted chunk payloads
+    long long *pK = reinterpret_cast<long long *>(smem + L.pK);     // pending keys [F][3]
+    long long *pP = reinterpret_cast<long long *>(smem + L.pP);     // pending payloads [F][3]
+    long long **ob = reinterpret_cast<long long **>(smem + L.ob);   // key output address of q = 0
+    int2 *qt = reinterpret_cast<int2 *>(smem + L.qt);               // {q of sorted row 0, rows t < y written now}
+    int32_t *rq = reinterpret_cast<int32_t *>(smem + L.rq);         // q of the next row
+    uint32_t *hist = reinterpret_cast<uint32_t *>(smem + L.hist);
+    uint32_t *start = reinterpret_cast<uint32_t *>(smem + L.start);
+    uint16_t *cnt = reinterpret_cast<uint16_t *>(smem + L.cnt);     // [NWARP][FC]
+    uint16_t *sD = reinterpret_cast<uint16_t *>(smem + L.sD);       // sorted chunk destinations
+
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1;
-    const int ndig = 1 << bits;
-    const unsigned dmask = ndig - 1;
-    for (int i = threadIdx.x; i < ndig * CSTRIDE; i += PT) cnt[i] = 0;
-    __syncthreads();
-    uint32_t wv[P_ITEMS], r[P_ITEMS];
-#pragma unroll
-    for (int k = 0; k < P_ITEMS; k++) {
-        const int s2 = warp * 32 * P_ITEMS + k * 32 + lane;
-        const bool valid = s2 < m;
-        wv[k] = valid ? in[s2] : 0;
-        const unsigned d = valid ? ((wv[k] >> (12 + shift)) & dmask) : 0xffffu;
-        const unsigned peers = __match_any_sync(QE_FULL_MASK, d);
-        uint32_t basec = 0;
-        if (valid) basec = cnt[d * CSTRIDE + warp];
-        __syncwarp();
-        if (valid && lane == __ffs(peers) - 1) cnt[d * CSTRIDE + warp] = basec + __popc(peers);
-        __syncwarp();
-        r[k] = basec + __popc(peers & lt);
-    }
-    __syncthreads();
-    block_excl_scan_cnt(cnt, ndig, s_w);
-#pragma unroll
-    for (int k = 0; k < P_ITEMS; k++) {
-        const int s2 = warp * 32 * P_ITEMS + k * 32 + lane;
-        if (s2 < m) {
-            const unsigned d = (wv[k] >> (12 + shift)) & dmask;
-            out[cnt[d * CSTRIDE + warp] + r[k]] = wv[k];
-        }
-    }
-    __syncthreads();
-}
-
-__device__ __forceinline__ void copy_elem(void *dst, const void *src, int type, int64_t d, int64_t s)
-{
-    if (type == QE_I64)
-        static_cast<long long *>(dst)[d] = __ldg(static_cast<const long long *>(src) + s);
-    else if (type == QE_I32)
-        static_cast<int32_t *>(dst)[d] = __ldg(static_cast<const int32_t *>(src) + s);
-    else
-        static_cast<signed char *>(dst)[d] = __ldg(static_cast<const signed char *>(src) + s);
-}
-
-// FAST: exactly one int64 payload column, staged in shared memory with the
-// keys.  Otherwise payload columns are gathered by chunk-local source row.
-template <bool FAST>
-__global__ void __launch_bounds__(PT, 1) k_part_scatter(PartArgs A)
-{
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) unsigned long long s_bar[2];
-    __shared__ int s_w[NW];
-    __shared__ int s_abort;
-    const int F = 1 << A.log2f;
-    // layout: bufK[2][CHUNK] i64 | bufP[2][CHUNK] i64 (FAST) | run[F] i64 |
-    //         wA, wB [CHUNK] u32 (destination << 12 | source row) | start[F] u16 |
-    //         cnt[64 * CSTRIDE] u32
-    int64_t *bufK = reinterpret_cast<int64_t *>(smem);
-    int64_t *bufP = bufK + 2 * CHUNK;
-    int64_t *run = FAST ? bufP + 2 * CHUNK : bufP;
-    uint32_t *wA = reinterpret_cast<uint32_t *>(run + F);
-    uint32_t *wB = wA + CHUNK;
-    uint32_t *cnt = wB + CHUNK;
-    uint16_t *start = reinterpret_cast<uint16_t *>(cnt + 64 * CSTRIDE);
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int b = blockIdx.x;
     const int64_t lo = static_cast<int64_t>(b) * A.rows_per_block;
     const int64_t hi = min(A.n, lo + A.rows_per_block);
-    const int64_t nch = (hi - lo + CHUNK - 1) / CHUNK;
-    for (int p = threadIdx.x; p < F; p += PT) run[p] = A.base[p] + A.off[static_cast<int64_t>(b) * F + p];
-    if (threadIdx.x == 0) {
-        s_abort = 0;
-        mbar_init(&s_bar[0], 1);
-        mbar_init(&s_bar[1], 1);
-        mbar_fence_init();
-    }
-    const int passes = A.log2f == 0 ? 0 : (A.log2f <= 6 ? 1 : 2);
-    const int bits1 = passes == 2 ? (A.log2f + 1) / 2 : A.log2f;
-    const int bits2 = A.log2f - bits1;
-    __syncthreads();
-    const uint64_t pol = l2_evict_first_policy();
+    const int64_t nch = (hi - lo + CH - 1) / CH;
+    long long *outK = reinterpret_cast<long long *>(A.out_keys);
+    // payload address = key address + dP elements
+    const int64_t dP = PAY ? static_cast<long long *>(A.out_pay[0]) - outK : 0;
+    // Block b's rows for destination p are the output rows [g, g + n_p).  A
+    // row is numbered q = (its rank among them) - hl, where hl rows fill the
+    // key sector that g starts in (0 if g starts one); q = 0 then starts a
+    // sector and the sectors are q in [4j, 4j + 4).  Rows with q < 0 share
+    // their sector with the previous block and are written at once.
+    const int aoff = static_cast<int>((reinterpret_cast<uintptr_t>(outK) >> 3) & 3);
 
-    // chunk c: rows [lo + c*CHUNK, ...) into buffer c & 1
-    auto issue = [&](int64_t c) {
-        const int64_t r0 = lo + c * CHUNK;
-        const int m = static_cast<int>(hi - r0 < CHUNK ? hi - r0 : CHUNK);
-        const int mc = A.tma ? (m & ~1) : 0;      // 16-byte multiple
-        unsigned long long *bar = &s_bar[c & 1];
-        const uint32_t bytes = static_cast<uint32_t>(mc) * 8u * (FAST ? 2u : 1u);
-        if (bytes) {
-            fence_proxy_async_smem();
-            mbar_arrive_expect_tx(bar, bytes);
-            tma_load_1d(bufK + (c & 1) * CHUNK, A.keys + r0, mc * 8u, bar, pol);
-            if (FAST) tma_load_1d(bufP + (c & 1) * CHUNK, static_cast<const long long *>(A.pay[0]) + r0, mc * 8u, bar, pol);
-        } else {
-            mbar_arrive(bar);
-        }
-    };
-    if (threadIdx.x == 0 && nch > 0) issue(0);
+    for (int p = threadIdx.x; p < F; p += T) {
+        const int64_t g = A.base[p] + A.off[static_cast<int64_t>(b) * F + p];
+        const int hl = static_cast<int>((4 - ((g + aoff) & 3)) & 3);
+        ob[p] = outK + g + hl;
+        rq[p] = -hl;
+    }
+    for (int i = threadIdx.x; i < NWARP * FC / 8; i += T) reinterpret_cast<uint4 *>(cnt)[i] = make_uint4(0, 0, 0, 0);
+    long long ck[W_ITEMS], cv[W_ITEMS];
+    wc_load<PAY, T>(A, lo, hi, ck, cv);
+    __syncthreads();
 
     for (int64_t c = 0; c < nch; c++) {
-        if (threadIdx.x == 0 && c + 1 < nch) issue(c + 1);
-        const int64_t r0 = lo + c * CHUNK;
-        const int m = static_cast<int>(hi - r0 < CHUNK ? hi - r0 : CHUNK);
-        const int mc = A.tma ? (m & ~1) : 0;
-        int64_t *keys = bufK + (c & 1) * CHUNK;
-        int64_t *pays = bufP + (c & 1) * CHUNK;
-        if (!mbar_wait(&s_bar[c & 1], static_cast<uint32_t>((c >> 1) & 1), A.spin_limit)) {
-            if (threadIdx.x == 0) dev_report(A.st, QE_ERR_TIMEOUT, 0);
-            s_abort = 1;
-        }
-        // rows the bulk copy did not cover (unaligned columns, odd tail)
-        for (int s2 = mc + threadIdx.x; s2 < m; s2 += PT) {
-            keys[s2] = A.keys[r0 + s2];
-            if (FAST) pays[s2] = static_cast<const long long *>(A.pay[0])[r0 + s2];
-        }
-        __syncthreads();
-        if (s_abort) break;
+        const int64_t r0 = lo + c * CH;
+        const int m = static_cast<int>(hi - r0 < CH ? hi - r0 : CH);
+        long long nk[W_ITEMS], nv[W_ITEMS];
+        wc_load<PAY, T>(A, r0 + CH, hi, nk, nv);     // rows past hi are not read
+
+        // destination and rank among the warp's earlier rows of that destination
+        uint32_t dg[W_ITEMS], rk[W_ITEMS];
 #pragma unroll
-        for (int k = 0; k < P_ITEMS; k++) {
-            const int s2 = warp * 32 * P_ITEMS + k * 32 + lane;
-            if (s2 < m) wA[s2] = (dev_part_id(keys[s2], A.log2f, A.mode, A.shift) << 12) | static_cast<uint32_t>(s2);
+        for (int i = 0; i < W_ITEMS; i++) {
+            const bool valid = warp * 32 * W_ITEMS + i * 32 + lane < m;
+            const uint32_t d = valid ? dev_part_id(ck[i], A.log2f, A.mode, A.shift) : 0u;
+            const unsigned peers = match_label<BITS>(d, __ballot_sync(QE_FULL_MASK, valid));
+            uint16_t *cp = cnt + warp * FC + d;
+            uint32_t basec = 0;
+            if (valid) basec = *cp;
+            __syncwarp();
+            if (valid && lane == __ffs(peers) - 1) *cp = static_cast<uint16_t>(basec + __popc(peers));
+            __syncwarp();
+            dg[i] = valid ? d : 0xffffffffu;
+            rk[i] = basec + __popc(peers & lt);
         }
         __syncthreads();
-        const uint32_t *sorted = wA;
-        if (passes >= 1) {
-            rank_pass(wA, wB, m, 0, bits1, cnt, s_w);
-            sorted = wB;
-        }
-        if (passes == 2) {
-            rank_pass(wB, wA, m, bits1, bits2, cnt, s_w);
-            sorted = wA;
-        }
-        // run starts (positions where the destination changes)
-        for (int t = threadIdx.x; t < m; t += PT) {
-            const uint32_t p = sorted[t] >> 12;
-            if (t == 0 || (sorted[t - 1] >> 12) != p) start[p] = static_cast<uint16_t>(t);
-        }
-        __syncthreads();
-        for (int t = threadIdx.x; t < m; t += PT) {
-            const uint32_t w = sorted[t];
-            const uint32_t p = w >> 12;
-            const int src = static_cast<int>(w & 0xfffu);
-            const int64_t d = run[p] + (t - start[p]);
-            __stcs(reinterpret_cast<long long *>(A.out_keys) + d, keys[src]);
-            if (FAST) {
-                __stcs(static_cast<long long *>(A.out_pay[0]) + d, pays[src]);
+        // per destination pair (two 16-bit counters in a word): prefix over
+        // warps and totals; both halves stay below 2^16
+        {
+            uint32_t *cw = reinterpret_cast<uint32_t *>(cnt);
+            const int FW = FC / 2;
+            if (NWARP * FW <= T) {
+                // one thread per (pair, warp); the warps of a pair are
+                // NWARP consecutive lanes, scanned with shuffles
+                const int j = threadIdx.x / NWARP, w = threadIdx.x % NWARP;
+                const bool on = j < FW;
+                const uint32_t x = on ? cw[w * FW + j] : 0u;
+                uint32_t inc = x;
+#pragma unroll
+                for (int o = 1; o < NWARP; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(QE_FULL_MASK, inc, o, NWARP);
+                    if (w >= o) inc += y;
+                }
+                if (on) {
+                    cw[w * FW + j] = inc - x;
+                    if (w == NWARP - 1) {
+                        if (2 * j < F) hist[2 * j] = inc & 0xffffu;
+                        if (2 * j + 1 < F) hist[2 * j + 1] = inc >> 16;
+                    }
+                }
             } else {
-                for (int j = 0; j < A.npay; j++) copy_elem(A.out_pay[j], A.pay[j], A.pay_type[j], d, r0 + src);
+                for (int j = threadIdx.x; j < FW; j += T) {
+                    uint32_t tot = 0;
+#pragma unroll
+                    for (int w = 0; w < NWARP; w++) {
+                        const uint32_t x = cw[w * FW + j];
+                        cw[w * FW + j] = tot;
+                        tot += x;
+                    }
+                    if (2 * j < F) hist[2 * j] = tot & 0xffffu;
+                    if (2 * j + 1 < F) hist[2 * j + 1] = tot >> 16;
+                }
             }
         }
         __syncthreads();
-        for (int t = threadIdx.x; t < m; t += PT) {
-            const uint32_t p = sorted[t] >> 12;
-            if (t == m - 1 || (sorted[t + 1] >> 12) != p) run[p] += t - start[p] + 1;
+        wc_block_scan<T>(hist, start, F, s_w);
+        __syncthreads();
+        for (int p = threadIdx.x; p < F; p += T) {
+            const int r = rq[p];
+            const int h = static_cast<int>(hist[p]);
+            const int e = r + h;
+            const int r4 = r & ~3, e4 = e & ~3;
+            const int np = r > 0 ? (r & 3) : 0;
+            if (np && e4 > r4) {
+                // this chunk completes the pending sector: write its earlier rows
+                long long *o = ob[p] + r4;
+                for (int j = 0; j < np; j++) {
+                    __stcs(o + j, pK[p * 3 + j]);
+                    if (PAY) __stcs(o + dP + j, pP[p * 3 + j]);
+                }
+            }
+            const int lim = e4 > 0 ? e4 : 0;          // rows with q < lim are written now
+            const int k = lim - r;                    // of this chunk's h rows, the first k
+            const int st = static_cast<int>(start[p]);
+            qt[p] = make_int2(r - st, st + (k < 0 ? 0 : (k > h ? h : k)));
+            rq[p] = e;
+        }
+#pragma unroll
+        for (int i = 0; i < W_ITEMS; i++) {
+            if (dg[i] != 0xffffffffu) {
+                const uint32_t pos = start[dg[i]] + cnt[warp * FC + dg[i]] + rk[i];
+                sK[pos] = ck[i];
+                if (PAY) sP[pos] = cv[i];
+                sD[pos] = static_cast<uint16_t>(dg[i]);
+            }
         }
         __syncthreads();
+        for (int t = threadIdx.x; t < m; t += T) {
+            const int p = sD[t];
+            const int2 x = qt[p];
+            const int q = x.x + t;
+            if (t < x.y) {
+                long long *o = ob[p] + q;
+                __stcs(o, sK[t]);
+                if (PAY) __stcs(o + dP, sP[t]);
+            } else {
+                pK[p * 3 + (q & 3)] = sK[t];
+                if (PAY) pP[p * 3 + (q & 3)] = sP[t];
+            }
+        }
+        for (int i = threadIdx.x; i < NWARP * FC / 8; i += T) reinterpret_cast<uint4 *>(cnt)[i] = make_uint4(0, 0, 0, 0);
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < W_ITEMS; i++) {
+            ck[i] = nk[i];
+            if (PAY) cv[i] = nv[i];
+        }
     }
-    if (s_abort && threadIdx.x == 0) {
-        // let copies still in flight land before the block exits (bounded)
-        mbar_wait(&s_bar[0], 0, A.spin_limit);
-        mbar_wait(&s_bar[1], 0, A.spin_limit);
+    // rows still pending at the end of the range
+    for (int p = threadIdx.x; p < F; p += T) {
+        const int r = rq[p];
+        const int np = r > 0 ? (r & 3) : 0;
+        long long *o = ob[p] + (r & ~3);
+        for (int j = 0; j < np; j++) {
+            __stcs(o + j, pK[p * 3 + j]);
+            if (PAY) __stcs(o + dP + j, pP[p * 3 + j]);
+        }
     }
 }
 
-size_t scatter_smem(int log2f, bool fast)
+// Threads per block of the write-combining scatter.  Two blocks of 256 per SM
+// let one block's per-destination phases overlap the other's row phases, but
+// double the output pages an SM writes at a time (one per destination and
+// column per block); beyond a few hundred pages per SM the address
+// translation caches miss and the scatter slows down, so larger fan-outs run
+// one block of 512 per SM.
+inline int wc_threads(int log2f) { return log2f <= 6 ? 256 : 512; }
+
+template <bool PAY>
+static const void *wc_kernel(int log2f)
 {
-    const size_t F = size_t(1) << log2f;
-    return 2 * CHUNK * 8 * (fast ? 2 : 1) + F * 8 + 2 * CHUNK * 4 + 64 * CSTRIDE * 4 + F * 2;
+    if (log2f <= 6) return reinterpret_cast<const void *>(k_part_scatter_wc<PAY, 6, 256>);
+    if (log2f <= 8) return reinterpret_cast<const void *>(k_part_scatter_wc<PAY, 8, 512>);
+    return reinterpret_cast<const void *>(k_part_scatter_wc<PAY, 10, 512>);
 }
+
+// General scatter (any payload columns, any fan-out up to 4096), at 1024
+// threads per block where its shared memory fits and at 512 otherwise.
+namespace gen1024 {
+constexpr int PT = 1024;
+constexpr bool EVICT_LAST = false;
+#include "qe_part_general.cuh"
+}  // namespace gen1024
+namespace gen512 {
+constexpr int PT = 512;
+constexpr bool EVICT_LAST = true;
+#include "qe_part_general.cuh"
+}  // namespace gen512
 
 }  // namespace
 
@@ -387,20 +491,36 @@ extern "C" qe_status qe_partition(qe_ctx *ctx, const int64_t *keys, const qe_col
         return QE_OK;
     }
     const bool fast = npayload == 1 && A.pay_type[0] == QE_I64 && qe_aligned(A.pay[0], 8);
-    const size_t smem = scatter_smem(log2_fanout, fast);
+    // write-combining scatter when the payload allows it and its tables fit
+    const int wt = wc_threads(log2_fanout);
+    const bool wc = !ctx->tune_part_general && log2_fanout <= WC_MAX_LOG2F && (npayload == 0 || fast) &&
+                    WcLayout(F, fast, wt).total <= ctx->smem_optin;
+    const bool big = gen1024::scatter_smem(log2_fanout, fast) <= ctx->smem_optin;
+    const size_t smem = wc ? WcLayout(F, fast, wt).total
+                           : (big ? gen1024::scatter_smem(log2_fanout, fast) : gen512::scatter_smem(log2_fanout, fast));
     if (smem > ctx->smem_optin) return qe_fail(ctx, QE_ERR_INVALID_ARG, "partition: fan-out too large");
-    auto kscatter = fast ? k_part_scatter<true> : k_part_scatter<false>;
+    const void *kscatter;
+    if (wc)
+        kscatter = fast ? wc_kernel<true>(log2_fanout) : wc_kernel<false>(log2_fanout);
+    else if (big)
+        kscatter = fast ? reinterpret_cast<const void *>(gen1024::k_part_scatter<true>)
+                        : reinterpret_cast<const void *>(gen1024::k_part_scatter<false>);
+    else
+        kscatter = fast ? reinterpret_cast<const void *>(gen512::k_part_scatter<true>)
+                        : reinterpret_cast<const void *>(gen512::k_part_scatter<false>);
+    const int threads = wc ? wt : (big ? gen1024::PT : gen512::PT);
+    const int64_t chunk = wc ? static_cast<int64_t>(wt) * W_ITEMS : (big ? gen1024::CHUNK : gen512::CHUNK);
     QE_CUDA(ctx, cudaFuncSetAttribute(kscatter, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
     int per_sm = 0;
-    QE_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kscatter, PT, smem));
+    QE_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kscatter, threads, smem));
     if (per_sm < 1) per_sm = 1;
     int64_t G = static_cast<int64_t>(ctx->num_sms) * per_sm;
-    int64_t need = qe_ceil_div(nrows, CHUNK);
+    int64_t need = qe_ceil_div(nrows, chunk);
     if (G > need) G = need;
-    // whole chunks per block, so every chunk but the last starts 32 KB-aligned
-    A.rows_per_block = qe_ceil_div(qe_ceil_div(nrows, G), CHUNK) * CHUNK;
+    // whole chunks per block, so every chunk but the last starts 16 KB-aligned
+    A.rows_per_block = qe_ceil_div(qe_ceil_div(nrows, G), chunk) * chunk;
     G = qe_ceil_div(nrows, A.rows_per_block);
-    A.tma = qe_aligned(keys, 16) && (!fast || qe_aligned(A.pay[0], 16));
+    A.tma = !wc && qe_aligned(keys, 16) && (!fast || qe_aligned(A.pay[0], 16));
     A.spin_limit = ctx->spin_limit;
     A.st = ctx->dstat;
 
@@ -434,9 +554,10 @@ extern "C" qe_status qe_partition(qe_ctx *ctx, const int64_t *keys, const qe_col
     }
     if (e == cudaSuccess) {
         ProfScope prof(ctx, "part_scatter", s);
-        kscatter<<<static_cast<unsigned>(G), PT, smem, s>>>(A);
+        void *args[] = {&A};
+        e = cudaLaunchKernel(kscatter, dim3(static_cast<unsigned>(G)), dim3(threads), args, smem, s);
         QE_LAUNCHED(ctx);
-        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaGetLastError();
     }
     qe_free(ctx, scratch, s);
     if (e != cudaSuccess) return qe_cuda_fail(ctx, e, "partition launch");

@@ -110,6 +110,47 @@ def test_partition_radix_generic_payloads(ctx, log2f, shift):
     _check_partition(ctx, keys, [], log2f, qe.PART_RADIX, shift)
 
 
+@pytest.mark.parametrize("log2f", [3, 10])
+def test_partition_many_chunks_per_block(ctx, log2f):
+    """Several chunks per block, so the rows a block holds back for an
+    incomplete output sector are carried across chunks; keys only and with
+    one payload."""
+    n = 3_000_001
+    k, p = datagen.key_payload_pairs(n, seed=77)
+    _check_partition(ctx, k.numpy(), [p.numpy()], log2f)
+    _check_partition(ctx, k.numpy(), [], log2f)
+
+
+@pytest.mark.parametrize("koff,poff", [(1, 0), (2, 3), (3, 1)])
+def test_partition_unaligned_outputs(ctx, koff, poff):
+    """Output columns that start mid-sector (8-byte but not 32-byte aligned)."""
+    n = 1_000_003
+    k, p = datagen.key_payload_pairs(n, seed=koff * 4 + poff)
+    kb = torch.empty(n + 4, dtype=torch.int64, device="cuda")
+    pb = torch.empty(n + 4, dtype=torch.int64, device="cuda")
+    ok, op = kb[koff:koff + n], pb[poff:poff + n]
+    offs = torch.empty(1025, dtype=torch.int64, device="cuda")
+    qe.qe_partition(ctx, cuda(k.numpy()), [cuda(p.numpy())], 10, qe.PART_HASH, 0, ok, [op], offs)
+    rk, rp, roffs = O.partition(k.numpy(), [p.numpy()], 10, qe.PART_HASH, 0)
+    assert np.array_equal(offs.cpu().numpy(), roffs)
+    assert np.array_equal(ok.cpu().numpy(), rk)
+    assert np.array_equal(op.cpu().numpy(), rp[0])
+
+
+@pytest.mark.parametrize("log2f", [5, 10])
+def test_partition_general_kernel(ctx, log2f):
+    """The general scatter (two-pass chunk ranking) on the inputs the
+    write-combining scatter normally takes."""
+    n = 1_500_007
+    k, p = datagen.key_payload_pairs(n, seed=log2f + 100)
+    ctx.set_tuning("part_general", 1)
+    try:
+        _check_partition(ctx, k.numpy(), [p.numpy()], log2f)
+        _check_partition(ctx, k.numpy(), [], log2f)
+    finally:
+        ctx.set_tuning("part_general", 0)
+
+
 def test_partition_skew_and_empty(ctx):
     n = 70_000
     keys = np.full(n, 42, np.int64)           # every row to one destination
