@@ -1,0 +1,231 @@
+"""GPU parity at the full sizes of the at-scale and skewed workloads.
+
+The oracle cannot process these inputs whole in a test's time, so each test
+checks (1) sampled outputs that the oracle computes one by one and (2)
+properties that hold at any size, with checks done by plain torch reductions
+on the device:
+
+* star pipeline at scale (fact 600M rows, dimension 20M rows, 3,000 groups),
+  in the launch configuration bench.py times: sampled groups against the
+  oracle over the full input; sum of COUNT = rows passing the filter; sum of
+  SUM(price*qty) and the global MIN / MAX over those rows;
+* partition of 600M (int64 key, int64 payload) pairs at fan-out 256 / 1024 /
+  4096: offsets, payloads a permutation of the row ids, key/payload pairs
+  intact, input order inside every destination, and the destination of
+  sampled rows against the oracle's partition function;
+* skewed, high-cardinality pipeline (fact 300M rows, Zipf(1.1) foreign keys
+  over 50M dimension keys, group-by on ~40M distinct int64 keys in HBM,
+  selectivity 1 % / 50 % / 90 %; group-by on 10^6 dictionary codes):
+  every group of 1000 sampled keys against the oracle run over exactly the
+  rows of those keys; the number of groups; sums of COUNT and SUM.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2506_09226_gb300 import datagen
+from paper_2506_09226_gb300 import qe
+
+pytestmark = pytest.mark.gpu
+
+COLS = ("fk", "date", "price", "qty", "flag")
+STAR_AGGS = [(qe.SUM, 2, 3), (qe.COUNT, -1, -1), (qe.MIN, 2, -1), (qe.MAX, 2, -1)]
+O_AGGS = [(O.SUM, 2, 3), (O.COUNT, -1, -1), (O.MIN, 2, -1), (O.MAX, 2, -1)]
+DATE_LT = 1278
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = qe.Context(0)
+    yield c
+    c.close()
+
+
+class _Groups:
+    """Groups sorted by key, with lookup of single keys."""
+
+    def __init__(self, g):
+        k, a = g.to_host()
+        o = np.argsort(k.numpy(), kind="stable")
+        self.keys = k.numpy()[o]
+        self.aggs = [x.numpy()[o] for x in a]
+
+    def __len__(self):
+        return len(self.keys)
+
+    def __getitem__(self, key):
+        i = int(np.searchsorted(self.keys, key))
+        assert i < len(self.keys) and self.keys[i] == key, key
+        return tuple(int(a[i]) for a in self.aggs)
+
+    def total(self, j):
+        return int(self.aggs[j].sum(dtype=np.int64))
+
+
+def _filtered_totals(fact, mask):
+    """(rows, sum price*qty, min price, max price) over the rows in mask."""
+    price = fact["price"][mask]
+    qty = fact["qty"][mask].to(torch.int64)
+    return (int(mask.sum().item()), int((price * qty).sum().item()), int(price.min().item()),
+            int(price.max().item()))
+
+
+# ---------------------------------------------------------------- star pipeline at scale
+def test_star_pipeline_600M(ctx):
+    dev = torch.device("cuda", 0)
+    n_fact, n_dim = 600_000_000, 20_000_000
+    dim = datagen.star_dim(n_dim, 1000, seed=1, device=dev)
+    fact = datagen.star_fact(n_fact, n_dim, seed=1, device=dev)
+    d = qe.pipeline_desc([fact[c] for c in COLS], [(1, qe.LT, DATE_LT)], fk_col=0, dim_key=dim["key"],
+                         dim_payload=dim["attr"], key_hi_col=4, key_lo_col=qe.JOIN_PAYLOAD, aggs=STAR_AGGS,
+                         expected_groups=3000, est_selectivity=DATE_LT / 2557, key_range=((0, 2), None))
+    g = qe.qe_pipeline(ctx, d, 4096)
+    got = _Groups(g)
+    assert len(got) == 3000
+
+    # properties over all rows (every foreign key has a dimension row)
+    mask = fact["date"] < DATE_LT
+    rows, s, mn, mx = _filtered_totals(fact, mask)
+    del mask
+    assert got.total(1) == rows
+    assert got.total(0) == s
+    assert int(got.aggs[2].min()) == mn
+    assert int(got.aggs[3].max()) == mx
+
+    # sampled groups against the oracle over the full input
+    host = [fact[c].cpu().numpy() for c in COLS]
+    dk, da = dim["key"].cpu().numpy(), dim["attr"].cpu().numpy()
+    q = O.Query(preds=[O.Pred(1, O.LT, DATE_LT)], fk_col=0, key_hi_col=4, key_lo_col=O.JOIN_PAYLOAD, aggs=O_AGGS)
+    rng = np.random.default_rng(11)
+    keys = got.keys
+    for gk in [int(keys[0]), int(keys[-1]), int(keys[rng.integers(1, len(keys) - 1)])]:
+        cnt, ref = O.pipeline_group(host, q, gk, dk, da)
+        assert cnt == got[gk][1]
+        assert tuple(int(x) for x in ref) == got[gk], gk
+
+
+# ---------------------------------------------------------------- partition at scale
+@pytest.fixture(scope="module")
+def pairs():
+    dev = torch.device("cuda", 0)
+    key, pay = datagen.key_payload_pairs(600_000_000, seed=2, device=dev)
+    yield key, pay
+    del key, pay
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("log2f", [8, 10, 12])
+def test_partition_600M(ctx, pairs, log2f):
+    key, pay = pairs
+    n, F = key.numel(), 1 << log2f
+    ok, op = torch.empty_like(key), torch.empty_like(pay)
+    offs = torch.empty(F + 1, dtype=torch.int64, device=key.device)
+    qe.qe_partition(ctx, key, [pay], log2f, qe.PART_HASH, 0, ok, [op], offs)
+
+    o = offs.cpu().numpy()
+    assert o[0] == 0 and o[-1] == n and np.all(np.diff(o) >= 0)
+    # payloads are the row ids: a permutation, with each key still beside its payload
+    assert int(op.min().item()) == 0 and int(op.max().item()) == n - 1
+    seen = torch.zeros(n, dtype=torch.bool, device=key.device)
+    seen[op] = True
+    assert bool(seen.all().item())
+    del seen
+    assert bool(torch.equal(ok, key[op]))
+    # input order inside every destination: row ids increase except where a destination starts
+    step_up = op[1:] > op[:-1]
+    starts = torch.from_numpy(o[1:-1]).to(key.device)
+    starts = starts[(starts > 0) & (starts < n)] - 1
+    step_up[starts] = True
+    assert bool(step_up.all().item())
+    del step_up
+    # destination of sampled output rows against the oracle's partition function
+    rng = np.random.default_rng(log2f)
+    pos = np.sort(rng.choice(n, 20_000, replace=False))
+    ks = ok[torch.from_numpy(pos).to(key.device)].cpu().numpy()
+    seg = np.searchsorted(o, pos, side="right") - 1
+    for p, k in zip(seg, ks):
+        assert O.partition_of(int(k), log2f) == p
+    # each destination's size against the oracle's function on a sample of input rows
+    samp = key[torch.from_numpy(rng.choice(n, 200_000, replace=False)).to(key.device)].cpu().numpy()
+    hist = np.bincount([O.partition_of(int(k), log2f) for k in samp], minlength=F) * (n / len(samp))
+    sizes = np.diff(o)
+    sigma = np.sqrt(hist.clip(min=1) * (n / len(samp)))
+    assert np.all(np.abs(sizes - hist) < 6 * sigma + 5)
+
+
+# ---------------------------------------------------------------- skew and high cardinality
+@pytest.fixture(scope="module")
+def skew():
+    dev = torch.device("cuda", 0)
+    dim = datagen.star_dim(50_000_000, 1000, seed=3, device=dev)
+    fact = datagen.star_fact(300_000_000, 50_000_000, seed=3, device=dev, zipf_s=1.1, n_codes=1_000_000,
+                             n_gkeys=40_000_000)
+    yield fact, dim
+    del fact, dim
+    torch.cuda.empty_cache()
+
+
+SKEW_COLS = ("fk", "date", "price", "qty", "flag", "code", "gkey")
+
+
+def _check_sampled_groups(fact, dim, got, key_col, preds_qe, preds_o, rng, nsample=1000):
+    """Every group of nsample sampled keys against the oracle, run over the
+    rows holding those keys (and the dimension rows they reference)."""
+    pick = torch.from_numpy(rng.choice(got.keys, min(nsample, len(got)), replace=False)).to(fact["fk"].device)
+    col = fact[key_col]
+    rows = torch.isin(col.to(torch.int64), pick)
+    sub = [fact[c][rows].cpu().numpy() for c in SKEW_COLS]
+    fks = fact["fk"][rows]
+    drows = torch.isin(dim["key"], fks)
+    dk, da = dim["key"][drows].cpu().numpy(), dim["attr"][drows].cpu().numpy()
+    q = O.Query(preds=preds_o, fk_col=0, key_hi_col=-1, key_lo_col=SKEW_COLS.index(key_col), aggs=O_AGGS)
+    ref = O.pipeline(sub, q, dk, da)
+    picked = set(int(x) for x in pick.cpu().numpy())
+    seen = 0
+    for i, k in enumerate(ref["keys"]):
+        k = int(k)
+        if k in picked:
+            assert got[k] == tuple(int(a[i]) for a in ref["aggs"]), k
+            seen += 1
+    assert seen == len(picked)
+
+
+@pytest.mark.parametrize("sel", [0.01, 0.50, 0.90])
+def test_skew_pipeline_40M_groups(ctx, skew, sel):
+    fact, dim = skew
+    c = int(round(sel * datagen.DATE_SPAN))
+    f = [fact[x] for x in SKEW_COLS]
+    d = qe.pipeline_desc(f, [(1, qe.LT, c)], fk_col=0, dim_key=dim["key"], dim_payload=dim["attr"],
+                         key_hi_col=-1, key_lo_col=SKEW_COLS.index("gkey"), aggs=STAR_AGGS,
+                         expected_groups=40_000_000, est_selectivity=sel)
+    g = qe.qe_pipeline(ctx, d, 40_000_000)
+    mask = fact["date"] < c
+    nkeys = int(torch.unique(fact["gkey"][mask]).numel())
+    rows, s, _, _ = _filtered_totals(fact, mask)
+    del mask
+    assert int(g.ngroups.item()) == nkeys
+    got = _Groups(g)
+    assert got.total(1) == rows
+    assert got.total(0) == s
+    _check_sampled_groups(fact, dim, got, "gkey", None, [O.Pred(1, O.LT, c)], np.random.default_rng(c))
+
+
+def test_skew_pipeline_dictionary_codes(ctx, skew):
+    """Group by the int32 dictionary codes (10^6 values) under a code-range predicate."""
+    fact, dim = skew
+    k = 250_000
+    f = [fact[x] for x in SKEW_COLS]
+    d = qe.pipeline_desc(f, [(5, qe.LT, k)], fk_col=0, dim_key=dim["key"], dim_payload=dim["attr"],
+                         key_hi_col=-1, key_lo_col=SKEW_COLS.index("code"), aggs=STAR_AGGS,
+                         expected_groups=k)
+    g = qe.qe_pipeline(ctx, d, 1_000_000)
+    mask = fact["code"] < k
+    nkeys = int(torch.unique(fact["code"][mask]).numel())
+    rows, s, _, _ = _filtered_totals(fact, mask)
+    del mask
+    assert int(g.ngroups.item()) == nkeys
+    got = _Groups(g)
+    assert got.total(1) == rows
+    assert got.total(0) == s
+    _check_sampled_groups(fact, dim, got, "code", None, [O.Pred(5, O.LT, k)], np.random.default_rng(5))
