@@ -172,25 +172,43 @@ def star_desc(qe, fact, dim, expected_groups):
 
 
 # ---------------------------------------------------------------- CPU oracle leg
-def oracle_sample(n_fact_sample, n_dim, n_pairs_sample, n_attr=1000):
-    """Time the oracle on a bounded sample of the same workload (CPU tensors,
-    same generator and distributions).  Returns (rows, seconds, desc)."""
-    from oracle import oracle as O
-    from paper_2506_09226_gb300 import datagen
-    dim = datagen.star_dim(n_dim, n_attr, seed=1)
-    fact = datagen.star_fact(n_fact_sample, n_dim, seed=1)
-    key, pay = datagen.key_payload_pairs(n_pairs_sample, seed=2)
-    fl = [fact[c].numpy() for c in COLS]
-    q = O.Query(preds=[O.Pred(1, O.LT, DATE_LT)], fk_col=0, key_hi_col=4, key_lo_col=O.JOIN_PAYLOAD,
-                aggs=[(O.SUM, 2, 3), (O.COUNT, -1, -1), (O.MIN, 2, -1), (O.MAX, 2, -1)])
-    dk, da, kk, pp = dim["key"].numpy(), dim["attr"].numpy(), key.numpy(), pay.numpy()
-    O.lib()
-    t0 = time.perf_counter()
-    O.pipeline(fl, q, dk, da)
-    O.partition(kk, [pp], 10)
-    dt = time.perf_counter() - t0
-    return n_fact_sample + n_pairs_sample, dt, (f"oracle (single-threaded C) on fact rows [0,{n_fact_sample}) with the "
-                                                f"full {n_dim}-row dimension, plus {n_pairs_sample} pairs at fan-out 1024")
+class OracleSample:
+    """A bounded, proportionally scaled instance of the step's workload for
+    the CPU oracle: n fact rows with n // 30 dimension rows (the 600M : 20M
+    ratio of the at-scale star), the same distributions and query, and n
+    (key, payload) pairs at the same fan-out.  Generated once; run() times
+    the oracle alone."""
+
+    def __init__(self, n, log2f, n_attr=1000):
+        from oracle import oracle as O
+        from paper_2506_09226_gb300 import datagen
+        self.O, self.n, self.log2f = O, n, log2f
+        self.nd = max(1, n // 30)
+        dim = datagen.star_dim(self.nd, n_attr, seed=1)
+        fact = datagen.star_fact(n, self.nd, seed=1)
+        key, pay = datagen.key_payload_pairs(n, seed=2)
+        self.fl = [fact[c].numpy() for c in COLS]
+        self.q = O.Query(preds=[O.Pred(1, O.LT, DATE_LT)], fk_col=0, key_hi_col=4, key_lo_col=O.JOIN_PAYLOAD,
+                         aggs=[(O.SUM, 2, 3), (O.COUNT, -1, -1), (O.MIN, 2, -1), (O.MAX, 2, -1)])
+        self.dk, self.da, self.kk, self.pp = dim["key"].numpy(), dim["attr"].numpy(), key.numpy(), pay.numpy()
+        O.lib()
+
+    def run(self):
+        """Seconds for one step: the pipeline over the fact sample, then the partition."""
+        t0 = time.perf_counter()
+        self.O.pipeline(self.fl, self.q, self.dk, self.da)
+        self.O.partition(self.kk, [self.pp], self.log2f)
+        return time.perf_counter() - t0
+
+    @property
+    def rows(self):
+        return 2 * self.n
+
+    @property
+    def desc(self):
+        return (f"oracle (single-threaded C): the star pipeline over {self.n} fact rows joined to {self.nd} "
+                f"dimension rows (the 30:1 ratio of the 600M x 20M workload), plus {self.n} pairs partitioned "
+                f"at fan-out {1 << self.log2f}; rows = fact + pairs")
 
 
 # ---------------------------------------------------------------- reference arm
@@ -198,17 +216,17 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    n_fact_s = args.ref_sample
     W, K = args.warmup, args.steps
+    sample = OracleSample(args.ref_sample, args.log2f)
     times = []
-    desc = ""
     for i in range(W + K):
-        rows, dt, desc = oracle_sample(n_fact_s, args.dim_rows, n_fact_s)
+        dt = sample.run()
         if i >= W:
             times.append(dt)
         log(f"reference step {i}: {dt:.2f}s")
     t = sum(times) / len(times)
-    v = rows / t
+    v = sample.rows / t
+    desc = sample.desc
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": K, "warmup": W,
             "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int64", "data": "synthetic", "impl": "reference",
@@ -336,8 +354,11 @@ def run_qe(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        rows, dt, desc_s = oracle_sample(args.ref_sample, args.dim_rows, args.ref_sample)
-        cpu = {"value": rows / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc_s}
+        sample = OracleSample(args.cpu_sample, args.log2f)
+        runs = [sample.run() for _ in range(2)]
+        dt = sum(runs) / len(runs)
+        cpu = {"value": sample.rows / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": sample.desc + f"; mean of 2 runs ({sum(runs):.1f} s of CPU work)"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -492,7 +513,10 @@ def main():
     ap.add_argument("--batch-count", type=int, default=10_000)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-scale", type=float, default=1.0)
-    ap.add_argument("--ref-sample", type=int, default=4_000_000)
+    ap.add_argument("--ref-sample", type=int, default=2_000_000,
+                    help="fact rows (and pairs) per reference-arm step")
+    ap.add_argument("--cpu-sample", type=int, default=24_000_000,
+                    help="fact rows (and pairs) of the cpu_baseline sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
