@@ -47,6 +47,25 @@ struct PartArgs {
     int tma;                  // keys (and the int64 payload) are 16-byte aligned
     int64_t spin_limit;
     qe_dev_status *st;
+    // Write-combining scatter only: which digit of the destination it sorts
+    // by, and where its work items and their output offsets come from.
+    int dshift;               // digit = (destination >> dshift) & dmask
+    uint32_t dmask;
+    int omode;                // WC_SINGLE, WC_PASS1 or WC_PASS2
+    int sub_bits;             // two passes: bits of the second-pass digit
+    int64_t nitems;           // work items (WC_SINGLE / WC_PASS1: one per block range)
+    int g1;                   // two passes: first-pass block ranges
+    const int64_t *t1;        // two passes: [g1][F1] first-pass start of (range, digit)
+    const uint32_t *h1;       // two passes: [g1][F1] rows of (range, digit)
+};
+
+// Work items of the write-combining scatter.
+enum : int {
+    WC_SINGLE = 0,  // one pass: item b = input range b, digit = destination
+    WC_PASS1 = 1,   // first of two passes: item b = input range b, digit = the
+                    // destination's high bits, output = scratch at t1[b][digit]
+    WC_PASS2 = 2,   // second pass: item (q, b) = the scratch rows of input
+                    // range b with high bits q, digit = the low bits
 };
 
 // Histogram of destinations; H_SPLIT blocks share each scatter block's range
@@ -131,7 +150,7 @@ __global__ void __launch_bounds__(1024) k_part_basescan(const int64_t *tot, int6
 
 // ---------------------------------------------------------------------------
 // Write-combining scatter: int64 keys with no payload or one int64 payload,
-// fan-out F <= 512.  A block walks its rows in chunks of T * W_ITEMS;
+// fan-out F <= 512.  A block walks its rows in chunks of T * IT;
 // the next chunk is loaded into registers while the current one is ranked.
 //
 // Ranking is one pass: each warp counts destinations in its own row of the
@@ -148,16 +167,15 @@ __global__ void __launch_bounds__(1024) k_part_basescan(const int64_t *tot, int6
 // most three) until a later chunk fills the sector; only whole sectors are
 // written, except the first and last sector of the block's range, which it
 // shares with the neighbouring blocks.
-constexpr int W_ITEMS = 8;                    // rows per thread per chunk
 constexpr int WC_MAX_LOG2F = 9;
 
-// Shared-memory layout of a block of T threads (chunks of T * W_ITEMS rows).
+// Shared-memory layout of a block of T threads (chunks of T * IT rows).
 struct WcLayout {
     size_t sK, sP, pK, pP, ob, qt, rq, hist, start, cnt, sD, total;
     int FC;                                       // counter row width (even)
-    __host__ __device__ WcLayout(int F, bool pay, int T)
+    __host__ __device__ WcLayout(int F, bool pay, int T, int IT)
     {
-        const size_t f = static_cast<size_t>(F), ch = static_cast<size_t>(T) * W_ITEMS;
+        const size_t f = static_cast<size_t>(F), ch = static_cast<size_t>(T) * IT;
         FC = F < 2 ? 2 : F;
         sK = 0;
         sP = sK + ch * 8;
@@ -174,14 +192,14 @@ struct WcLayout {
     }
 };
 
-template <bool PAY, int T>
-__device__ __forceinline__ void wc_load(const PartArgs &A, int64_t r0, int64_t hi, long long (&k)[W_ITEMS],
-                                        long long (&v)[W_ITEMS])
+template <bool PAY, int IT>
+__device__ __forceinline__ void wc_load(const PartArgs &A, int64_t r0, int64_t hi, long long (&k)[IT],
+                                        long long (&v)[IT])
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-    for (int i = 0; i < W_ITEMS; i++) {
-        const int64_t r = r0 + warp * 32 * W_ITEMS + i * 32 + lane;
+    for (int i = 0; i < IT; i++) {
+        const int64_t r = r0 + warp * 32 * IT + i * 32 + lane;
         k[i] = r < hi ? __ldcs(reinterpret_cast<const long long *>(A.keys) + r) : 0;
         if (PAY) v[i] = r < hi ? __ldcs(static_cast<const long long *>(A.pay[0]) + r) : 0;
     }
@@ -248,16 +266,16 @@ __device__ __forceinline__ void wc_block_scan(const uint32_t *a, uint32_t *out, 
     }
 }
 
-template <bool PAY, int BITS, int T>
-__global__ void __launch_bounds__(T, T <= 256 ? 2 : 1) k_part_scatter_wc(PartArgs A)
+template <bool PAY, int BITS, int T, int IT, int MINB>
+__global__ void __launch_bounds__(T, MINB) k_part_scatter_wc(PartArgs A)
 {
     constexpr int NWARP = T / 32;
-    constexpr int CH = T * W_ITEMS;
+    constexpr int CH = T * IT;
     static_assert(CH < 65536, "counters are 16-bit");
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int s_w[NWARP];
-    const int F = 1 << A.log2f;
-    const WcLayout L(F, PAY, T);
+    const int F = static_cast<int>(A.dmask) + 1;            // digits sorted by this launch
+    const WcLayout L(F, PAY, T, IT);
     const int FC = L.FC;
     long long *sK = reinterpret_cast<long long *>(smem + L.sK);     // sorted chunk keys
     long long *sP = reinterpret_cast<long long *>(smem + L.sP);     // sorted chunk payloads
@@ -273,172 +291,219 @@ __global__ void __launch_bounds__(T, T <= 256 ? 2 : 1) k_part_scatter_wc(PartArg
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1;
-    const int b = blockIdx.x;
-    const int64_t lo = static_cast<int64_t>(b) * A.rows_per_block;
-    const int64_t hi = min(A.n, lo + A.rows_per_block);
-    const int64_t nch = (hi - lo + CH - 1) / CH;
+    const int Ffull = 1 << A.log2f;
     long long *outK = reinterpret_cast<long long *>(A.out_keys);
     // payload address = key address + dP elements
     const int64_t dP = PAY ? static_cast<long long *>(A.out_pay[0]) - outK : 0;
-    // Block b's rows for destination p are the output rows [g, g + n_p).  A
+    // A work item's rows for digit p go to the output rows [g, g + n_p).  A
     // row is numbered q = (its rank among them) - hl, where hl rows fill the
     // key sector that g starts in (0 if g starts one); q = 0 then starts a
     // sector and the sectors are q in [4j, 4j + 4).  Rows with q < 0 share
-    // their sector with the previous block and are written at once.
+    // their sector with the previous item and are written at once.
     const int aoff = static_cast<int>((reinterpret_cast<uintptr_t>(outK) >> 3) & 3);
-
-    for (int p = threadIdx.x; p < F; p += T) {
-        const int64_t g = A.base[p] + A.off[static_cast<int64_t>(b) * F + p];
-        const int hl = static_cast<int>((4 - ((g + aoff) & 3)) & 3);
-        ob[p] = outK + g + hl;
-        rq[p] = -hl;
-    }
     for (int i = threadIdx.x; i < NWARP * FC / 8; i += T) reinterpret_cast<uint4 *>(cnt)[i] = make_uint4(0, 0, 0, 0);
-    long long ck[W_ITEMS], cv[W_ITEMS];
-    wc_load<PAY, T>(A, lo, hi, ck, cv);
-    __syncthreads();
 
-    for (int64_t c = 0; c < nch; c++) {
-        const int64_t r0 = lo + c * CH;
-        const int m = static_cast<int>(hi - r0 < CH ? hi - r0 : CH);
-        long long nk[W_ITEMS], nv[W_ITEMS];
-        wc_load<PAY, T>(A, r0 + CH, hi, nk, nv);     // rows past hi are not read
-
-        // destination and rank among the warp's earlier rows of that destination
-        uint32_t dg[W_ITEMS], rk[W_ITEMS];
-#pragma unroll
-        for (int i = 0; i < W_ITEMS; i++) {
-            const bool valid = warp * 32 * W_ITEMS + i * 32 + lane < m;
-            const uint32_t d = valid ? dev_part_id(ck[i], A.log2f, A.mode, A.shift) : 0u;
-            const unsigned peers = match_label<BITS>(d, __ballot_sync(QE_FULL_MASK, valid));
-            uint16_t *cp = cnt + warp * FC + d;
-            uint32_t basec = 0;
-            if (valid) basec = *cp;
-            __syncwarp();
-            if (valid && lane == __ffs(peers) - 1) *cp = static_cast<uint16_t>(basec + __popc(peers));
-            __syncwarp();
-            dg[i] = valid ? d : 0xffffffffu;
-            rk[i] = basec + __popc(peers & lt);
+    for (int64_t item = blockIdx.x; item < A.nitems; item += gridDim.x) {
+        int64_t lo, hi;
+        int b = static_cast<int>(item), qhi = 0;
+        if (A.omode == WC_PASS2) {
+            qhi = static_cast<int>(item / A.g1);
+            b = static_cast<int>(item % A.g1);
+            const int64_t j = static_cast<int64_t>(b) * (Ffull >> A.sub_bits) + qhi;
+            lo = A.t1[j];
+            hi = lo + A.h1[j];
+        } else {
+            lo = static_cast<int64_t>(b) * A.rows_per_block;
+            hi = min(A.n, lo + A.rows_per_block);
         }
-        __syncthreads();
-        // per destination pair (two 16-bit counters in a word): prefix over
-        // warps and totals; both halves stay below 2^16
-        {
-            uint32_t *cw = reinterpret_cast<uint32_t *>(cnt);
-            const int FW = FC / 2;
-            if (NWARP * FW <= T) {
-                // one thread per (pair, warp); the warps of a pair are
-                // NWARP consecutive lanes, scanned with shuffles
-                const int j = threadIdx.x / NWARP, w = threadIdx.x % NWARP;
-                const bool on = j < FW;
-                const uint32_t x = on ? cw[w * FW + j] : 0u;
-                uint32_t inc = x;
-#pragma unroll
-                for (int o = 1; o < NWARP; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(QE_FULL_MASK, inc, o, NWARP);
-                    if (w >= o) inc += y;
-                }
-                if (on) {
-                    cw[w * FW + j] = inc - x;
-                    if (w == NWARP - 1) {
-                        if (2 * j < F) hist[2 * j] = inc & 0xffffu;
-                        if (2 * j + 1 < F) hist[2 * j + 1] = inc >> 16;
-                    }
-                }
+        const int64_t nch = (hi - lo + CH - 1) / CH;
+        __syncthreads();                              // the previous item's tables are done with
+        for (int p = threadIdx.x; p < F; p += T) {
+            int64_t g;
+            if (A.omode == WC_SINGLE) {
+                g = A.base[p] + A.off[static_cast<int64_t>(b) * Ffull + p];
+            } else if (A.omode == WC_PASS1) {
+                g = A.t1[static_cast<int64_t>(b) * F + p];
             } else {
-                for (int j = threadIdx.x; j < FW; j += T) {
-                    uint32_t tot = 0;
+                const int dst = (qhi << A.sub_bits) | p;
+                g = A.base[dst] + A.off[static_cast<int64_t>(b) * Ffull + dst];
+            }
+            const int hl = static_cast<int>((4 - ((g + aoff) & 3)) & 3);
+            ob[p] = outK + g + hl;
+            rq[p] = -hl;
+        }
+        long long ck[IT], cv[IT];
+        wc_load<PAY, IT>(A, lo, hi, ck, cv);
+        __syncthreads();
+
+        for (int64_t c = 0; c < nch; c++) {
+            const int64_t r0 = lo + c * CH;
+            const int m = static_cast<int>(hi - r0 < CH ? hi - r0 : CH);
+            long long nk[IT], nv[IT];
+            wc_load<PAY, IT>(A, r0 + CH, hi, nk, nv);    // rows past hi are not read
+
+            // digit and rank among the warp's earlier rows of that digit
+            uint32_t dg[IT], rk[IT];
 #pragma unroll
-                    for (int w = 0; w < NWARP; w++) {
-                        const uint32_t x = cw[w * FW + j];
-                        cw[w * FW + j] = tot;
-                        tot += x;
+            for (int i = 0; i < IT; i++) {
+                const bool valid = warp * 32 * IT + i * 32 + lane < m;
+                const uint32_t d =
+                    valid ? (dev_part_id(ck[i], A.log2f, A.mode, A.shift) >> A.dshift) & A.dmask : 0u;
+                const unsigned peers = match_label<BITS>(d, __ballot_sync(QE_FULL_MASK, valid));
+                uint16_t *cp = cnt + warp * FC + d;
+                uint32_t basec = 0;
+                if (valid) basec = *cp;
+                __syncwarp();
+                if (valid && lane == __ffs(peers) - 1) *cp = static_cast<uint16_t>(basec + __popc(peers));
+                __syncwarp();
+                dg[i] = valid ? d : 0xffffffffu;
+                rk[i] = basec + __popc(peers & lt);
+            }
+            __syncthreads();
+            // per digit pair (two 16-bit counters in a word): prefix over
+            // warps and totals; both halves stay below 2^16
+            {
+                uint32_t *cw = reinterpret_cast<uint32_t *>(cnt);
+                const int FW = FC / 2;
+                if (NWARP * FW <= T) {
+                    // one thread per (pair, warp); the warps of a pair are
+                    // NWARP consecutive lanes, scanned with shuffles
+                    const int j = threadIdx.x / NWARP, w = threadIdx.x % NWARP;
+                    const bool on = j < FW;
+                    const uint32_t x = on ? cw[w * FW + j] : 0u;
+                    uint32_t inc = x;
+#pragma unroll
+                    for (int o = 1; o < NWARP; o <<= 1) {
+                        const uint32_t y = __shfl_up_sync(QE_FULL_MASK, inc, o, NWARP);
+                        if (w >= o) inc += y;
                     }
-                    if (2 * j < F) hist[2 * j] = tot & 0xffffu;
-                    if (2 * j + 1 < F) hist[2 * j + 1] = tot >> 16;
+                    if (on) {
+                        cw[w * FW + j] = inc - x;
+                        if (w == NWARP - 1) {
+                            if (2 * j < F) hist[2 * j] = inc & 0xffffu;
+                            if (2 * j + 1 < F) hist[2 * j + 1] = inc >> 16;
+                        }
+                    }
+                } else {
+                    for (int j = threadIdx.x; j < FW; j += T) {
+                        uint32_t tot = 0;
+#pragma unroll
+                        for (int w = 0; w < NWARP; w++) {
+                            const uint32_t x = cw[w * FW + j];
+                            cw[w * FW + j] = tot;
+                            tot += x;
+                        }
+                        if (2 * j < F) hist[2 * j] = tot & 0xffffu;
+                        if (2 * j + 1 < F) hist[2 * j + 1] = tot >> 16;
+                    }
                 }
             }
+            __syncthreads();
+            wc_block_scan<T>(hist, start, F, s_w);
+            __syncthreads();
+            for (int p = threadIdx.x; p < F; p += T) {
+                const int r = rq[p];
+                const int h = static_cast<int>(hist[p]);
+                const int e = r + h;
+                const int r4 = r & ~3, e4 = e & ~3;
+                const int np = r > 0 ? (r & 3) : 0;
+                if (np && e4 > r4) {
+                    // this chunk completes the pending sector: write its earlier rows
+                    long long *o = ob[p] + r4;
+                    for (int j = 0; j < np; j++) {
+                        __stcs(o + j, pK[p * 3 + j]);
+                        if (PAY) __stcs(o + dP + j, pP[p * 3 + j]);
+                    }
+                }
+                const int lim = e4 > 0 ? e4 : 0;          // rows with q < lim are written now
+                const int k = lim - r;                    // of this chunk's h rows, the first k
+                const int st = static_cast<int>(start[p]);
+                qt[p] = make_int2(r - st, st + (k < 0 ? 0 : (k > h ? h : k)));
+                rq[p] = e;
+            }
+#pragma unroll
+            for (int i = 0; i < IT; i++) {
+                if (dg[i] != 0xffffffffu) {
+                    const uint32_t pos = start[dg[i]] + cnt[warp * FC + dg[i]] + rk[i];
+                    sK[pos] = ck[i];
+                    if (PAY) sP[pos] = cv[i];
+                    sD[pos] = static_cast<uint16_t>(dg[i]);
+                }
+            }
+            __syncthreads();
+            for (int t = threadIdx.x; t < m; t += T) {
+                const int p = sD[t];
+                const int2 x = qt[p];
+                const int q = x.x + t;
+                if (t < x.y) {
+                    long long *o = ob[p] + q;
+                    __stcs(o, sK[t]);
+                    if (PAY) __stcs(o + dP, sP[t]);
+                } else {
+                    pK[p * 3 + (q & 3)] = sK[t];
+                    if (PAY) pP[p * 3 + (q & 3)] = sP[t];
+                }
+            }
+            for (int i = threadIdx.x; i < NWARP * FC / 8; i += T) reinterpret_cast<uint4 *>(cnt)[i] = make_uint4(0, 0, 0, 0);
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < IT; i++) {
+                ck[i] = nk[i];
+                if (PAY) cv[i] = nv[i];
+            }
         }
-        __syncthreads();
-        wc_block_scan<T>(hist, start, F, s_w);
-        __syncthreads();
+        // rows still pending at the end of the item
         for (int p = threadIdx.x; p < F; p += T) {
             const int r = rq[p];
-            const int h = static_cast<int>(hist[p]);
-            const int e = r + h;
-            const int r4 = r & ~3, e4 = e & ~3;
             const int np = r > 0 ? (r & 3) : 0;
-            if (np && e4 > r4) {
-                // this chunk completes the pending sector: write its earlier rows
-                long long *o = ob[p] + r4;
-                for (int j = 0; j < np; j++) {
-                    __stcs(o + j, pK[p * 3 + j]);
-                    if (PAY) __stcs(o + dP + j, pP[p * 3 + j]);
-                }
+            long long *o = ob[p] + (r & ~3);
+            for (int j = 0; j < np; j++) {
+                __stcs(o + j, pK[p * 3 + j]);
+                if (PAY) __stcs(o + dP + j, pP[p * 3 + j]);
             }
-            const int lim = e4 > 0 ? e4 : 0;          // rows with q < lim are written now
-            const int k = lim - r;                    // of this chunk's h rows, the first k
-            const int st = static_cast<int>(start[p]);
-            qt[p] = make_int2(r - st, st + (k < 0 ? 0 : (k > h ? h : k)));
-            rq[p] = e;
-        }
-#pragma unroll
-        for (int i = 0; i < W_ITEMS; i++) {
-            if (dg[i] != 0xffffffffu) {
-                const uint32_t pos = start[dg[i]] + cnt[warp * FC + dg[i]] + rk[i];
-                sK[pos] = ck[i];
-                if (PAY) sP[pos] = cv[i];
-                sD[pos] = static_cast<uint16_t>(dg[i]);
-            }
-        }
-        __syncthreads();
-        for (int t = threadIdx.x; t < m; t += T) {
-            const int p = sD[t];
-            const int2 x = qt[p];
-            const int q = x.x + t;
-            if (t < x.y) {
-                long long *o = ob[p] + q;
-                __stcs(o, sK[t]);
-                if (PAY) __stcs(o + dP, sP[t]);
-            } else {
-                pK[p * 3 + (q & 3)] = sK[t];
-                if (PAY) pP[p * 3 + (q & 3)] = sP[t];
-            }
-        }
-        for (int i = threadIdx.x; i < NWARP * FC / 8; i += T) reinterpret_cast<uint4 *>(cnt)[i] = make_uint4(0, 0, 0, 0);
-        __syncthreads();
-#pragma unroll
-        for (int i = 0; i < W_ITEMS; i++) {
-            ck[i] = nk[i];
-            if (PAY) cv[i] = nv[i];
-        }
-    }
-    // rows still pending at the end of the range
-    for (int p = threadIdx.x; p < F; p += T) {
-        const int r = rq[p];
-        const int np = r > 0 ? (r & 3) : 0;
-        long long *o = ob[p] + (r & ~3);
-        for (int j = 0; j < np; j++) {
-            __stcs(o + j, pK[p * 3 + j]);
-            if (PAY) __stcs(o + dP + j, pP[p * 3 + j]);
         }
     }
 }
 
-// Threads per block of the write-combining scatter.  Two blocks of 256 per SM
-// let one block's per-destination phases overlap the other's row phases, but
-// double the output pages an SM writes at a time (one per destination and
-// column per block); beyond a few hundred pages per SM the address
-// translation caches miss and the scatter slows down, so larger fan-outs run
-// one block of 512 per SM.
-inline int wc_threads(int log2f) { return log2f <= 6 ? 256 : 512; }
+// Two passes: per first-pass range b and high digit q, the rows and the
+// scratch start: h1[b][q] = sum over the low digits r of hist[b][q, r] and
+// t1[b][q] = base[q, 0] + sum over r of off[b][q, r] (range b's rows with
+// high digit q follow those of the earlier ranges, inside the run of q).
+__global__ void k_part_two_pass_tables(const uint32_t *hist, const int64_t *off, const int64_t *base, int G, int F,
+                                       int sub_bits, int64_t *t1, uint32_t *h1)
+{
+    const int F1 = F >> sub_bits, F2 = 1 << sub_bits;
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= static_cast<int64_t>(G) * F1) return;
+    const int b = static_cast<int>(i / F1), q = static_cast<int>(i % F1);
+    uint32_t h = 0;
+    int64_t o = 0;
+    for (int r = 0; r < F2; r++) {
+        const int64_t j = static_cast<int64_t>(b) * F + (q << sub_bits) + r;
+        h += hist[j];
+        o += off[j];
+    }
+    h1[i] = h;
+    t1[i] = base[q << sub_bits] + o;
+}
+
+// Block shapes of the write-combining scatter, by fan-out.  Several blocks
+// per SM let one block's per-destination phases overlap another's row
+// phases, but every block writes one output page per destination and
+// column at a time; beyond a few hundred pages per SM the address
+// translation caches miss and the scatter slows down, so larger fan-outs
+// run a single block of 512 per SM.
+struct WcShape {
+    int threads, items;
+    const void *kernel;
+};
 
 template <bool PAY>
-static const void *wc_kernel(int log2f)
+static WcShape wc_shape(int log2f)
 {
-    if (log2f <= 6) return reinterpret_cast<const void *>(k_part_scatter_wc<PAY, 6, 256>);
-    if (log2f <= 8) return reinterpret_cast<const void *>(k_part_scatter_wc<PAY, 8, 512>);
-    return reinterpret_cast<const void *>(k_part_scatter_wc<PAY, 10, 512>);
+    if (log2f <= 6) return {256, 8, reinterpret_cast<const void *>(k_part_scatter_wc<PAY, 6, 256, 8, 2>)};
+    if (log2f <= 8) return {512, 8, reinterpret_cast<const void *>(k_part_scatter_wc<PAY, 8, 512, 8, 1>)};
+    return {512, 8, reinterpret_cast<const void *>(k_part_scatter_wc<PAY, 10, 512, 8, 1>)};
 }
 
 // General scatter (any payload columns, any fan-out up to 4096), at 1024
@@ -491,26 +556,39 @@ extern "C" qe_status qe_partition(qe_ctx *ctx, const int64_t *keys, const qe_col
         return QE_OK;
     }
     const bool fast = npayload == 1 && A.pay_type[0] == QE_I64 && qe_aligned(A.pay[0], 8);
-    // write-combining scatter when the payload allows it and its tables fit
-    const int wt = wc_threads(log2_fanout);
-    const bool wc = !ctx->tune_part_general && log2_fanout <= WC_MAX_LOG2F && (npayload == 0 || fast) &&
-                    WcLayout(F, fast, wt).total <= ctx->smem_optin;
+    // Plan.  The write-combining scatter takes keys with one int64 payload or
+    // none: in one pass up to fan-out 2^WC_MAX_LOG2F, and in two passes of
+    // at most 64 digits each beyond (the first by the high bits of the
+    // destination into scratch, the second by the low bits), which keeps the
+    // output pages an SM writes at a time within the translation caches.
+    // Everything else takes the general scatter.
+    const bool wc = !ctx->tune_part_general && (npayload == 0 || fast);
+    const bool two = wc && log2_fanout > WC_MAX_LOG2F;
+    const int sub_bits = two ? log2_fanout / 2 : 0;
+    const int F1 = F >> sub_bits;
+    const WcShape ws = fast ? wc_shape<true>(log2_fanout - sub_bits) : wc_shape<false>(log2_fanout - sub_bits);
+    const WcShape ws2 = fast ? wc_shape<true>(sub_bits) : wc_shape<false>(sub_bits);
     const bool big = gen1024::scatter_smem(log2_fanout, fast) <= ctx->smem_optin;
-    const size_t smem = wc ? WcLayout(F, fast, wt).total
+    const size_t smem = wc ? WcLayout(F1, fast, ws.threads, ws.items).total
                            : (big ? gen1024::scatter_smem(log2_fanout, fast) : gen512::scatter_smem(log2_fanout, fast));
-    if (smem > ctx->smem_optin) return qe_fail(ctx, QE_ERR_INVALID_ARG, "partition: fan-out too large");
+    const size_t smem2 = two ? WcLayout(1 << sub_bits, fast, ws2.threads, ws2.items).total : 0;
+    if (smem > ctx->smem_optin || smem2 > ctx->smem_optin)
+        return qe_fail(ctx, QE_ERR_INVALID_ARG, "partition: fan-out too large");
     const void *kscatter;
     if (wc)
-        kscatter = fast ? wc_kernel<true>(log2_fanout) : wc_kernel<false>(log2_fanout);
+        kscatter = ws.kernel;
     else if (big)
         kscatter = fast ? reinterpret_cast<const void *>(gen1024::k_part_scatter<true>)
                         : reinterpret_cast<const void *>(gen1024::k_part_scatter<false>);
     else
         kscatter = fast ? reinterpret_cast<const void *>(gen512::k_part_scatter<true>)
                         : reinterpret_cast<const void *>(gen512::k_part_scatter<false>);
-    const int threads = wc ? wt : (big ? gen1024::PT : gen512::PT);
-    const int64_t chunk = wc ? static_cast<int64_t>(wt) * W_ITEMS : (big ? gen1024::CHUNK : gen512::CHUNK);
-    QE_CUDA(ctx, cudaFuncSetAttribute(kscatter, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    const int threads = wc ? ws.threads : (big ? gen1024::PT : gen512::PT);
+    const int64_t chunk = wc ? static_cast<int64_t>(ws.threads) * ws.items : (big ? gen1024::CHUNK : gen512::CHUNK);
+    // (both passes may use the same kernel: allow the larger footprint)
+    const size_t smem_attr = two && ws2.kernel == kscatter && smem2 > smem ? smem2 : smem;
+    QE_CUDA(ctx, cudaFuncSetAttribute(kscatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(smem_attr)));
     int per_sm = 0;
     QE_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kscatter, threads, smem));
     if (per_sm < 1) per_sm = 1;
@@ -523,20 +601,39 @@ extern "C" qe_status qe_partition(qe_ctx *ctx, const int64_t *keys, const qe_col
     A.tma = !wc && qe_aligned(keys, 16) && (!fast || qe_aligned(A.pay[0], 16));
     A.spin_limit = ctx->spin_limit;
     A.st = ctx->dstat;
+    int64_t G2 = 0;
+    if (two) {
+        if (ws2.kernel != kscatter)
+            QE_CUDA(ctx, cudaFuncSetAttribute(ws2.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              static_cast<int>(smem2)));
+        int per_sm2 = 0;
+        QE_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, ws2.kernel, ws2.threads, smem2));
+        G2 = static_cast<int64_t>(ctx->num_sms) * (per_sm2 < 1 ? 1 : per_sm2);
+    }
 
+    // scratch: hist | off | tot, and for two passes t1 | h1 | keys | payload
+    auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t hist_bytes = up(static_cast<size_t>(G) * F * sizeof(uint32_t));
+    const size_t off_bytes = up(static_cast<size_t>(G) * F * sizeof(int64_t));
+    const size_t tot_bytes = up(static_cast<size_t>(F) * sizeof(int64_t));
+    const size_t t1_bytes = two ? up(static_cast<size_t>(G) * F1 * sizeof(int64_t)) : 0;
+    const size_t h1_bytes = two ? up(static_cast<size_t>(G) * F1 * sizeof(uint32_t)) : 0;
+    const size_t col_bytes = two ? up(static_cast<size_t>(nrows) * sizeof(int64_t)) : 0;
     void *scratch = nullptr;
-    const size_t hist_bytes = static_cast<size_t>(G) * F * sizeof(uint32_t);
-    const size_t off_bytes = static_cast<size_t>(G) * F * sizeof(int64_t);
-    const size_t tot_bytes = static_cast<size_t>(F) * sizeof(int64_t);
-    qe_status st = qe_alloc(ctx, &scratch, hist_bytes + off_bytes + tot_bytes + 64, s);
+    qe_status st = qe_alloc(ctx, &scratch,
+                            hist_bytes + off_bytes + tot_bytes + t1_bytes + h1_bytes + col_bytes * (fast ? 2 : 1), s);
     if (st != QE_OK) return st;
     unsigned char *sp = static_cast<unsigned char *>(scratch);
     A.off = reinterpret_cast<int64_t *>(sp);
     int64_t *tot = reinterpret_cast<int64_t *>(sp + off_bytes);
     A.hist = reinterpret_cast<uint32_t *>(sp + off_bytes + tot_bytes);
     A.base = out_offsets;
+    int64_t *t1 = reinterpret_cast<int64_t *>(sp + off_bytes + tot_bytes + hist_bytes);
+    uint32_t *h1 = reinterpret_cast<uint32_t *>(sp + off_bytes + tot_bytes + hist_bytes + t1_bytes);
+    int64_t *tmpK = reinterpret_cast<int64_t *>(sp + off_bytes + tot_bytes + hist_bytes + t1_bytes + h1_bytes);
+    int64_t *tmpP = tmpK + col_bytes / sizeof(int64_t);
 
-    cudaError_t e = cudaMemsetAsync(A.hist, 0, hist_bytes, s);
+    cudaError_t e = cudaMemsetAsync(A.hist, 0, static_cast<size_t>(G) * F * sizeof(uint32_t), s);
     if (e == cudaSuccess) {
         ProfScope prof(ctx, "part_hist", s);
         k_part_hist<<<static_cast<unsigned>(G * H_SPLIT), HT, F * sizeof(uint32_t), s>>>(A);
@@ -552,11 +649,44 @@ extern "C" qe_status qe_partition(qe_ctx *ctx, const int64_t *keys, const qe_col
         QE_LAUNCHED(ctx);
         e = cudaGetLastError();
     }
+    if (e == cudaSuccess && two) {
+        const int64_t cells = G * F1;
+        k_part_two_pass_tables<<<static_cast<unsigned>((cells + 255) / 256), 256, 0, s>>>(
+            A.hist, A.off, out_offsets, static_cast<int>(G), F, sub_bits, t1, h1);
+        QE_LAUNCHED(ctx);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) {
         ProfScope prof(ctx, "part_scatter", s);
-        void *args[] = {&A};
+        PartArgs A1 = A;
+        A1.dshift = sub_bits;
+        A1.dmask = static_cast<uint32_t>(F1 - 1);
+        A1.omode = two ? WC_PASS1 : WC_SINGLE;
+        A1.nitems = G;
+        if (two) {
+            A1.t1 = t1;
+            A1.out_keys = tmpK;
+            if (fast) A1.out_pay[0] = tmpP;
+        }
+        void *args[] = {&A1};
         e = cudaLaunchKernel(kscatter, dim3(static_cast<unsigned>(G)), dim3(threads), args, smem, s);
         QE_LAUNCHED(ctx);
+        if (e == cudaSuccess && two) {
+            PartArgs A2 = A;
+            A2.keys = tmpK;
+            if (fast) A2.pay[0] = tmpP;
+            A2.dshift = 0;
+            A2.dmask = static_cast<uint32_t>((1 << sub_bits) - 1);
+            A2.omode = WC_PASS2;
+            A2.sub_bits = sub_bits;
+            A2.g1 = static_cast<int>(G);
+            A2.t1 = t1;
+            A2.h1 = h1;
+            A2.nitems = G * F1;
+            void *args2[] = {&A2};
+            e = cudaLaunchKernel(ws2.kernel, dim3(static_cast<unsigned>(G2)), dim3(ws2.threads), args2, smem2, s);
+            QE_LAUNCHED(ctx);
+        }
         if (e == cudaSuccess) e = cudaGetLastError();
     }
     qe_free(ctx, scratch, s);

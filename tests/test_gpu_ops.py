@@ -92,7 +92,7 @@ def _check_partition(ctx, keys, pays, log2f, mode=qe.PART_HASH, shift=0):
         assert np.array_equal(a.cpu().numpy(), b)
 
 
-@pytest.mark.parametrize("log2f", [0, 1, 5, 8, 10, 12])
+@pytest.mark.parametrize("log2f", [0, 1, 5, 8, 9, 10, 11, 12])
 @pytest.mark.parametrize("n", [1, 33, 4097, 123_457])
 def test_partition_hash_fast_path(ctx, n, log2f):
     k, p = datagen.key_payload_pairs(n, seed=log2f)
@@ -110,11 +110,11 @@ def test_partition_radix_generic_payloads(ctx, log2f, shift):
     _check_partition(ctx, keys, [], log2f, qe.PART_RADIX, shift)
 
 
-@pytest.mark.parametrize("log2f", [3, 10])
+@pytest.mark.parametrize("log2f", [3, 10, 11, 12])
 def test_partition_many_chunks_per_block(ctx, log2f):
     """Several chunks per block, so the rows a block holds back for an
     incomplete output sector are carried across chunks; keys only and with
-    one payload."""
+    one payload.  Fan-outs above 512 take two passes."""
     n = 3_000_001
     k, p = datagen.key_payload_pairs(n, seed=77)
     _check_partition(ctx, k.numpy(), [p.numpy()], log2f)
