@@ -342,49 +342,177 @@ __global__ void __launch_bounds__(T, MINB) k_part_scatter_wc(PartArgs A)
             long long nk[IT], nv[IT];
             wc_load<PAY, IT>(A, r0 + CH, hi, nk, nv);    // rows past hi are not read
 
-            // digit and rank among the warp's earlier rows of that digit
             uint32_t dg[IT], rk[IT];
+            if constexpr (BITS <= 6) {
+                // ---- up to 64 digits: register counters, every warp scans
+                // the counter matrix itself and owns digits p == warp
+                // (mod NWARP): their running offsets, pending rows and
+                // output runs.
+                constexpr int NCL = BITS > 5 ? 2 : 1;     // digits per lane: lane, lane + 32
+                uint32_t cl[NCL];
 #pragma unroll
-            for (int i = 0; i < IT; i++) {
-                const bool valid = warp * 32 * IT + i * 32 + lane < m;
-                const uint32_t d =
-                    valid ? (dev_part_id(ck[i], A.log2f, A.mode, A.shift) >> A.dshift) & A.dmask : 0u;
-                const unsigned peers = match_label<BITS>(d, __ballot_sync(QE_FULL_MASK, valid));
-                uint16_t *cp = cnt + warp * FC + d;
-                uint32_t basec = 0;
-                if (valid) basec = *cp;
-                __syncwarp();
-                if (valid && lane == __ffs(peers) - 1) *cp = static_cast<uint16_t>(basec + __popc(peers));
-                __syncwarp();
-                dg[i] = valid ? d : 0xffffffffu;
-                rk[i] = basec + __popc(peers & lt);
-            }
-            __syncthreads();
-            // per digit pair (two 16-bit counters in a word): prefix over
-            // warps and totals; both halves stay below 2^16
-            {
-                uint32_t *cw = reinterpret_cast<uint32_t *>(cnt);
-                const int FW = FC / 2;
-                if (NWARP * FW <= T) {
-                    // one thread per (pair, warp); the warps of a pair are
-                    // NWARP consecutive lanes, scanned with shuffles
-                    const int j = threadIdx.x / NWARP, w = threadIdx.x % NWARP;
-                    const bool on = j < FW;
-                    const uint32_t x = on ? cw[w * FW + j] : 0u;
-                    uint32_t inc = x;
+                for (int k = 0; k < NCL; k++) cl[k] = 0;
+                // digit and rank among the warp's earlier rows of that digit:
+                // lane e computes which lanes hold digit e (AND over bits of
+                // the bit ballots or their complements); a row reads its
+                // peers and its base count from lane (digit & 31)
 #pragma unroll
-                    for (int o = 1; o < NWARP; o <<= 1) {
-                        const uint32_t y = __shfl_up_sync(QE_FULL_MASK, inc, o, NWARP);
-                        if (w >= o) inc += y;
+                for (int i = 0; i < IT; i++) {
+                    const bool valid = m == CH || warp * 32 * IT + i * 32 + lane < m;
+                    const uint32_t d =
+                        valid ? (dev_part_id(ck[i], A.log2f, A.mode, A.shift) >> A.dshift) & A.dmask : 0u;
+                    unsigned me = m == CH ? QE_FULL_MASK : __ballot_sync(QE_FULL_MASK, valid);
+#pragma unroll
+                    for (int bit = 0; bit < (BITS < 5 ? BITS : 5); bit++) {
+                        const unsigned set = __ballot_sync(QE_FULL_MASK, (d >> bit) & 1u);
+                        me &= ((lane >> bit) & 1) ? set : ~set;
                     }
-                    if (on) {
-                        cw[w * FW + j] = inc - x;
-                        if (w == NWARP - 1) {
-                            if (2 * j < F) hist[2 * j] = inc & 0xffffu;
-                            if (2 * j + 1 < F) hist[2 * j + 1] = inc >> 16;
+                    unsigned me1 = 0;
+                    if (BITS > 5) {
+                        const unsigned set5 = __ballot_sync(QE_FULL_MASK, (d >> 5) & 1u);
+                        me1 = me & set5;
+                        me &= ~set5;
+                    }
+                    const int src = static_cast<int>(d & 31u);
+                    unsigned peers = __shfl_sync(QE_FULL_MASK, me, src);
+                    uint32_t basec = __shfl_sync(QE_FULL_MASK, cl[0], src);
+                    if (BITS > 5) {
+                        const unsigned peers1 = __shfl_sync(QE_FULL_MASK, me1, src);
+                        const uint32_t base1 = __shfl_sync(QE_FULL_MASK, cl[NCL - 1], src);
+                        if (d >= 32u) {
+                            peers = peers1;
+                            basec = base1;
                         }
                     }
-                } else {
+                    cl[0] += __popc(me);
+                    if (BITS > 5) cl[NCL - 1] += __popc(me1);
+                    dg[i] = valid ? d : 0xffffffffu;
+                    rk[i] = basec + __popc(peers & lt);
+                }
+#pragma unroll
+                for (int k = 0; k < NCL; k++)
+                    if (lane + 32 * k < F) cnt[warp * FC + lane + 32 * k] = static_cast<uint16_t>(cl[k]);
+                __syncthreads();
+                // per digit: rows of earlier warps (pre), the chunk's total
+                // (tot) and the digit's first sorted position (st)
+                uint32_t pre[NCL], tot[NCL], st[NCL];
+#pragma unroll
+                for (int k = 0; k < NCL; k++) {
+                    pre[k] = 0;
+                    tot[k] = 0;
+                    const int d = lane + 32 * k;
+                    if (d < F) {
+#pragma unroll
+                        for (int w = 0; w < NWARP; w++) {
+                            const uint32_t x = cnt[w * FC + d];
+                            pre[k] += w < warp ? x : 0u;
+                            tot[k] += x;
+                        }
+                    }
+                }
+                {
+                    const uint32_t inc0 = warp_incl_scan(tot[0]);
+                    st[0] = inc0 - tot[0];
+                    if (BITS > 5) {
+                        const uint32_t all0 = __shfl_sync(QE_FULL_MASK, inc0, 31);
+                        const uint32_t inc1 = warp_incl_scan(tot[NCL - 1]);
+                        st[NCL - 1] = all0 + inc1 - tot[NCL - 1];
+                    }
+                }
+                // the owned digits' running offsets; a chunk that completes a
+                // pending sector writes the sector's earlier rows
+#pragma unroll
+                for (int k = 0; k < NCL; k++) {
+                    const int d = lane + 32 * k;
+                    if (d < F && d % NWARP == warp) {
+                        const int r = rq[d];
+                        const int h = static_cast<int>(tot[k]);
+                        const int e = r + h;
+                        const int r4 = r & ~3, e4 = e & ~3;
+                        const int np = r > 0 ? (r & 3) : 0;
+                        if (np && e4 > r4) {
+                            long long *o = ob[d] + r4;
+                            for (int j = 0; j < np; j++) {
+                                __stcs(o + j, pK[d * 3 + j]);
+                                if (PAY) __stcs(o + dP + j, pP[d * 3 + j]);
+                            }
+                        }
+                        const int lim = e4 > 0 ? e4 : 0;
+                        const int kk = lim - r;
+                        const int s0 = static_cast<int>(st[k]);
+                        qt[d] = make_int2(r - s0, s0 + (kk < 0 ? 0 : (kk > h ? h : kk)));
+                        start[d] = st[k];
+                        hist[d] = tot[k];
+                        rq[d] = e;
+                    }
+                }
+                // rows to their sorted positions, (key, payload) as one element
+                uint32_t o0 = st[0] + pre[0], o1 = BITS > 5 ? st[NCL - 1] + pre[NCL - 1] : 0u;
+#pragma unroll
+                for (int i = 0; i < IT; i++) {
+                    const int src = static_cast<int>(dg[i] & 31u);
+                    uint32_t pos = __shfl_sync(QE_FULL_MASK, o0, src);
+                    if (BITS > 5) {
+                        const uint32_t pos1 = __shfl_sync(QE_FULL_MASK, o1, src);
+                        if (dg[i] >= 32u && dg[i] != 0xffffffffu) pos = pos1;
+                    }
+                    if (dg[i] != 0xffffffffu) {
+                        pos += rk[i];
+                        if (PAY)
+                            reinterpret_cast<longlong2 *>(sK)[pos] = make_longlong2(ck[i], cv[i]);
+                        else
+                            sK[pos] = ck[i];
+                    }
+                }
+                __syncthreads();
+                // each warp writes its digits' runs
+                for (int p = warp; p < F; p += NWARP) {
+                    const int s0 = static_cast<int>(start[p]), h = static_cast<int>(hist[p]);
+                    const int2 x = qt[p];
+                    long long *o = ob[p];
+                    for (int t = s0 + lane; t < s0 + h; t += 32) {
+                        const int q = x.x + t;
+                        long long k, v = 0;
+                        if (PAY) {
+                            const longlong2 kv = reinterpret_cast<const longlong2 *>(sK)[t];
+                            k = kv.x;
+                            v = kv.y;
+                        } else {
+                            k = sK[t];
+                        }
+                        if (t < x.y) {
+                            __stcs(o + q, k);
+                            if (PAY) __stcs(o + q + dP, v);
+                        } else {
+                            pK[p * 3 + (q & 3)] = k;
+                            if (PAY) pP[p * 3 + (q & 3)] = v;
+                        }
+                    }
+                }
+                __syncthreads();
+            } else {
+                // ---- many digits: shared-memory counters per warp
+#pragma unroll
+                for (int i = 0; i < IT; i++) {
+                    const bool valid = warp * 32 * IT + i * 32 + lane < m;
+                    const uint32_t d =
+                        valid ? (dev_part_id(ck[i], A.log2f, A.mode, A.shift) >> A.dshift) & A.dmask : 0u;
+                    const unsigned peers = match_label<BITS>(d, __ballot_sync(QE_FULL_MASK, valid));
+                    uint16_t *cp = cnt + warp * FC + d;
+                    uint32_t basec = 0;
+                    if (valid) basec = *cp;
+                    __syncwarp();
+                    if (valid && lane == __ffs(peers) - 1) *cp = static_cast<uint16_t>(basec + __popc(peers));
+                    __syncwarp();
+                    dg[i] = valid ? d : 0xffffffffu;
+                    rk[i] = basec + __popc(peers & lt);
+                }
+                __syncthreads();
+                // per digit pair (two 16-bit counters in a word): prefix over
+                // warps and totals; both halves stay below 2^16
+                {
+                    uint32_t *cw = reinterpret_cast<uint32_t *>(cnt);
+                    const int FW = FC / 2;
                     for (int j = threadIdx.x; j < FW; j += T) {
                         uint32_t tot = 0;
 #pragma unroll
@@ -397,55 +525,56 @@ __global__ void __launch_bounds__(T, MINB) k_part_scatter_wc(PartArgs A)
                         if (2 * j + 1 < F) hist[2 * j + 1] = tot >> 16;
                     }
                 }
-            }
-            __syncthreads();
-            wc_block_scan<T>(hist, start, F, s_w);
-            __syncthreads();
-            for (int p = threadIdx.x; p < F; p += T) {
-                const int r = rq[p];
-                const int h = static_cast<int>(hist[p]);
-                const int e = r + h;
-                const int r4 = r & ~3, e4 = e & ~3;
-                const int np = r > 0 ? (r & 3) : 0;
-                if (np && e4 > r4) {
-                    // this chunk completes the pending sector: write its earlier rows
-                    long long *o = ob[p] + r4;
-                    for (int j = 0; j < np; j++) {
-                        __stcs(o + j, pK[p * 3 + j]);
-                        if (PAY) __stcs(o + dP + j, pP[p * 3 + j]);
+                __syncthreads();
+                wc_block_scan<T>(hist, start, F, s_w);
+                __syncthreads();
+                for (int p = threadIdx.x; p < F; p += T) {
+                    const int r = rq[p];
+                    const int h = static_cast<int>(hist[p]);
+                    const int e = r + h;
+                    const int r4 = r & ~3, e4 = e & ~3;
+                    const int np = r > 0 ? (r & 3) : 0;
+                    if (np && e4 > r4) {
+                        // this chunk completes the pending sector: write its earlier rows
+                        long long *o = ob[p] + r4;
+                        for (int j = 0; j < np; j++) {
+                            __stcs(o + j, pK[p * 3 + j]);
+                            if (PAY) __stcs(o + dP + j, pP[p * 3 + j]);
+                        }
+                    }
+                    const int lim = e4 > 0 ? e4 : 0;          // rows with q < lim are written now
+                    const int k = lim - r;                    // of this chunk's h rows, the first k
+                    const int s0 = static_cast<int>(start[p]);
+                    qt[p] = make_int2(r - s0, s0 + (k < 0 ? 0 : (k > h ? h : k)));
+                    rq[p] = e;
+                }
+#pragma unroll
+                for (int i = 0; i < IT; i++) {
+                    if (dg[i] != 0xffffffffu) {
+                        const uint32_t pos = start[dg[i]] + cnt[warp * FC + dg[i]] + rk[i];
+                        sK[pos] = ck[i];
+                        if (PAY) sP[pos] = cv[i];
+                        sD[pos] = static_cast<uint16_t>(dg[i]);
                     }
                 }
-                const int lim = e4 > 0 ? e4 : 0;          // rows with q < lim are written now
-                const int k = lim - r;                    // of this chunk's h rows, the first k
-                const int st = static_cast<int>(start[p]);
-                qt[p] = make_int2(r - st, st + (k < 0 ? 0 : (k > h ? h : k)));
-                rq[p] = e;
-            }
-#pragma unroll
-            for (int i = 0; i < IT; i++) {
-                if (dg[i] != 0xffffffffu) {
-                    const uint32_t pos = start[dg[i]] + cnt[warp * FC + dg[i]] + rk[i];
-                    sK[pos] = ck[i];
-                    if (PAY) sP[pos] = cv[i];
-                    sD[pos] = static_cast<uint16_t>(dg[i]);
+                __syncthreads();
+                for (int t = threadIdx.x; t < m; t += T) {
+                    const int p = sD[t];
+                    const int2 x = qt[p];
+                    const int q = x.x + t;
+                    if (t < x.y) {
+                        long long *o = ob[p] + q;
+                        __stcs(o, sK[t]);
+                        if (PAY) __stcs(o + dP, sP[t]);
+                    } else {
+                        pK[p * 3 + (q & 3)] = sK[t];
+                        if (PAY) pP[p * 3 + (q & 3)] = sP[t];
+                    }
                 }
+                for (int i = threadIdx.x; i < NWARP * FC / 8; i += T)
+                    reinterpret_cast<uint4 *>(cnt)[i] = make_uint4(0, 0, 0, 0);
+                __syncthreads();
             }
-            __syncthreads();
-            for (int t = threadIdx.x; t < m; t += T) {
-                const int p = sD[t];
-                const int2 x = qt[p];
-                const int q = x.x + t;
-                if (t < x.y) {
-                    long long *o = ob[p] + q;
-                    __stcs(o, sK[t]);
-                    if (PAY) __stcs(o + dP, sP[t]);
-                } else {
-                    pK[p * 3 + (q & 3)] = sK[t];
-                    if (PAY) pP[p * 3 + (q & 3)] = sP[t];
-                }
-            }
-            for (int i = threadIdx.x; i < NWARP * FC / 8; i += T) reinterpret_cast<uint4 *>(cnt)[i] = make_uint4(0, 0, 0, 0);
-            __syncthreads();
 #pragma unroll
             for (int i = 0; i < IT; i++) {
                 ck[i] = nk[i];
@@ -501,6 +630,7 @@ struct WcShape {
 template <bool PAY>
 static WcShape wc_shape(int log2f)
 {
+    if (log2f <= 5) return {256, 8, reinterpret_cast<const void *>(k_part_scatter_wc<PAY, 5, 256, 8, 2>)};
     if (log2f <= 6) return {256, 8, reinterpret_cast<const void *>(k_part_scatter_wc<PAY, 6, 256, 8, 2>)};
     if (log2f <= 8) return {512, 8, reinterpret_cast<const void *>(k_part_scatter_wc<PAY, 8, 512, 8, 1>)};
     return {512, 8, reinterpret_cast<const void *>(k_part_scatter_wc<PAY, 10, 512, 8, 1>)};
