@@ -140,7 +140,16 @@ __device__ __forceinline__ uint32_t dev_part_id(int64_t key, int log2f, int mode
 {
     if (log2f == 0) return 0;
     uint64_t k = static_cast<uint64_t>(key);
-    if (mode == QE_PART_HASH) return static_cast<uint32_t>(dev_fmix64(k) >> (64 - log2f));
+    if (mode == QE_PART_HASH) {
+        // The destination is the top log2f (<= 12) bits of fmix64(k).  They
+        // lie in the high word, which fmix64's last step k ^= k >> 33 leaves
+        // unchanged, so it is skipped.
+        k ^= k >> 33;
+        k *= 0xff51afd7ed558ccdULL;
+        k ^= k >> 33;
+        k *= 0xc4ceb9fe1a85ec53ULL;
+        return static_cast<uint32_t>(k >> 32) >> (32 - log2f);
+    }
     return static_cast<uint32_t>((k >> shift) & ((uint64_t(1) << log2f) - 1));
 }
 

@@ -192,16 +192,17 @@ struct WcLayout {
     }
 };
 
+// Rows r0 + (warp-striped positions) into registers, key in .x and payload
+// in .y, so that a row moves to shared memory as one 16-byte element.
 template <bool PAY, int IT>
-__device__ __forceinline__ void wc_load(const PartArgs &A, int64_t r0, int64_t hi, long long (&k)[IT],
-                                        long long (&v)[IT])
+__device__ __forceinline__ void wc_load(const PartArgs &A, int64_t r0, int64_t hi, longlong2 (&kv)[IT])
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
     for (int i = 0; i < IT; i++) {
         const int64_t r = r0 + warp * 32 * IT + i * 32 + lane;
-        k[i] = r < hi ? __ldcs(reinterpret_cast<const long long *>(A.keys) + r) : 0;
-        if (PAY) v[i] = r < hi ? __ldcs(static_cast<const long long *>(A.pay[0]) + r) : 0;
+        kv[i].x = r < hi ? __ldcs(reinterpret_cast<const long long *>(A.keys) + r) : 0;
+        kv[i].y = PAY && r < hi ? __ldcs(static_cast<const long long *>(A.pay[0]) + r) : 0;
     }
 }
 
@@ -332,15 +333,15 @@ __global__ void __launch_bounds__(T, MINB) k_part_scatter_wc(PartArgs A)
             ob[p] = outK + g + hl;
             rq[p] = -hl;
         }
-        long long ck[IT], cv[IT];
-        wc_load<PAY, IT>(A, lo, hi, ck, cv);
+        longlong2 kv[IT];
+        wc_load<PAY, IT>(A, lo, hi, kv);
         __syncthreads();
 
         for (int64_t c = 0; c < nch; c++) {
             const int64_t r0 = lo + c * CH;
             const int m = static_cast<int>(hi - r0 < CH ? hi - r0 : CH);
-            long long nk[IT], nv[IT];
-            wc_load<PAY, IT>(A, r0 + CH, hi, nk, nv);    // rows past hi are not read
+            longlong2 nkv[IT];
+            wc_load<PAY, IT>(A, r0 + CH, hi, nkv);       // rows past hi are not read
 
             uint32_t dg[IT], rk[IT];
             if constexpr (BITS <= 6) {
@@ -360,7 +361,7 @@ __global__ void __launch_bounds__(T, MINB) k_part_scatter_wc(PartArgs A)
                 for (int i = 0; i < IT; i++) {
                     const bool valid = m == CH || warp * 32 * IT + i * 32 + lane < m;
                     const uint32_t d =
-                        valid ? (dev_part_id(ck[i], A.log2f, A.mode, A.shift) >> A.dshift) & A.dmask : 0u;
+                        valid ? (dev_part_id(kv[i].x, A.log2f, A.mode, A.shift) >> A.dshift) & A.dmask : 0u;
                     unsigned me = m == CH ? QE_FULL_MASK : __ballot_sync(QE_FULL_MASK, valid);
 #pragma unroll
                     for (int bit = 0; bit < (BITS < 5 ? BITS : 5); bit++) {
@@ -459,9 +460,9 @@ __global__ void __launch_bounds__(T, MINB) k_part_scatter_wc(PartArgs A)
                     if (dg[i] != 0xffffffffu) {
                         pos += rk[i];
                         if (PAY)
-                            reinterpret_cast<longlong2 *>(sK)[pos] = make_longlong2(ck[i], cv[i]);
+                            reinterpret_cast<longlong2 *>(sK)[pos] = kv[i];
                         else
-                            sK[pos] = ck[i];
+                            sK[pos] = kv[i].x;
                     }
                 }
                 __syncthreads();
@@ -474,9 +475,9 @@ __global__ void __launch_bounds__(T, MINB) k_part_scatter_wc(PartArgs A)
                         const int q = x.x + t;
                         long long k, v = 0;
                         if (PAY) {
-                            const longlong2 kv = reinterpret_cast<const longlong2 *>(sK)[t];
-                            k = kv.x;
-                            v = kv.y;
+                            const longlong2 kv2 = reinterpret_cast<const longlong2 *>(sK)[t];
+                            k = kv2.x;
+                            v = kv2.y;
                         } else {
                             k = sK[t];
                         }
@@ -496,7 +497,7 @@ __global__ void __launch_bounds__(T, MINB) k_part_scatter_wc(PartArgs A)
                 for (int i = 0; i < IT; i++) {
                     const bool valid = warp * 32 * IT + i * 32 + lane < m;
                     const uint32_t d =
-                        valid ? (dev_part_id(ck[i], A.log2f, A.mode, A.shift) >> A.dshift) & A.dmask : 0u;
+                        valid ? (dev_part_id(kv[i].x, A.log2f, A.mode, A.shift) >> A.dshift) & A.dmask : 0u;
                     const unsigned peers = match_label<BITS>(d, __ballot_sync(QE_FULL_MASK, valid));
                     uint16_t *cp = cnt + warp * FC + d;
                     uint32_t basec = 0;
@@ -552,8 +553,8 @@ __global__ void __launch_bounds__(T, MINB) k_part_scatter_wc(PartArgs A)
                 for (int i = 0; i < IT; i++) {
                     if (dg[i] != 0xffffffffu) {
                         const uint32_t pos = start[dg[i]] + cnt[warp * FC + dg[i]] + rk[i];
-                        sK[pos] = ck[i];
-                        if (PAY) sP[pos] = cv[i];
+                        sK[pos] = kv[i].x;
+                        if (PAY) sP[pos] = kv[i].y;
                         sD[pos] = static_cast<uint16_t>(dg[i]);
                     }
                 }
@@ -577,8 +578,7 @@ __global__ void __launch_bounds__(T, MINB) k_part_scatter_wc(PartArgs A)
             }
 #pragma unroll
             for (int i = 0; i < IT; i++) {
-                ck[i] = nk[i];
-                if (PAY) cv[i] = nv[i];
+                kv[i] = nkv[i];
             }
         }
         // rows still pending at the end of the item
