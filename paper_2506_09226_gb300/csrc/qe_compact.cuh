@@ -5,7 +5,7 @@
 // so every column read is one 128-byte (int32) or 256-byte (int64) coalesced
 // warp access and the natural row order is (warp, item, lane).  Survivors of
 // item k are ranked inside the warp with one ballot, warps are ranked with a
-// shared-memory scan, and tiles with the decoupled look-back; each survivor
+// shared-memory scan, and tiles with a block-wide decoupled look-back; each survivor
 // is written once at its final position.  Tiles are claimed from an atomic
 // counter by a persistent grid.
 #pragma once
@@ -24,18 +24,78 @@ struct CompactCommon {
 };
 
 // Op must provide:
+//   struct Pre;                                       per-thread loads of a tile
 //   struct Slot;                                      per-thread item data
-//   __device__ void eval(int64_t pos0, bool (&ok)[ITEMS], Slot &s) const;
+//   __device__ void load(int64_t pos0, const bool (&in)[ITEMS], Pre &p) const;
+//        the tile's independent loads (in[k]: position in range);
+//   __device__ void eval(int64_t pos0, bool (&ok)[ITEMS], const Pre &p, Slot &s) const;
 //        pos0 = this lane's first position (item k is pos0 + 32k); ok[k]
 //        arrives true for in-range positions; eval clears non-survivors.
 //   __device__ void emit(int64_t out_pos, int64_t pos, int k, const Slot &s) const;
+//
+// Tiles are not prefetched across claims: a claimed tile that waits behind
+// its block's current one would hold up the look-back of every later tile.
+// Loads in flight come from resident blocks instead (registers per thread
+// kept low so that many blocks fit).
+// Decoupled look-back by the whole block (Merrill & Garland's single-pass
+// scan): tile `tile` publishes its aggregate, then its 256 threads read 256
+// predecessors per round, nearest first, and sum back to the nearest one
+// that has published its inclusive prefix (all tiles up to it must have
+// published at least their aggregate).  With hundreds of tiles in flight the
+// nearest inclusive prefix is often a few hundred tiles back, which one
+// warp would reach only after many dependent rounds.  Returns the exclusive
+// prefix to every thread.  Bounded: after spin_limit empty rounds it records
+// QE_ERR_TIMEOUT and returns what it has.
+__device__ __forceinline__ int64_t lb_exclusive_block(unsigned long long *state, int64_t tile, int64_t agg,
+                                                      qe_dev_status *st, int64_t spin_limit, int *s_min,
+                                                      long long *s_sum)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) lb_store(state + tile, LB_AGG | static_cast<unsigned long long>(agg));
+    int64_t excl = 0, pred = tile - 1, spins = 0;
+    while (true) {
+        if (threadIdx.x == 0) *s_min = 256;
+        if (threadIdx.x < 8) s_sum[threadIdx.x] = 0;
+        __syncthreads();
+        const int64_t t = pred - threadIdx.x;
+        const unsigned long long w = t >= 0 ? lb_load(state + t) : LB_PRE;
+        const unsigned flag = static_cast<unsigned>(w >> 62);
+        const unsigned pm = __ballot_sync(QE_FULL_MASK, flag == 2);
+        if (lane == 0 && pm) atomicMin(s_min, warp * 32 + __ffs(pm) - 1);
+        __syncthreads();
+        const int stop = *s_min;                  // nearest inclusive prefix, 256 if none
+        const bool mine = static_cast<int>(threadIdx.x) <= stop;
+        if (__syncthreads_or(mine && flag == 0)) {
+            if (++spins > spin_limit) {
+                if (threadIdx.x == 0) dev_report(st, QE_ERR_TIMEOUT, 0);
+                break;
+            }
+            __nanosleep(32);
+            continue;
+        }
+        const int64_t v = warp_sum(mine ? static_cast<int64_t>(w & LB_VAL) : 0);
+        if (lane == 0) s_sum[warp] = v;
+        __syncthreads();
+        int64_t round = 0;
+#pragma unroll
+        for (int i = 0; i < 8; i++) round += s_sum[i];
+        excl += round;
+        if (stop < 256) break;
+        pred -= 256;
+        __syncthreads();                          // s_sum / s_min are reused
+    }
+    if (threadIdx.x == 0) lb_store(state + tile, LB_PRE | static_cast<unsigned long long>(excl + agg));
+    return excl;
+}
+
 template <int ITEMS, class Op>
 __global__ void __launch_bounds__(256) k_compact(CompactCommon C, Op op)
 {
     constexpr int TILE = 256 * ITEMS;
     __shared__ long long s_tile;
     __shared__ int s_wofs[8];
-    __shared__ long long s_excl;
+    __shared__ int s_min;
+    __shared__ long long s_sum[8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1;
     while (true) {
@@ -47,8 +107,10 @@ __global__ void __launch_bounds__(256) k_compact(CompactCommon C, Op op)
         bool ok[ITEMS];
 #pragma unroll
         for (int k = 0; k < ITEMS; k++) ok[k] = pos0 + 32 * k < C.n;
+        typename Op::Pre pre;
+        op.load(pos0, ok, pre);
         typename Op::Slot slot;
-        op.eval(pos0, ok, slot);
+        op.eval(pos0, ok, pre, slot);
         unsigned mask[ITEMS];
         int wtotal = 0;
 #pragma unroll
@@ -58,23 +120,20 @@ __global__ void __launch_bounds__(256) k_compact(CompactCommon C, Op op)
         }
         if (lane == 0) s_wofs[warp] = wtotal;
         __syncthreads();
-        if (warp == 0) {
-            int v = lane < 8 ? s_wofs[lane] : 0;
-            int inc = warp_incl_scan(v);
-            int tot = __shfl_sync(QE_FULL_MASK, inc, 7);
-            int64_t excl = lb_exclusive(C.tile_state, tile, tot, C.st, C.spin_limit);
-            if (lane < 8) s_wofs[lane] = inc - v;
-            if (lane == 0) {
-                s_excl = excl;
-                if (tile == C.ntiles - 1) {
-                    int64_t total = excl + tot;
-                    *C.out_count = total;
-                    if (total > C.capacity) dev_report(C.st, QE_ERR_CAPACITY, total);
-                }
-            }
+        int woff = 0, tot = 0;
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const int x = s_wofs[i];
+            woff += i < warp ? x : 0;
+            tot += x;
         }
-        __syncthreads();
-        int64_t pos = s_excl + s_wofs[warp];
+        const int64_t excl = lb_exclusive_block(C.tile_state, tile, tot, C.st, C.spin_limit, &s_min, s_sum);
+        if (threadIdx.x == 0 && tile == C.ntiles - 1) {
+            const int64_t total = excl + tot;
+            *C.out_count = total;
+            if (total > C.capacity) dev_report(C.st, QE_ERR_CAPACITY, total);
+        }
+        int64_t pos = excl + woff;
 #pragma unroll
         for (int k = 0; k < ITEMS; k++) {
             if (ok[k]) {

@@ -182,6 +182,30 @@ __device__ __forceinline__ bool dev_cmp(int64_t x, int op, int64_t lo, int64_t h
     }
 }
 
+// A comparison as a closed range [a, b], possibly negated: x satisfies
+// (lo, op, hi) iff (a <= x <= b) != neg.  Returns false when [a, b] is empty.
+__host__ __device__ inline bool qe_pred_range(int op, int64_t lo, int64_t hi, int64_t &a, int64_t &b, bool &neg)
+{
+    a = INT64_MIN;
+    b = INT64_MAX;
+    neg = false;
+    switch (op) {
+    case QE_LT:
+        if (lo == INT64_MIN) return false;
+        b = lo - 1;
+        return true;
+    case QE_LE: b = lo; return true;
+    case QE_GT:
+        if (lo == INT64_MAX) return false;
+        a = lo + 1;
+        return true;
+    case QE_GE: a = lo; return true;
+    case QE_EQ: a = b = lo; return true;
+    case QE_NE: a = b = lo; neg = true; return true;
+    default: a = lo; b = hi; return lo <= hi;
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_incl_scan(T v)
 {
@@ -239,10 +263,17 @@ __device__ __forceinline__ int64_t lb_exclusive(unsigned long long *state, int64
     if (lane == 0) lb_store(state + tile, LB_AGG | static_cast<unsigned long long>(agg));
     int64_t excl = 0, pred = tile - 1, spins = 0;
     while (true) {
+        // a window of 32 predecessors, nearest in lane 0: sum back to the
+        // nearest one that published its inclusive prefix; only the tiles up
+        // to it must have published something
         int64_t t = pred - lane;
         unsigned long long w = t >= 0 ? lb_load(state + t) : LB_PRE;
         unsigned flag = static_cast<unsigned>(w >> 62);
-        if (__any_sync(QE_FULL_MASK, flag == 0)) {
+        const unsigned pm = __ballot_sync(QE_FULL_MASK, flag == 2);
+        const unsigned nr = __ballot_sync(QE_FULL_MASK, flag == 0);
+        const int stop = pm ? __ffs(pm) - 1 : 31;
+        const unsigned need = stop == 31 ? QE_FULL_MASK : ((2u << stop) - 1u);
+        if (nr & need) {
             if (++spins > spin_limit) {
                 if (lane == 0) dev_report(st, QE_ERR_TIMEOUT, 0);
                 break;
@@ -250,8 +281,6 @@ __device__ __forceinline__ int64_t lb_exclusive(unsigned long long *state, int64
             __nanosleep(32);
             continue;
         }
-        unsigned pm = __ballot_sync(QE_FULL_MASK, flag == 2);
-        int stop = pm ? __ffs(pm) - 1 : 31;
         int64_t v = lane <= stop ? static_cast<int64_t>(w & LB_VAL) : 0;
         excl += warp_sum(v);
         if (pm) break;

@@ -142,18 +142,30 @@ struct ProbeOp {
         int32_t row[PROBE_ITEMS];
         int32_t pay[PROBE_ITEMS];
     };
+    // the probe rows (selection vector entries), loaded a tile ahead
+    struct Pre {
+        int32_t row[PROBE_ITEMS];
+    };
 
     template <int ITEMS>
-    __device__ __forceinline__ void eval(int64_t pos0, bool (&ok)[ITEMS], Slot &s) const
+    __device__ __forceinline__ void load(int64_t pos0, const bool (&in)[ITEMS], Pre &p) const
     {
 #pragma unroll
         for (int k = 0; k < ITEMS; k++) {
             int64_t i = pos0 + 32 * k;
-            s.row[k] = ok[k] ? (sel ? __ldcs(sel + i) : static_cast<int32_t>(i)) : 0;
+            p.row[k] = in[k] ? (sel ? __ldcs(sel + i) : static_cast<int32_t>(i)) : 0;
         }
+    }
+
+    template <int ITEMS>
+    __device__ __forceinline__ void eval(int64_t, bool (&ok)[ITEMS], const Pre &pre, Slot &s) const
+    {
         int32_t key[ITEMS];
 #pragma unroll
-        for (int k = 0; k < ITEMS; k++) key[k] = ok[k] ? __ldg(keys + s.row[k]) : 0;
+        for (int k = 0; k < ITEMS; k++) {
+            s.row[k] = pre.row[k];
+            key[k] = ok[k] ? __ldg(keys + s.row[k]) : 0;
+        }
 #pragma unroll
         for (int k = 0; k < ITEMS; k++) {
             int32_t p = 0;
