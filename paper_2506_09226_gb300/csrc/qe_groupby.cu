@@ -11,8 +11,8 @@
 
 namespace {
 
-constexpr int GB_THREADS = 256;
-constexpr int GB_ITEMS = 8;
+constexpr int GB_THREADS = 1024;   // one block per SM shares the shared-memory table
+constexpr int GB_ITEMS = 4;
 
 struct ColRef {
     const void *data;
@@ -153,8 +153,14 @@ extern "C" qe_status qe_groupby(qe_ctx *ctx, int64_t n, const int32_t *rows, qe_
     const size_t budget = ctx->smem_optin > 4096 ? ctx->smem_optin - 4096 : 0;
     A.S = 0;
     if (placement != QE_GB_HBM) {
-        A.S = st_slots_for(out->capacity, naggs, placement == QE_GB_SMEM ? budget : budget / 2);
-        if (placement == QE_GB_SMEM && A.S == 0) A.S = st_slots_max(naggs, budget);
+        // The capacity bounds the number of groups, so a table of
+        // pow2 >= capacity slots cannot fill up; a table that does not fit
+        // the budget is used only when shared memory is asked for, as a
+        // cache in front of the HBM table.
+        uint64_t want = 64;
+        while (want < static_cast<uint64_t>(out->capacity)) want <<= 1;
+        if (want * 8 * (1 + naggs) <= budget) A.S = static_cast<int>(want);
+        else if (placement == QE_GB_SMEM) A.S = st_slots_max(naggs, budget);
     }
     A.log2S = 0;
     while ((1 << A.log2S) < A.S) A.log2S++;
