@@ -398,9 +398,12 @@ def test_pipeline_dense_hint_too_narrow_spills(ctx, generic):
         ctx.set_tuning("force_generic", 0)
 
 
-def test_pipeline_dense_hbm_25k(ctx):
+@pytest.mark.parametrize("n", [1_000, 400_000, 3_000_001])
+def test_pipeline_dense_hbm_25k(ctx, n):
+    """25,002 groups: a direct array too large for one SM's shared memory,
+    kept in HBM."""
     dim = datagen.star_dim(50_000, 8334, seed=7)
-    fact = datagen.star_fact(400_000, 50_000, seed=7)
+    fact = datagen.star_fact(n, 50_000, seed=7)
     g = run_star_hint(ctx, fact, dim, ((0, 2), (0, 8333)), 30_000)
     assert_groups_equal(g, oracle_star(fact, dim))
 
