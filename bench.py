@@ -247,6 +247,21 @@ def workload_config(args):
 
 
 # ---------------------------------------------------------------- our arm
+def job_time(ms_local: float, dist=None, device=None) -> float:
+    """The step time of the whole job: the maximum over ranks (replicas run
+    the same step on their own GPU), by an all-reduce when distributed."""
+    if dist is None:
+        return ms_local
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job throughput: the units every rank processed over the job time."""
+    return units_per_rank * world / (ms * 1e-3)
+
+
 def timed(fn, iters, stream):
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -299,16 +314,13 @@ def run_qe(args):
     ms = timed(step, args.steps, stream)
     launches = ctx.launch_count() - l0
     clocks = sampler.stop()
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = job_time(ms, dist, dev)
     ctx.sync_status()
     prof = {n: ctx.profile_read(n) for n in ("build", "pipeline", "part_hist", "part_scatter")}
     ctx.profile(False)
     ngroups = int(groups.ngroups.item())
     rows_step = args.fact_rows + args.pairs
-    value = rows_step * world / (ms * 1e-3)
+    value = job_value(rows_step, world, ms)
 
     # ---- per-kernel breakdown and the dominant kernel's roofline
     alg_bytes = {"pipeline": BYTES_FACT_ROW * args.fact_rows,
