@@ -357,6 +357,10 @@ __global__ void __launch_bounds__(T, MINB) k_part_scatter_wc(PartArgs A)
                 // lane e computes which lanes hold digit e (AND over bits of
                 // the bit ballots or their complements); a row reads its
                 // peers and its base count from lane (digit & 31)
+                // first every item's masks (independent of each other), then
+                // the counters' prefix over items, then the shuffles: no
+                // dependency chain through the counters
+                unsigned me0[IT], me1[IT];
 #pragma unroll
                 for (int i = 0; i < IT; i++) {
                     const bool valid = m == CH || warp * 32 * IT + i * 32 + lane < m;
@@ -368,27 +372,33 @@ __global__ void __launch_bounds__(T, MINB) k_part_scatter_wc(PartArgs A)
                         const unsigned set = __ballot_sync(QE_FULL_MASK, (d >> bit) & 1u);
                         me &= ((lane >> bit) & 1) ? set : ~set;
                     }
-                    unsigned me1 = 0;
+                    unsigned me1v = 0;
                     if (BITS > 5) {
                         const unsigned set5 = __ballot_sync(QE_FULL_MASK, (d >> 5) & 1u);
-                        me1 = me & set5;
+                        me1v = me & set5;
                         me &= ~set5;
                     }
+                    me0[i] = me;
+                    me1[i] = me1v;
+                    dg[i] = valid ? d : 0xffffffffu;
+                }
+#pragma unroll
+                for (int i = 0; i < IT; i++) {
+                    const uint32_t d = dg[i] == 0xffffffffu ? 0u : dg[i];
                     const int src = static_cast<int>(d & 31u);
-                    unsigned peers = __shfl_sync(QE_FULL_MASK, me, src);
+                    unsigned peers = __shfl_sync(QE_FULL_MASK, me0[i], src);
                     uint32_t basec = __shfl_sync(QE_FULL_MASK, cl[0], src);
                     if (BITS > 5) {
-                        const unsigned peers1 = __shfl_sync(QE_FULL_MASK, me1, src);
+                        const unsigned peers1 = __shfl_sync(QE_FULL_MASK, me1[i], src);
                         const uint32_t base1 = __shfl_sync(QE_FULL_MASK, cl[NCL - 1], src);
                         if (d >= 32u) {
                             peers = peers1;
                             basec = base1;
                         }
                     }
-                    cl[0] += __popc(me);
-                    if (BITS > 5) cl[NCL - 1] += __popc(me1);
-                    dg[i] = valid ? d : 0xffffffffu;
                     rk[i] = basec + __popc(peers & lt);
+                    cl[0] += __popc(me0[i]);
+                    if (BITS > 5) cl[NCL - 1] += __popc(me1[i]);
                 }
 #pragma unroll
                 for (int k = 0; k < NCL; k++)
