@@ -626,12 +626,13 @@ __global__ void k_part_two_pass_tables(const uint32_t *hist, const int64_t *off,
     t1[i] = base[q << sub_bits] + o;
 }
 
-// Block shapes of the write-combining scatter, by fan-out.  Several blocks
-// per SM let one block's per-destination phases overlap another's row
-// phases, but every block writes one output page per destination and
-// column at a time; beyond a few hundred pages per SM the address
-// translation caches miss and the scatter slows down, so larger fan-outs
-// run a single block of 512 per SM.
+// Block shapes of the write-combining scatter, by fan-out (measured on
+// GB300).  Two blocks of 256 per SM let one block's per-destination phases
+// overlap the other's row phases (up to 32 digits).  From 64 digits a chunk
+// of 256 x 8 rows gives each digit runs too short for the per-digit work, so
+// one block of 512 runs per SM; and every block writes one output page per
+// destination and column at a time, so beyond a few hundred pages per SM
+// (two blocks at 256 digits) the address translation caches miss.
 struct WcShape {
     int threads, items;
     const void *kernel;
@@ -641,7 +642,7 @@ template <bool PAY>
 static WcShape wc_shape(int log2f)
 {
     if (log2f <= 5) return {256, 8, reinterpret_cast<const void *>(k_part_scatter_wc<PAY, 5, 256, 8, 2>)};
-    if (log2f <= 6) return {256, 8, reinterpret_cast<const void *>(k_part_scatter_wc<PAY, 6, 256, 8, 2>)};
+    if (log2f <= 6) return {512, 8, reinterpret_cast<const void *>(k_part_scatter_wc<PAY, 6, 512, 8, 1>)};
     if (log2f <= 8) return {512, 8, reinterpret_cast<const void *>(k_part_scatter_wc<PAY, 8, 512, 8, 1>)};
     return {512, 8, reinterpret_cast<const void *>(k_part_scatter_wc<PAY, 10, 512, 8, 1>)};
 }
