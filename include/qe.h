@@ -137,8 +137,9 @@ void qe_debug_set_spin_limit(qe_ctx *ctx, int64_t iterations);
  *                   (0 = default 3);
  *   "force_generic" nonzero: run every pipeline through the generic kernel.
  *   "part_general"  nonzero: qe_partition always uses its general scatter
- *                   kernel (two-pass chunk ranking, any payload types)
- *                   instead of the write-combining one.
+ *                   kernel (chunks ranked over one or two digits, any
+ *                   payload types, one pass at every fan-out) instead of the
+ *                   write-combining one.
  * Unknown names return QE_ERR_INVALID_ARG. */
 qe_status qe_set_tuning(qe_ctx *ctx, const char *name, int64_t value);
 
@@ -216,7 +217,13 @@ typedef enum {
  *                overlap the inputs;
  *   out_offsets: device int64 [F + 1]; out_offsets[p] is the first output
  *                row of destination p, out_offsets[F] = nrows.
- * log2_fanout in [0, 12]; shift in [0, 63] (radix mode). */
+ * log2_fanout in [0, 12]; shift in [0, 63] (radix mode).
+ * Scratch, taken from the context's HBM budget for the duration of the call:
+ * per-block histograms and offsets (about 12 bytes x F x 304), and, when the
+ * rows are int64 keys with one int64 payload or none and F > 512, a copy of
+ * the keys and payload (16 bytes per row), because such fan-outs run as two
+ * passes of at most 64 destinations each.  QE_ERR_OOM when the budget does
+ * not hold it. */
 qe_status qe_partition(qe_ctx *ctx, const int64_t *keys, const qe_col *payload, int npayload,
                        int64_t nrows, int log2_fanout, int mode, int shift, int64_t *out_keys,
                        void *const *out_payload, int64_t *out_offsets, void *stream);
