@@ -189,3 +189,169 @@ qe_status launch_compact(qe_ctx *ctx, const char *name, int64_t n, int64_t capac
     if (e != cudaSuccess) return qe_cuda_fail(ctx, e, "k_compact launch");
     return QE_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Two-pass stable compaction for large inputs, with no dependency between
+// blocks (so as many tiles are in flight as occupancy allows; the price is
+// evaluating every row twice).  A warp segment is 32 lanes x ITEMS rows in
+// the tile order above (item k of lane l is position seg*32*ITEMS + 32k + l).
+// Pass 1 counts each segment's survivors; a two-level scan turns the counts
+// into offsets (blocks of TP_SCAN_B counts, then at most 4 * 1024 block
+// totals); pass 2 re-evaluates each segment and writes its survivors item by
+// item at the segment's offset.
+constexpr int TP_SCAN_B = 4096;
+
+template <int ITEMS, class Op>
+__global__ void __launch_bounds__(256) k_tp_count(Op op, int64_t n, int64_t nseg, uint32_t *cnt)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = static_cast<int64_t>(gridDim.x) * 8;
+    for (int64_t seg = static_cast<int64_t>(blockIdx.x) * 8 + (threadIdx.x >> 5); seg < nseg; seg += warps) {
+        const int64_t pos0 = seg * 32 * ITEMS + lane;
+        bool ok[ITEMS];
+#pragma unroll
+        for (int k = 0; k < ITEMS; k++) ok[k] = pos0 + 32 * k < n;
+        typename Op::Pre pre;
+        typename Op::Slot slot;
+        op.load(pos0, ok, pre);
+        op.eval(pos0, ok, pre, slot);
+        uint32_t c = 0;
+#pragma unroll
+        for (int k = 0; k < ITEMS; k++) c += __popc(__ballot_sync(QE_FULL_MASK, ok[k]));
+        if (lane == 0) cnt[seg] = c;
+    }
+}
+
+// Each block of 1024 threads scans TP_SCAN_B counts into local offsets and
+// writes its total.
+static __global__ void __launch_bounds__(1024) k_tp_scan_local(const uint32_t *cnt, uint32_t *loc, int64_t nseg,
+                                                        int64_t *bsum)
+{
+    __shared__ uint32_t s_w[32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int64_t base = static_cast<int64_t>(blockIdx.x) * TP_SCAN_B + 4 * t;
+    uint32_t v[4], local = 0;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        v[j] = base + j < nseg ? cnt[base + j] : 0u;
+        local += v[j];
+    }
+    const uint32_t inc = warp_incl_scan(local);
+    if (lane == 31) s_w[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t w = s_w[lane];
+        const uint32_t wi = warp_incl_scan(w);
+        s_w[lane] = wi - w;
+        if (lane == 31) bsum[blockIdx.x] = wi;
+    }
+    __syncthreads();
+    uint32_t run = s_w[warp] + inc - local;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        if (base + j < nseg) loc[base + j] = run;
+        run += v[j];
+    }
+}
+
+// One block: exclusive scan of at most 4096 block totals in place, the total
+// into out_count, capacity check.
+static __global__ void __launch_bounds__(1024) k_tp_scan_top(int64_t *bsum, int nblk, int64_t *out_count, int64_t capacity,
+                                                      qe_dev_status *st)
+{
+    __shared__ int64_t s_w[32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    int64_t v[4], local = 0;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        v[j] = 4 * t + j < nblk ? bsum[4 * t + j] : 0;
+        local += v[j];
+    }
+    const int64_t inc = warp_incl_scan(local);
+    if (lane == 31) s_w[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const int64_t w = s_w[lane];
+        const int64_t wi = warp_incl_scan(w);
+        s_w[lane] = wi - w;
+    }
+    __syncthreads();
+    int64_t run = s_w[warp] + inc - local;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        if (4 * t + j < nblk) bsum[4 * t + j] = run;
+        run += v[j];
+    }
+    if (t == 1023) {
+        *out_count = run;
+        if (run > capacity) dev_report(st, QE_ERR_CAPACITY, run);
+    }
+}
+
+template <int ITEMS, class Op>
+__global__ void __launch_bounds__(256) k_tp_write(Op op, int64_t n, int64_t nseg, const uint32_t *loc,
+                                                 const int64_t *bsum, int64_t capacity)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1;
+    const int64_t warps = static_cast<int64_t>(gridDim.x) * 8;
+    for (int64_t seg = static_cast<int64_t>(blockIdx.x) * 8 + (threadIdx.x >> 5); seg < nseg; seg += warps) {
+        const int64_t pos0 = seg * 32 * ITEMS + lane;
+        bool ok[ITEMS];
+#pragma unroll
+        for (int k = 0; k < ITEMS; k++) ok[k] = pos0 + 32 * k < n;
+        typename Op::Pre pre;
+        typename Op::Slot slot;
+        op.load(pos0, ok, pre);
+        op.eval(pos0, ok, pre, slot);
+        int64_t pos = bsum[seg / TP_SCAN_B] + loc[seg];
+#pragma unroll
+        for (int k = 0; k < ITEMS; k++) {
+            const unsigned m = __ballot_sync(QE_FULL_MASK, ok[k]);
+            if (ok[k]) {
+                const int64_t o = pos + __popc(m & lt);
+                if (o < capacity) op.emit(o, pos0 + 32 * k, k, slot);
+            }
+            pos += __popc(m);
+        }
+    }
+}
+
+// Host: scratch, the two passes and the scan.  nseg must not exceed
+// 4 * 1024 * TP_SCAN_B.
+template <int ITEMS, class Op>
+qe_status launch_two_pass(qe_ctx *ctx, const char *name, int64_t n, int64_t capacity, int64_t *out_count,
+                          const Op &op, cudaStream_t s)
+{
+    const int64_t nseg = qe_ceil_div(n, static_cast<int64_t>(32) * ITEMS);
+    const int64_t nblk = qe_ceil_div(nseg, TP_SCAN_B);
+    if (nblk > 4 * 1024) return qe_fail(ctx, QE_ERR_INVALID_ARG, std::string(name) + ": too many rows");
+    void *scratch = nullptr;
+    const size_t cnt_bytes = ((static_cast<size_t>(nseg) * 4 + 255) / 256) * 256;
+    qe_status st = qe_alloc(ctx, &scratch, 2 * cnt_bytes + static_cast<size_t>(nblk) * 8, s);
+    if (st != QE_OK) return st;
+    uint32_t *cnt = static_cast<uint32_t *>(scratch);
+    uint32_t *loc = reinterpret_cast<uint32_t *>(static_cast<char *>(scratch) + cnt_bytes);
+    int64_t *bsum = reinterpret_cast<int64_t *>(static_cast<char *>(scratch) + 2 * cnt_bytes);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tp_write<ITEMS, Op>, 256, 0);
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = static_cast<int64_t>(ctx->num_sms) * per_sm;
+    if (grid > qe_ceil_div(nseg, 8)) grid = qe_ceil_div(nseg, 8);
+    cudaError_t e;
+    {
+        ProfScope prof(ctx, name, s);
+        k_tp_count<ITEMS, Op><<<static_cast<unsigned>(grid), 256, 0, s>>>(op, n, nseg, cnt);
+        QE_LAUNCHED(ctx);
+        k_tp_scan_local<<<static_cast<unsigned>(nblk), 1024, 0, s>>>(cnt, loc, nseg, bsum);
+        QE_LAUNCHED(ctx);
+        k_tp_scan_top<<<1, 1024, 0, s>>>(bsum, static_cast<int>(nblk), out_count, capacity, ctx->dstat);
+        QE_LAUNCHED(ctx);
+        k_tp_write<ITEMS, Op><<<static_cast<unsigned>(grid), 256, 0, s>>>(op, n, nseg, loc, bsum, capacity);
+        QE_LAUNCHED(ctx);
+        e = cudaGetLastError();
+    }
+    qe_free(ctx, scratch, s);
+    if (e != cudaSuccess) return qe_cuda_fail(ctx, e, "two-pass compaction launch");
+    return QE_OK;
+}

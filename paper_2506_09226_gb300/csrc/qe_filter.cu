@@ -108,6 +108,8 @@ struct FilterOp : FilterSpec {
 // so both passes keep as many loads in flight as registers allow; the
 // price is a second read of the predicate columns.
 //
+// The segment counts are scanned by the generic two-pass kernels of
+// qe_compact.cuh.
 // Layout: a warp segment is IT items x 32 lanes x 4 rows; lane l of item k
 // holds the 4 consecutive rows seg*SEGR + 128k + 4l + v (v = 0..3), read
 // with one vector load of the first predicate's column, so row order is
@@ -193,67 +195,6 @@ __global__ void __launch_bounds__(256) k_filter_count(FilterSpec f, int64_t n, i
     }
 }
 
-// Exclusive scan of the segment counts in two levels: each block of 1024
-// threads scans SCAN_B = 4096 counts into local offsets and writes its
-// total; one block then scans the totals (at most 2^31 / (512 * 4096) =
-// 1024 of them).
-constexpr int SCAN_B = 4096;
-
-__global__ void __launch_bounds__(1024) k_filter_scan_local(const uint32_t *cnt, uint32_t *loc, int64_t nseg,
-                                                            int64_t *bsum)
-{
-    __shared__ uint32_t s_w[32];
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int64_t base = static_cast<int64_t>(blockIdx.x) * SCAN_B + 4 * t;
-    uint32_t v[4], local = 0;
-#pragma unroll
-    for (int j = 0; j < 4; j++) {
-        v[j] = base + j < nseg ? cnt[base + j] : 0u;
-        local += v[j];
-    }
-    const uint32_t inc = warp_incl_scan(local);
-    if (lane == 31) s_w[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-        const uint32_t w = s_w[lane];
-        const uint32_t wi = warp_incl_scan(w);
-        s_w[lane] = wi - w;
-        if (lane == 31) bsum[blockIdx.x] = wi;
-    }
-    __syncthreads();
-    uint32_t run = s_w[warp] + inc - local;
-#pragma unroll
-    for (int j = 0; j < 4; j++) {
-        if (base + j < nseg) loc[base + j] = run;
-        run += v[j];
-    }
-}
-
-// One block: exclusive scan of the block totals in place, the total into
-// out_count, capacity check.
-__global__ void __launch_bounds__(1024) k_filter_scan_top(int64_t *bsum, int nblk, int64_t *out_count,
-                                                          int64_t capacity, qe_dev_status *st)
-{
-    __shared__ int64_t s_w[32];
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int64_t x = t < nblk ? bsum[t] : 0;
-    const int64_t inc = warp_incl_scan(x);
-    if (lane == 31) s_w[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-        const int64_t w = s_w[lane];
-        const int64_t wi = warp_incl_scan(w);
-        s_w[lane] = wi - w;
-    }
-    __syncthreads();
-    const int64_t ex = s_w[warp] + inc - x;
-    if (t < nblk) bsum[t] = ex;
-    if (t == nblk - 1) {
-        *out_count = ex + x;
-        if (ex + x > capacity) dev_report(st, QE_ERR_CAPACITY, ex + x);
-    }
-}
-
 template <class T0>
 __global__ void __launch_bounds__(256) k_filter_write(FilterSpec f, int64_t n, int64_t nseg, const uint32_t *loc,
                                                      const int64_t *bsum, int64_t capacity)
@@ -269,7 +210,7 @@ __global__ void __launch_bounds__(256) k_filter_write(FilterSpec f, int64_t n, i
 #pragma unroll
         for (int k = 0; k < IT; k++) seg_load<T0>(f, row0 + 128 * k, n, x[k]);
         const bool full = (seg + 1) * SEGR <= n;
-        int64_t pos = bsum[seg / SCAN_B] + loc[seg];
+        int64_t pos = bsum[seg / TP_SCAN_B] + loc[seg];
 #pragma unroll
         for (int k = 0; k < IT; k++) {
             const int64_t row = row0 + 128 * k;
@@ -299,7 +240,7 @@ static qe_status filter_two_pass(qe_ctx *ctx, const FilterSpec &spec, int64_t n,
                                  cudaStream_t s)
 {
     const int64_t nseg = qe_ceil_div(n, static_cast<int64_t>(Vec4<T0>::IT) * 128);
-    const int64_t nblk = qe_ceil_div(nseg, SCAN_B);     // <= 1024 for n < 2^31 (segments >= 512 rows)
+    const int64_t nblk = qe_ceil_div(nseg, TP_SCAN_B);  // <= 1024 for n < 2^31 (segments >= 512 rows)
     void *scratch = nullptr;
     const size_t cnt_bytes = ((static_cast<size_t>(nseg) * 4 + 255) / 256) * 256;
     qe_status st = qe_alloc(ctx, &scratch, 2 * cnt_bytes + static_cast<size_t>(nblk) * 8, s);
@@ -317,9 +258,9 @@ static qe_status filter_two_pass(qe_ctx *ctx, const FilterSpec &spec, int64_t n,
         ProfScope prof(ctx, "filter", s);
         k_filter_count<T0><<<static_cast<unsigned>(grid), 256, 0, s>>>(spec, n, nseg, cnt);
         QE_LAUNCHED(ctx);
-        k_filter_scan_local<<<static_cast<unsigned>(nblk), 1024, 0, s>>>(cnt, loc, nseg, bsum);
+        k_tp_scan_local<<<static_cast<unsigned>(nblk), 1024, 0, s>>>(cnt, loc, nseg, bsum);
         QE_LAUNCHED(ctx);
-        k_filter_scan_top<<<1, 1024, 0, s>>>(bsum, static_cast<int>(nblk), out_count, capacity, ctx->dstat);
+        k_tp_scan_top<<<1, 1024, 0, s>>>(bsum, static_cast<int>(nblk), out_count, capacity, ctx->dstat);
         QE_LAUNCHED(ctx);
         k_filter_write<T0><<<static_cast<unsigned>(grid), 256, 0, s>>>(spec, n, nseg, loc, bsum, capacity);
         QE_LAUNCHED(ctx);

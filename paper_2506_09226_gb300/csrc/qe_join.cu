@@ -130,6 +130,7 @@ unsigned grid_for(qe_ctx *ctx, int64_t n)
 
 // Probe as a stable compaction: position i probes row sel[i] (or i).
 constexpr int PROBE_ITEMS = 8;
+constexpr int64_t PROBE_TWO_PASS_ROWS = int64_t(1) << 22;   // from here on: the two-pass compaction
 
 struct ProbeOp {
     HtView ht;
@@ -319,6 +320,8 @@ extern "C" qe_status qe_join_probe(qe_ctx *ctx, const qe_hash_table *ht, const i
     op.sel = sel;
     op.out_row = out_probe_row;
     op.out_pay = out_build_payload;
+    if (n >= PROBE_TWO_PASS_ROWS)
+        return launch_two_pass<PROBE_ITEMS>(ctx, "probe", n, capacity, out_count, op, static_cast<cudaStream_t>(stream));
     return launch_compact<PROBE_ITEMS>(ctx, "probe", n, capacity, out_count, op, static_cast<cudaStream_t>(stream));
 }
 

@@ -73,6 +73,54 @@ def test_filter_selectivity_extremes_and_views(ctx):
         assert np.array_equal(sel[:int(cnt.item())].cpu().numpy(), ref)
 
 
+# large inputs take the two-pass filter (4-row vector loads of the first
+# predicate's column); unaligned first columns fall back to the one-pass scan
+TWO_PASS_N = 5_000_011
+
+
+@pytest.mark.parametrize("first", ["i32", "i8", "i64"])
+@pytest.mark.parametrize("op", list(OPMAP))
+def test_filter_two_pass(ctx, first, op):
+    rng = np.random.default_rng(op * 7 + len(first))
+    n = TWO_PASS_N
+    c32 = rng.integers(-100, 100, n).astype(np.int32)
+    c8 = rng.integers(-128, 127, n).astype(np.int8)
+    c64 = rng.integers(-2 ** 40, 2 ** 40, n, dtype=np.int64)
+    cols = {"i32": [c32, c8, c64], "i8": [c8, c32, c64], "i64": [c64, c32, c8]}[first]
+    lo = {"i32": (-7, 40), "i8": (-60, 11), "i64": (-2 ** 39, 2 ** 38)}[first]
+    preds = [(0, op, lo[0], lo[1]), (1, qe.GE, -50)]
+    sel, cnt = qe.qe_filter(ctx, [cuda(c) for c in cols], preds)
+    ref = O.filter(cols, [O.Pred(c, OPMAP[o], a, b[0] if b else 0) for c, o, a, *b in preds])
+    assert int(cnt.item()) == len(ref)
+    assert np.array_equal(sel[:len(ref)].cpu().numpy(), ref)
+
+
+def test_filter_two_pass_bounds_and_views(ctx):
+    n = TWO_PASS_N
+    date = datagen.star_fact(n, 10, seed=9)["date"].numpy()
+    d = cuda(date)
+    # a range that clamps to the column's width, and the empty ranges
+    for pred, o_pred in (((0, qe.LT, 2 ** 40), O.Pred(0, O.LT, 2 ** 40)),
+                         ((0, qe.GT, 2 ** 40), O.Pred(0, O.GT, 2 ** 40)),
+                         ((0, qe.NE, -(2 ** 40)), O.Pred(0, O.NE, -(2 ** 40))),
+                         ((0, qe.BETWEEN, 900, 100), O.Pred(0, O.BETWEEN, 900, 100))):
+        sel, cnt = qe.qe_filter(ctx, [d], [pred])
+        ref = O.filter([date], [o_pred])
+        assert int(cnt.item()) == len(ref)
+        assert np.array_equal(sel[:len(ref)].cpu().numpy(), ref)
+    for off in (1, 2):
+        sel, cnt = qe.qe_filter(ctx, [d[off:]], [(0, qe.LT, 999)])
+        ref = O.filter([date[off:]], [O.Pred(0, O.LT, 999)])
+        assert np.array_equal(sel[:int(cnt.item())].cpu().numpy(), ref)
+    # capacity: the first rows are written, the required size reported
+    out = torch.full((1000,), -1, dtype=torch.int32, device="cuda")
+    with pytest.raises(qe.QeError) as e:
+        qe.qe_filter(ctx, [d], [(0, qe.LT, 1278)], out_sel=out)
+    ref = O.filter([date], [O.Pred(0, O.LT, 1278)])
+    assert e.value.status == qe.ERR_CAPACITY and e.value.required == len(ref)
+    assert np.array_equal(out.cpu().numpy(), ref[:1000])
+
+
 def test_filter_capacity_error(ctx):
     date = cuda(np.arange(10_000, dtype=np.int32))
     out = torch.full((100,), -1, dtype=torch.int32, device="cuda")
@@ -174,6 +222,26 @@ def test_join_probe(ctx, layout, with_sel):
     ht = qe.qe_join_build(ctx, cuda(bk), cuda(bp), layout=layout)
     info = ht.info()
     assert info.layout == (qe.HT_DENSE if layout == qe.HT_AUTO else layout)
+    rows, pay, cnt = qe.qe_join_probe(ctx, ht, cuda(pk), cuda(sel) if with_sel else None)
+    rr, rp = O.join(bk, bp, pk, sel)
+    c = int(cnt.item())
+    assert c == len(rr)
+    assert np.array_equal(rows[:c].cpu().numpy(), rr)
+    assert np.array_equal(pay[:c].cpu().numpy(), rp)
+    ht.destroy()
+
+
+@pytest.mark.parametrize("layout", [qe.HT_DENSE, qe.HT_OPEN])
+@pytest.mark.parametrize("with_sel", [False, True])
+def test_join_probe_two_pass(ctx, layout, with_sel):
+    """Large probes take the two-pass compaction."""
+    rng = np.random.default_rng(layout * 2 + with_sel + 10)
+    nb, npr = 300_000, 9_000_007
+    bk = rng.choice(np.arange(-500_000, 500_000), nb, replace=False).astype(np.int32)
+    bp = rng.integers(-2 ** 31, 2 ** 31 - 1, nb).astype(np.int32)
+    pk = rng.integers(-600_000, 600_000, npr).astype(np.int32)
+    sel = np.sort(rng.choice(npr, 5_000_000, replace=False)).astype(np.int32) if with_sel else None
+    ht = qe.qe_join_build(ctx, cuda(bk), cuda(bp), layout=layout)
     rows, pay, cnt = qe.qe_join_probe(ctx, ht, cuda(pk), cuda(sel) if with_sel else None)
     rr, rp = O.join(bk, bp, pk, sel)
     c = int(cnt.item())
