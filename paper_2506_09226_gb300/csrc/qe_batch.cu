@@ -28,8 +28,8 @@ constexpr int BUILD_ROWS = 1 << 16; // dimension rows per build item
 
 struct BatchItem {
     int32_t pipe;
-    int32_t kind;                   // 0 build, 1 probe
-    int64_t row0, row1;
+    int32_t kind;                   // 0 build: dimension rows [row0, row1)
+    int64_t row0, row1;             // 1 probe: item row0 of the pipeline's nprobe, over fact rows [0, row1)
 };
 
 struct BatchPipe {
@@ -129,22 +129,32 @@ __device__ void batch_finalize(const BatchPipe &B, qe_dev_status *st)
 }
 
 // The row paths of a probe item, each out of line so that each gets its own
-// register allocation.
-__device__ __noinline__ void item_star_smem(const PipeSpec &P, unsigned long long *sm, int64_t r0, int64_t r1)
+// register allocation.  Item j of a pipeline's m probe items takes the tiles
+// j, j + m, j + 2m, ... of its fact rows [0, n), one tile per call: the blocks
+// working on one pipeline read neighbouring tiles at any moment.  Measured on
+// GB300 this beats contiguous item ranges (4.39 vs 4.79 ms for 300 pipelines
+// of 1K-10M rows, 4.85 vs 5.48 ms for one of 400M rows) and also one strided
+// pass that prefetches the next tile across the stride (4.67 / 5.32 ms).
+constexpr int64_t STAR_TR = static_cast<int64_t>(BT) * 3;
+
+__device__ __noinline__ void item_star_smem(const PipeSpec &P, unsigned long long *sm, int64_t j, int64_t m, int64_t n)
 {
-    star_range<false, 3, BT>(P, sm, r0, r1, BT * 3);
+    for (int64_t t = j * STAR_TR; t < n; t += m * STAR_TR)
+        star_range<false, 3, BT>(P, sm, t, t + STAR_TR < n ? t + STAR_TR : n, STAR_TR);
 }
 
-__device__ __noinline__ void item_star_global(const PipeSpec &P, unsigned long long *sm, int64_t r0, int64_t r1)
+__device__ __noinline__ void item_star_global(const PipeSpec &P, unsigned long long *sm, int64_t j, int64_t m,
+                                              int64_t n)
 {
-    star_range<true, 3, BT>(P, sm, r0, r1, BT * 3);
+    for (int64_t t = j * STAR_TR; t < n; t += m * STAR_TR)
+        star_range<true, 3, BT>(P, sm, t, t + STAR_TR < n ? t + STAR_TR : n, STAR_TR);
 }
 
-__device__ __noinline__ void item_generic(const PipeSpec &P, const TableCfg T, unsigned long long *sm, int64_t r0,
-                                          int64_t r1)
+__device__ __noinline__ void item_generic(const PipeSpec &P, const TableCfg T, unsigned long long *sm, int64_t j,
+                                          int64_t m, int64_t r1)
 {
     constexpr int TR = BT * B_ITEMS;
-    for (int64_t t0 = r0; t0 < r1; t0 += TR) {
+    for (int64_t t0 = j * TR; t0 < r1; t0 += m * TR) {
         RowVals v[B_ITEMS];
 #pragma unroll
         for (int k = 0; k < B_ITEMS; k++) {
@@ -213,9 +223,9 @@ __global__ void __launch_bounds__(BT, 1) k_batch(BatchArgs A)
         if (!s_flag) {
             table_zero(P, T, sm);
             __syncthreads();
-            if (B.star && T.mode == TM_SMEM_DENSE) item_star_smem(P, sm, I.row0, I.row1);
-            else if (B.star) item_star_global(P, sm, I.row0, I.row1);
-            else item_generic(P, T, sm, I.row0, I.row1);
+            if (B.star && T.mode == TM_SMEM_DENSE) item_star_smem(P, sm, I.row0, B.nprobe, I.row1);
+            else if (B.star) item_star_global(P, sm, I.row0, B.nprobe, I.row1);
+            else item_generic(P, T, sm, I.row0, B.nprobe, I.row1);
             __syncthreads();
             table_flush(P, T, sm);
         }
@@ -369,10 +379,7 @@ extern "C" qe_status qe_batch_create(qe_ctx *ctx, const qe_pipeline_desc *descs,
             items.push_back({i, 0, r0, std::min<int64_t>(descs[i].n_dim, r0 + BUILD_ROWS)});
         }
     for (int i = 0; i < n; i++)
-        for (int j = 0; j < pipes[i].nprobe; j++) {
-            const int64_t r0 = static_cast<int64_t>(j) * item_rows;
-            items.push_back({i, 1, r0, std::min<int64_t>(descs[i].n_fact, r0 + item_rows)});
-        }
+        for (int j = 0; j < pipes[i].nprobe; j++) items.push_back({i, 1, j, descs[i].n_fact});
     const size_t pipes_bytes = up(sizeof(BatchPipe) * n), items_bytes = up(sizeof(BatchItem) * items.size());
 
     qe_batch *b = new qe_batch();
