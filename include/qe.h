@@ -166,7 +166,9 @@ qe_status qe_profile_reset(qe_ctx *ctx);
  *   preds:  npreds (0..QE_MAX_PREDS) comparisons over those columns;
  *   out_sel: device int32 [sel_capacity]; rows past the capacity are not
  *            written and QE_ERR_CAPACITY is recorded (required = count).
- * nrows must be < 2^31. */
+ * nrows must be < 2^31.  From 4M rows on the filter runs in two passes
+ * (count per 512-row segment, then write), with scratch of about 8 bytes per
+ * 512 rows from the context's budget. */
 qe_status qe_filter(qe_ctx *ctx, const qe_col *cols, int ncols, const qe_pred *preds,
                     int npreds, int64_t nrows, int32_t *out_sel, int64_t sel_capacity,
                     int64_t *out_count, void *stream);
@@ -180,7 +182,9 @@ qe_status qe_filter(qe_ctx *ctx, const qe_col *cols, int ncols, const qe_pred *p
  * own allocator (a library cudaMalloc would fail or fragment that pool), and
  * latency-critical callers that cannot afford an allocator call, which may
  * synchronize the device.  Arguments, result and errors are those of
- * qe_filter, computed by the same kernel.
+ * qe_filter; the rows are computed by the one-pass compaction kernel (the
+ * one qe_filter uses below 4M rows; above, qe_filter runs two passes with
+ * allocated scratch).
  *
  * Its scratch (a tile counter and one look-back status word per 4,096-row
  * tile, about 512 KB) is a static device array inside libqe, which every GPU
