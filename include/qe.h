@@ -278,7 +278,10 @@ qe_status qe_join_build(qe_ctx *ctx, const int32_t *keys, const int32_t *payload
  * position order (stable compaction).
  *   out_probe_row, out_build_payload: device int32 [capacity];
  *   *out_count (device int64): number of matches; past the capacity nothing
- *   is written and QE_ERR_CAPACITY is recorded. */
+ *   is written and QE_ERR_CAPACITY is recorded.
+ * From 4M positions on the probe runs in two passes (count per 256-position
+ * segment, then write; every lookup is made twice), with scratch of about 8
+ * bytes per 256 positions from the context's budget. */
 qe_status qe_join_probe(qe_ctx *ctx, const qe_hash_table *ht, const int32_t *probe_keys,
                         const int32_t *sel, int64_t n, int32_t *out_probe_row,
                         int32_t *out_build_payload, int64_t capacity, int64_t *out_count,
