@@ -95,6 +95,22 @@ class qe_batch_opts(ctypes.Structure):
                 ("smem_slots", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
 
 
+# exchange planner (include/qe_plan.h)
+EXCH_BROADCAST, EXCH_SHUFFLE = 0, 1
+JOIN_LOCAL, JOIN_BROADCAST_R, JOIN_BROADCAST_S, JOIN_SHUFFLE_BOTH = range(4)
+
+
+class qe_link(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_double), ("c", ctypes.c_double)]
+
+
+class qe_cluster(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("V", ctypes.c_int32), ("bcast_net", qe_link), ("bcast_gpu", qe_link),
+                ("shuf_net", qe_link), ("shuf_gpu", qe_link)]
+
+
+_DP = ctypes.POINTER(ctypes.c_double)
+
 _lib = None
 _SIGS = {
     "qe_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_size_t]),
@@ -140,6 +156,14 @@ _SIGS = {
     "qe_batch_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(qe_pipeline_desc),
                                     ctypes.POINTER(qe_groups_out), ctypes.c_int, ctypes.POINTER(qe_batch_opts),
                                     ctypes.c_void_p]),
+    "qe_plan_exchange_time": (ctypes.c_int, [ctypes.POINTER(qe_cluster), ctypes.c_int32, ctypes.c_double, _DP]),
+    "qe_plan_shuffle_skew": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _DP, ctypes.c_double, _DP, _DP, _DP]),
+    "qe_plan_join": (ctypes.c_int, [ctypes.POINTER(qe_cluster), ctypes.c_double, ctypes.c_double, ctypes.c_int32,
+                                    _DP, _DP, ctypes.POINTER(ctypes.c_int32), _DP, _DP]),
+    "qe_plan_fit_link": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _DP, _DP, ctypes.c_int64,
+                                        ctypes.POINTER(qe_link)]),
+    "qe_plan_skew_gradient": (ctypes.c_int, [ctypes.c_int32, ctypes.c_double, ctypes.c_double, _DP]),
+    "qe_plan_last_error": (ctypes.c_char_p, []),
 }
 
 EXPORTED = sorted(_SIGS)
@@ -487,3 +511,91 @@ def qe_batch_run(ctx: Context, descs, outs, opts=None, stream=None, check=True):
     ctx.check(ctx.lib.qe_batch_run(ctx.h, cd, co, n, ctypes.byref(o), _stream(stream)))
     if check:
         ctx.sync_status(stream)
+
+
+# ------------------------------------------------------------ exchange planner
+# Host-only entry points of include/qe_plan.h: no GPU or context needed.
+def link(bandwidth: float | None = None, L: float = 0.0, c: float | None = None) -> qe_link:
+    """A link of constant `bandwidth` bytes/s, or Hockney parameters (L, c)."""
+    if bandwidth is not None:
+        return qe_link(0.0, 1.0 / bandwidth)
+    return qe_link(L, 0.0 if c is None else c)
+
+
+def cluster(k: int, V: int, bcast_net: qe_link, bcast_gpu: qe_link, shuf_net: qe_link | None = None,
+            shuf_gpu: qe_link | None = None) -> qe_cluster:
+    """V machines of k GPUs; the shuffle links default to the broadcast's."""
+    return qe_cluster(k, V, bcast_net, bcast_gpu, shuf_net if shuf_net is not None else bcast_net,
+                      shuf_gpu if shuf_gpu is not None else bcast_gpu)
+
+
+def _plan_check(lib, st):
+    if st != OK:
+        raise QeError(st, lib.qe_plan_last_error().decode())
+
+
+def _f64(x):
+    import numpy as np
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    return a, a.ctypes.data_as(_DP)
+
+
+def qe_plan_exchange_time(cl: qe_cluster, op: int, nbytes: float) -> float:
+    lib = load_library()
+    t = ctypes.c_double(0)
+    _plan_check(lib, lib.qe_plan_exchange_time(ctypes.byref(cl), op, float(nbytes), ctypes.byref(t)))
+    return t.value
+
+
+def qe_plan_shuffle_skew(k: int, V: int, msg, bn: float):
+    """(seconds, per-machine sent bytes, per-machine received bytes)."""
+    import numpy as np
+    lib = load_library()
+    m, mp = _f64(msg)
+    if m.size != (k * V) ** 2:
+        raise QeError(ERR_INVALID_ARG, "msg must hold N*N sizes")
+    send, recv = np.zeros(max(V, 0)), np.zeros(max(V, 0))
+    t = ctypes.c_double(0)
+    _plan_check(lib, lib.qe_plan_shuffle_skew(k, V, mp, float(bn), ctypes.byref(t), send.ctypes.data_as(_DP),
+                                              recv.ctypes.data_as(_DP)))
+    return t.value, send, recv
+
+
+def qe_plan_join(cl: qe_cluster, r_bytes: float, s_bytes: float, copartitioned: bool = False, r_msg=None,
+                 s_msg=None):
+    """(strategy, broadcast seconds, shuffle seconds)."""
+    lib = load_library()
+    N = cl.k * cl.V
+    ptrs, keep = [], []
+    for m in (r_msg, s_msg):
+        if m is None:
+            ptrs.append(None)
+            continue
+        a, p = _f64(m)
+        if a.size != N * N:
+            raise QeError(ERR_INVALID_ARG, "a message matrix must hold N*N sizes")
+        keep.append(a)
+        ptrs.append(p)
+    st, tb, ts = ctypes.c_int32(-1), ctypes.c_double(0), ctypes.c_double(0)
+    _plan_check(lib, lib.qe_plan_join(ctypes.byref(cl), float(r_bytes), float(s_bytes), int(bool(copartitioned)),
+                                      ptrs[0], ptrs[1], ctypes.byref(st), ctypes.byref(tb), ctypes.byref(ts)))
+    return st.value, tb.value, ts.value
+
+
+def qe_plan_fit_link(op: int, k: int, V: int, sizes, times) -> qe_link:
+    lib = load_library()
+    b, bp = _f64(sizes)
+    t, tp = _f64(times)
+    if b.size != t.size:
+        raise QeError(ERR_INVALID_ARG, "sizes and times differ in length")
+    out = qe_link()
+    _plan_check(lib, lib.qe_plan_fit_link(op, k, V, bp, tp, b.size, ctypes.byref(out)))
+    return out
+
+
+def qe_plan_skew_gradient(n_gpus: int, f: float, total: float):
+    import numpy as np
+    lib = load_library()
+    out = np.zeros(max(n_gpus, 0))
+    _plan_check(lib, lib.qe_plan_skew_gradient(n_gpus, float(f), float(total), out.ctypes.data_as(_DP)))
+    return out

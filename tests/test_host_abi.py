@@ -3,6 +3,7 @@ every entry point qe.h declares, the ctypes mirrors of the ABI structs match
 the C layout (compiled with gcc from qe.h), and the autotuner's search and
 cache logic."""
 import ctypes
+import glob
 import os
 import re
 import subprocess
@@ -13,11 +14,12 @@ from paper_2506_09226_gb300 import qe, tune
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HDR = os.path.join(ROOT, "include", "qe.h")
+HDRS = sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
 LIB = os.path.join(ROOT, "paper_2506_09226_gb300", "libqe.so")
 
 
 def declared_functions():
-    src = open(HDR).read()
+    src = "".join(open(h).read() for h in HDRS)
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(qe_[a-z_0-9]+)\s*\(", src)))
 
@@ -50,11 +52,13 @@ STRUCTS = {
     "qe_col": qe.qe_col, "qe_pred": qe.qe_pred, "qe_groups_out": qe.qe_groups_out,
     "qe_build_opts": qe.qe_build_opts, "qe_ht_info": qe.qe_ht_info, "qe_agg": qe.qe_agg,
     "qe_agg_spec": qe.qe_agg_spec, "qe_pipeline_desc": qe.qe_pipeline_desc, "qe_batch_opts": qe.qe_batch_opts,
+    "qe_link": qe.qe_link, "qe_cluster": qe.qe_cluster,
 }
 
 
 def test_ctypes_layouts_match_header(tmp_path):
-    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "qe.h"', "int main(void) {"]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "qe.h"', '#include "qe_plan.h"',
+             "int main(void) {"]
     for name, cls in STRUCTS.items():
         lines.append(f'printf("{name} sizeof %zu\\n", sizeof({name}));')
         for fname, _ in cls._fields_:
