@@ -123,25 +123,26 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- kernel traffic record
-def kernel_source_hash():
+def kernel_source_hash(sources):
+    """sha256 prefix over the files a kernel is compiled from (paths relative
+    to the repository root, in the order given)."""
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2506_09226_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in sources:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def recorded_traffic(kernel: str, units: int):
     """DRAM bytes per launch from the committed ncu record, scaled to `units`,
-    or None when the record is missing or the kernels changed since."""
+    or None when the record is missing or any of the kernel's sources changed
+    since the capture."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(p))
+        r = d[kernel]
+        if r["source_hash"] != kernel_source_hash(r["sources"]):
+            return None
     except Exception:
-        return None
-    r = d.get(kernel)
-    if not r or r.get("source_hash") != kernel_source_hash():
         return None
     return r["dram_bytes_per_unit"] * units
 

@@ -22,7 +22,8 @@
 //                      k_part_scatter (qe_part_general.cuh; any payloads, any
 //                        fan-out): bulk-copy (TMA) double-buffered chunks and
 //                        a one- or two-digit LSD ranking.
-#include "qe_pipe_core.cuh"
+#include "qe_internal.cuh"
+#include "qe_tma.cuh"
 
 namespace {
 
