@@ -32,6 +32,7 @@ I8, I32, I64 = 0, 1, 2
 LT, LE, GT, GE, EQ, NE, BETWEEN = range(7)
 SUM, COUNT, MIN, MAX = range(4)
 JOIN_PAYLOAD = -2
+INNER, SEMI, ANTI = 0, 1, 2
 DUPLICATE_KEY = 5
 
 _NP_TYPE = {np.dtype(np.int8): I8, np.dtype(np.int32): I32, np.dtype(np.int64): I64}
@@ -70,11 +71,13 @@ def lib():
         L.oracle_groupby.argtypes = [i64, vp, ci, vp, vp, vp, vp]
         L.oracle_group_key.restype = i64
         L.oracle_group_key.argtypes = [ci, i64, i64]
+        L.oracle_semi_join.restype = i64
+        L.oracle_semi_join.argtypes = [i64, vp, i64, vp, vp, ci, vp]
         L.oracle_pipeline.restype = i64
-        L.oracle_pipeline.argtypes = [i64, vp, vp, ci, vp, vp, vp, vp, ci, i64, vp, vp,
+        L.oracle_pipeline.argtypes = [i64, vp, vp, ci, vp, vp, vp, vp, ci, i64, vp, vp, ci,
                                       ci, ci, ci, vp, vp, vp, vp, vp, vp, vp]
         L.oracle_pipeline_group.restype = i64
-        L.oracle_pipeline_group.argtypes = [i64, vp, vp, ci, vp, vp, vp, vp, ci, i64, vp, vp,
+        L.oracle_pipeline_group.argtypes = [i64, vp, vp, ci, vp, vp, vp, vp, ci, i64, vp, vp, ci,
                                             ci, ci, ci, vp, vp, vp, i64, vp]
         _ = i32
         _lib = L
@@ -157,6 +160,17 @@ def join(build_keys, build_payload, probe_keys, sel=None):
     return rows[:cnt.value].copy(), pay[:cnt.value].copy()
 
 
+def semi_join(build_keys, probe_keys, sel=None, anti=False):
+    """Probe rows (in probe order) whose key is among the build keys, or,
+    with anti, is not; build keys may repeat."""
+    bk, pk = _c(build_keys, np.int32), _c(probe_keys, np.int32)
+    s = None if sel is None else _c(sel, np.int32)
+    n = len(pk) if s is None else len(s)
+    rows = np.empty(max(n, 1), np.int32)
+    cnt = lib().oracle_semi_join(len(bk), _p(bk), n, _p(pk), _p(s), int(bool(anti)), _p(rows))
+    return rows[:cnt].copy()
+
+
 def groupby(keys, aggs):
     """aggs: list of (op, values or None).  Returns (keys, [agg arrays]) sorted by key."""
     keys = _c(keys, np.int64)
@@ -180,12 +194,13 @@ class Query:
 
     fk_col < 0 means no join; key_lo_col == JOIN_PAYLOAD takes the low key
     half from the joined dim payload; aggs are (op, col_a, col_b) with -1 for
-    an absent column."""
+    an absent column; join_kind is INNER, SEMI or ANTI."""
     preds: list = field(default_factory=list)
     fk_col: int = -1
     key_hi_col: int = -1
     key_lo_col: int = JOIN_PAYLOAD
     aggs: list = field(default_factory=list)
+    join_kind: int = 0
 
 
 def _query_args(fact, q: Query, dim_key, dim_pay):
@@ -203,7 +218,8 @@ def _query_args(fact, q: Query, dim_key, dim_pay):
     keep = (fact, types, pc, po, lo, hi, dk, dp, ops, aa, ab)
     n = len(fact[0]) if fact else 0
     args = [n, _ptr_array(fact), _p(types), len(q.preds), _p(pc), _p(po), _p(lo), _p(hi),
-            q.fk_col, len(dk), _p(dk), _p(dp), q.key_hi_col, q.key_lo_col, len(q.aggs),
+            q.fk_col, len(dk), _p(dk), _p(dp) if dim_pay is not None else None, q.join_kind,
+            q.key_hi_col, q.key_lo_col, len(q.aggs),
             _p(ops), _p(aa), _p(ab)]
     return args, keep
 
@@ -218,6 +234,8 @@ def pipeline(fact, q: Query, dim_key=None, dim_pay=None):
     ng = lib().oracle_pipeline(*args, _p(out_k), _ptr_array(out_a), ctypes.byref(nsel),
                                ctypes.byref(nj))
     del keep
+    if ng == -2:
+        raise ValueError("a semi- or anti-join has no payload to group by")
     if ng < 0:
         raise ValueError("duplicate build key")
     return dict(keys=out_k[:ng].copy(), aggs=[a[:ng].copy() for a in out_a],

@@ -18,7 +18,8 @@
  *                 the per-sender offsets into one contiguous tensor per
  *                 column);
  *   - join:       inner equi-join of a probe column against unique build
- *                 keys (Sec. 2.2, the local join after exchange);
+ *                 keys (Sec. 2.2, the local join after exchange), and the
+ *                 semi- and anti-join (membership in the build keys);
  *   - group-by:   SUM / COUNT / MIN / MAX per distinct key (Sec. 2.3, the
  *                 aggregation kinds of the final reduction; Sec. 2.4, group
  *                 by in the compiled tensor program);
@@ -200,6 +201,43 @@ int oracle_join(int64_t nb, const int32_t *bkeys, const int32_t *bpay,
     return OR_OK;
 }
 
+static int cmp_i32(const void *a, const void *b)
+{
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+/*
+ * Semi- and anti-join: the EXISTS and NOT EXISTS forms of the local join
+ * (Sec. 2.2), which the TPC-H queries the paper runs (Sec. 6.1) contain.
+ * For each probe position i in order (the row sel[i], or i when sel is
+ * NULL) the row is emitted when some build key equals its key (anti = 0),
+ * or when no build key does (anti = 1).  Build keys may repeat: only
+ * membership matters.  The lookup is a binary search of the sorted build
+ * keys.  Returns the number of rows written to out_row.
+ */
+int64_t oracle_semi_join(int64_t nb, const int32_t *bkeys, int64_t np, const int32_t *pkeys,
+                         const int32_t *sel, int anti, int32_t *out_row)
+{
+    int32_t *b = (int32_t *)malloc((size_t)(nb > 0 ? nb : 1) * sizeof(int32_t));
+    if (nb > 0) memcpy(b, bkeys, (size_t)nb * sizeof(int32_t));
+    qsort(b, (size_t)nb, sizeof(int32_t), cmp_i32);
+    int64_t count = 0;
+    for (int64_t i = 0; i < np; i++) {
+        int32_t row = sel ? sel[i] : (int32_t)i;
+        int32_t k = pkeys[row];
+        int64_t lo = 0, hi = nb;           /* first index with key >= k */
+        while (lo < hi) {
+            int64_t mid = lo + (hi - lo) / 2;
+            if (b[mid] < k) lo = mid + 1; else hi = mid;
+        }
+        int found = lo < nb && b[lo] == k;
+        if (found != (anti != 0)) out_row[count++] = row;
+    }
+    free(b);
+    return count;
+}
+
 typedef struct { int64_t key; int64_t idx; } key_idx;
 
 static int cmp_key_idx(const void *a, const void *b)
@@ -280,31 +318,40 @@ static int64_t agg_value(const void *const *cols, const int *types, int a, int b
  *   filter   : the fact-side conjunction of predicates;
  *   join     : fact column fk_col probes the dim (key -> payload) rows; when
  *              fk_col < 0 there is no join and the payload is absent;
+ *              join_kind 0 is the inner join, 1 the semi-join (keep rows
+ *              with a match) and 2 the anti-join (keep rows without one);
+ *              the latter two carry no payload and allow repeated dim keys;
  *   group key: oracle_group_key over fact column key_hi_col (or none when
  *              < 0) and key_lo_col (a fact column, or the join payload when
  *              key_lo_col == -2);
  *   aggregate: agg_op[a] over fact columns agg_a[a] (times agg_b[a] when
  *              >= 0); COUNT takes no column.
  *
- * Output in ascending key order; returns the number of groups, or -1 on a
- * duplicate build key.  out_nsel / out_njoin, when not NULL, receive the
+ * Output in ascending key order; returns the number of groups, -1 on a
+ * duplicate build key of an inner join, or -2 when a semi- or anti-join asks
+ * for the join payload as key.  out_nsel / out_njoin, when not NULL, receive the
  * row counts after the filter and after the join.
  */
 int64_t oracle_pipeline(int64_t n_fact, const void *const *fact, const int *types,
                         int npreds, const int *pred_col, const int *pred_op,
                         const int64_t *lo, const int64_t *hi,
                         int fk_col, int64_t n_dim, const int32_t *dim_key,
-                        const int32_t *dim_pay,
+                        const int32_t *dim_pay, int join_kind,
                         int key_hi_col, int key_lo_col,
                         int naggs, const int *agg_op, const int *agg_a, const int *agg_b,
                         int64_t *out_keys, int64_t *const *out_aggs,
                         int64_t *out_nsel, int64_t *out_njoin)
 {
+    if (fk_col >= 0 && join_kind != 0 && key_lo_col == -2) return -2;
     int32_t *sel = (int32_t *)malloc((size_t)(n_fact > 0 ? n_fact : 1) * sizeof(int32_t));
     int64_t nsel = oracle_filter(n_fact, fact, types, npreds, pred_col, pred_op, lo, hi, sel);
     int32_t *rows = sel, *pay = NULL;
     int64_t nj = nsel;
-    if (fk_col >= 0) {
+    if (fk_col >= 0 && join_kind != 0) {
+        rows = (int32_t *)malloc((size_t)(nsel > 0 ? nsel : 1) * sizeof(int32_t));
+        nj = oracle_semi_join(n_dim, dim_key, nsel, (const int32_t *)fact[fk_col], sel,
+                              join_kind == 2, rows);
+    } else if (fk_col >= 0) {
         rows = (int32_t *)malloc((size_t)(nsel > 0 ? nsel : 1) * sizeof(int32_t));
         pay = (int32_t *)malloc((size_t)(nsel > 0 ? nsel : 1) * sizeof(int32_t));
         int st = oracle_join(n_dim, dim_key, dim_pay, nsel, (const int32_t *)fact[fk_col],
@@ -339,7 +386,8 @@ int64_t oracle_pipeline(int64_t n_fact, const void *const *fact, const int *type
 /*
  * One output group of the pipeline, computed on its own over the whole
  * input: the aggregates of group `gkey` are accumulated row by row over the
- * fact rows that pass the predicates, join, and map to gkey.  Used for
+ * fact rows that pass the predicates, join (join_kind as in
+ * oracle_pipeline), and map to gkey.  Used for
  * sampled checks of results too large for the full oracle.  The join lookup
  * goes through the dim rows whose payload could produce gkey, sorted by key.
  * Returns the group's row count (0 when the group is absent).
@@ -348,7 +396,7 @@ int64_t oracle_pipeline_group(int64_t n_fact, const void *const *fact, const int
                               int npreds, const int *pred_col, const int *pred_op,
                               const int64_t *lo, const int64_t *hi,
                               int fk_col, int64_t n_dim, const int32_t *dim_key,
-                              const int32_t *dim_pay,
+                              const int32_t *dim_pay, int join_kind,
                               int key_hi_col, int key_lo_col,
                               int naggs, const int *agg_op, const int *agg_a, const int *agg_b,
                               int64_t gkey, int64_t *out_aggs)
@@ -364,7 +412,7 @@ int64_t oracle_pipeline_group(int64_t n_fact, const void *const *fact, const int
             if (!can_match) continue;
         }
         b[nb].key = dim_key[j];
-        b[nb].payload = dim_pay[j];
+        b[nb].payload = dim_pay ? dim_pay[j] : 0;
         nb++;
     }
     qsort(b, (size_t)nb, sizeof(build_row), cmp_build_row);
@@ -386,8 +434,13 @@ int64_t oracle_pipeline_group(int64_t n_fact, const void *const *fact, const int
                 int64_t m = l + (h - l) / 2;
                 if (b[m].key < k) l = m + 1; else h = m;
             }
-            if (!(l < nb && b[l].key == k)) continue;
-            payload = b[l].payload;
+            int found = l < nb && b[l].key == k;
+            if (join_kind != 0) {
+                if (found == (join_kind == 2)) continue;     /* semi: needs a match, anti: none */
+            } else {
+                if (!found) continue;
+                payload = b[l].payload;
+            }
         }
         int64_t hiv = key_hi_col >= 0 ? col_get(fact[key_hi_col], types[key_hi_col], i) : 0;
         int64_t lov = key_lo_col == -2 ? payload : col_get(fact[key_lo_col], types[key_lo_col], i);

@@ -251,6 +251,82 @@ def test_join_fk_invariant():
     assert np.array_equal(pay, direct[fk[sel]])
 
 
+# ---------------------------------------------------------------- semi- and anti-join
+def bf_semi(bkeys, pkeys, sel, anti):
+    """Nested loop: position i keeps its row when any build key equals its key
+    (or, anti, when none does)."""
+    rows = range(len(pkeys)) if sel is None else [int(r) for r in sel]
+    out = []
+    for r in rows:
+        found = any(int(b) == int(pkeys[r]) for b in bkeys)
+        if found != anti:
+            out.append(int(r))
+    return out
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_semi_anti_match_nested_loop(seed):
+    rng = np.random.default_rng(100 + seed)
+    nb = int(rng.integers(0, 150))
+    bkeys = rng.integers(-200, 200, nb).astype(np.int32)          # repeats allowed
+    pkeys = rng.integers(-220, 220, 300).astype(np.int32)
+    sel = np.sort(rng.choice(300, 120, replace=False)).astype(np.int32)
+    for s in (None, sel):
+        for anti in (False, True):
+            assert O.semi_join(bkeys, pkeys, s, anti).tolist() == bf_semi(bkeys, pkeys, s, anti)
+
+
+def test_semi_anti_invariants():
+    rng = np.random.default_rng(9)
+    bkeys = rng.integers(0, 50, 80).astype(np.int32)
+    pkeys = rng.integers(0, 100, 500).astype(np.int32)
+    sel = np.sort(rng.choice(500, 200, replace=False)).astype(np.int32)
+    semi, anti = O.semi_join(bkeys, pkeys, sel), O.semi_join(bkeys, pkeys, sel, anti=True)
+    # the two split the probe positions: disjoint, and together every position in order
+    assert not set(semi.tolist()) & set(anti.tolist())
+    assert sorted(semi.tolist() + anti.tolist()) == sel.tolist()
+    # with unique build keys the semi-join keeps exactly the inner join's rows
+    ub = np.unique(bkeys)
+    rows, _ = O.join(ub, np.zeros(len(ub), np.int32), pkeys, sel)
+    assert O.semi_join(ub, pkeys, sel).tolist() == rows.tolist()
+    # repeated build keys change nothing
+    assert O.semi_join(np.concatenate([bkeys, bkeys]), pkeys, sel).tolist() == semi.tolist()
+    # empty sides
+    assert O.semi_join(np.empty(0, np.int32), pkeys).tolist() == []
+    assert O.semi_join(np.empty(0, np.int32), pkeys, anti=True).tolist() == list(range(500))
+    assert O.semi_join(bkeys, np.empty(0, np.int32)).tolist() == []
+
+
+@pytest.mark.parametrize("kind", [O.SEMI, O.ANTI])
+def test_pipeline_semi_anti_matches_composition(kind):
+    """group-by over filter, then EXISTS / NOT EXISTS against repeated dim
+    keys, restated from the brute-force operators; and one group computed
+    on its own."""
+    rng = np.random.default_rng(4 + kind)
+    nf = 500
+    dk = rng.integers(0, 120, 90).astype(np.int32)
+    fact = [rng.integers(0, 200, nf).astype(np.int32), rng.integers(0, 2557, nf).astype(np.int32),
+            rng.integers(100, 10 ** 7, nf).astype(np.int64), rng.integers(1, 51, nf).astype(np.int32),
+            rng.integers(0, 3, nf).astype(np.int8)]
+    q = O.Query(preds=[O.Pred(1, O.LT, 1278)], fk_col=0, key_hi_col=-1, key_lo_col=4,
+                aggs=[(O.SUM, 2, 3), (O.COUNT, -1, -1), (O.MIN, 2, -1), (O.MAX, 2, -1)], join_kind=kind)
+    r = O.pipeline(fact, q, dk)
+    sel = bf_filter(fact, q.preds)
+    kept = bf_semi(dk, fact[0], sel, kind == O.ANTI)
+    keys = [int(fact[4][i]) for i in kept]
+    vals = [int(fact[2][i]) * int(fact[3][i]) for i in kept]
+    price = [int(fact[2][i]) for i in kept]
+    ref = bf_groupby(keys, [(O.SUM, vals), (O.COUNT, None), (O.MIN, price), (O.MAX, price)])
+    assert r["keys"].tolist() == sorted(ref)
+    for i, k in enumerate(r["keys"].tolist()):
+        assert [int(a[i]) for a in r["aggs"]] == ref[k]
+    assert r["nsel"] == len(sel) and r["njoin"] == len(kept)
+    cnt, aggs = O.pipeline_group(fact, q, int(r["keys"][0]), dk)
+    assert cnt == ref[int(r["keys"][0])][1] and aggs.tolist() == ref[int(r["keys"][0])]
+    with pytest.raises(ValueError):
+        O.pipeline(fact, O.Query(**{**q.__dict__, "key_lo_col": O.JOIN_PAYLOAD}), dk)
+
+
 # ---------------------------------------------------------------- group-by
 @pytest.mark.parametrize("seed", range(3))
 def test_groupby_matches_dict(seed):
