@@ -254,13 +254,13 @@ typedef struct {
 typedef struct {
     int32_t layout;       /* QE_HT_DENSE or QE_HT_OPEN */
     int32_t full;         /* dense table whose every slot is occupied */
-    int64_t nkeys;
+    int64_t nkeys;        /* build rows (a key set counts repeats) */
     int64_t slots;
     int64_t bytes;
     int32_t key_min, key_max;
     int32_t have_payload_range;   /* payload range known (read back with the key range) */
     int32_t payload_min, payload_max;
-    int32_t pad;
+    int32_t key_set;      /* built by qe_join_build_set: membership only */
 } qe_ht_info;
 
 /* Hash-join build (Sec. 2.2: the local join once both inputs are
@@ -286,6 +286,30 @@ qe_status qe_join_probe(qe_ctx *ctx, const qe_hash_table *ht, const int32_t *pro
                         const int32_t *sel, int64_t n, int32_t *out_probe_row,
                         int32_t *out_build_payload, int64_t capacity, int64_t *out_count,
                         void *stream);
+
+/* Key-set build for the semi- and anti-join: the EXISTS / NOT EXISTS forms
+ * of the local join (Sec. 2.2) that the TPC-H queries the paper runs
+ * (Sec. 6.1) contain.  Inserts key[j] for j < nrows; keys may repeat and no
+ * payload is stored (a dense set is its occupancy bitmap alone, range/8
+ * bytes).  opts as for qe_join_build (have_range skips the range read-back).
+ * The open-addressing layout reserves INT32_MIN (QE_ERR_RESERVED_KEY).
+ * A key set serves qe_join_semi and pipelines with a semi- or anti-join;
+ * qe_join_probe rejects it (QE_ERR_INVALID_ARG: it has no payloads). */
+qe_status qe_join_build_set(qe_ctx *ctx, const int32_t *keys, int64_t nrows, const qe_build_opts *opts,
+                            qe_hash_table **out, void *stream);
+
+/* Semi-join (anti = 0) or anti-join (anti = 1).  For each probe position
+ * i < n in order, row r = sel ? sel[i] : i is kept when probe_keys[r] is
+ * among the table's keys (semi) or is not (anti); the kept rows' ids are
+ * written in ascending position order (stable compaction).  `ht` may be a
+ * key set or a table from qe_join_build.
+ *   out_rows: device int32 [capacity]; *out_count (device int64) receives
+ *   the number of kept rows; past the capacity nothing is written and
+ *   QE_ERR_CAPACITY is recorded.
+ * From 4M positions on it runs in two passes, like qe_join_probe. */
+qe_status qe_join_semi(qe_ctx *ctx, const qe_hash_table *ht, const int32_t *probe_keys, const int32_t *sel,
+                       int64_t n, int anti, int32_t *out_rows, int64_t capacity, int64_t *out_count,
+                       void *stream);
 
 qe_status qe_join_info(const qe_hash_table *ht, qe_ht_info *info);
 
@@ -326,6 +350,10 @@ qe_status qe_groupby(qe_ctx *ctx, int64_t n, const int32_t *rows, qe_col key_hi,
 
 #define QE_JOIN_PAYLOAD (-2)
 
+/* Join of a pipeline: the inner join, or the semi- / anti-join that keeps
+ * the fact rows whose foreign key has a match / has none (no payload). */
+typedef enum { QE_JOIN_INNER = 0, QE_JOIN_SEMI = 1, QE_JOIN_ANTI = 2 } qe_join_kind;
+
 typedef struct {
     int32_t op;       /* qe_agg_op */
     int32_t a, b;     /* fact column indices; -1 = absent */
@@ -339,8 +367,13 @@ typedef struct {
  *   preds: conjunction over fact columns;
  *   fk_col: int32 fact column joined with the dimension keys, or -1 (no
  *           join);
+ *   join_kind: qe_join_kind.  A semi- or anti-join has no payload (so
+ *           key_lo_col may not be QE_JOIN_PAYLOAD), accepts repeated
+ *           dimension keys, and takes dim_payload = NULL;
  *   dim_key/dim_payload/n_dim: dimension columns (device int32), built into a
- *           table by the call when ht is NULL; or a prebuilt resident table;
+ *           table by the call when ht is NULL (a key set for a semi- or
+ *           anti-join); or a prebuilt resident table (a key set only with a
+ *           semi- or anti-join);
  *   group key: key_hi_col (fact column or -1) and key_lo_col (fact column or
  *           QE_JOIN_PAYLOAD), packed as in qe_groupby;
  *   aggs: over fact columns.
@@ -371,7 +404,7 @@ typedef struct {
      * correctly through the hash table.  Without it, a join-payload low part
      * takes its bounds from the join table when they are known. */
     int32_t have_key_range;
-    int32_t pad2;
+    int32_t join_kind;    /* qe_join_kind (0 = inner) */
     int64_t key_hi_min, key_hi_max, key_lo_min, key_lo_max;
 } qe_pipeline_desc;
 

@@ -68,7 +68,9 @@ __device__ void batch_build(const BatchPipe &B, const BatchItem &I, qe_dev_statu
             continue;
         }
         const uint32_t bit = 1u << (s & 31);
-        if (atomicOr(B.ht_bm + (s >> 5), bit) & bit) {
+        const uint32_t old = atomicOr(B.ht_bm + (s >> 5), bit);
+        if (!B.ht_pay) continue;          // a key set (semi- or anti-join): repeats are fine
+        if (old & bit) {
             dev_report(st, QE_ERR_DUPLICATE_KEY, 0);
             continue;
         }
@@ -304,14 +306,18 @@ extern "C" qe_status qe_batch_create(qe_ctx *ctx, const qe_pipeline_desc *descs,
         B.out = outs[i];
         int64_t pay_min = 1, pay_max = 0;
         if (B.P.has_join) {
+            const bool inner = B.P.join_kind == QE_JOIN_INNER;
             if (d.ht) {
+                if (inner && d.ht->set)
+                    return qe_fail(ctx, QE_ERR_INVALID_ARG,
+                                   "batch: pipeline " + std::to_string(i) + ": an inner join needs a table with payloads");
                 B.P.ht = ht_view(d.ht);
                 if (d.ht->have_pay) {
                     pay_min = d.ht->pay_min;
                     pay_max = d.ht->pay_max;
                 }
             } else {
-                if (!d.build.have_range || d.n_dim < 0 || (d.n_dim > 0 && (!d.dim_key || !d.dim_payload)))
+                if (!d.build.have_range || d.n_dim < 0 || (d.n_dim > 0 && (!d.dim_key || (inner && !d.dim_payload))))
                     return qe_fail(ctx, QE_ERR_INVALID_ARG,
                                    "batch: pipeline " + std::to_string(i) + " needs a prebuilt table or a key range");
                 const uint64_t range = static_cast<uint64_t>(static_cast<int64_t>(d.build.key_max) - d.build.key_min + 1);
@@ -323,9 +329,9 @@ extern "C" qe_status qe_batch_create(qe_ctx *ctx, const qe_pipeline_desc *descs,
                 B.P.ht.layout = QE_HT_DENSE;
                 B.P.ht.key_min = d.build.key_min;
                 B.P.ht.range = static_cast<uint32_t>(range);
-                B.P.ht.full = static_cast<uint64_t>(d.n_dim) == range ? 1 : 0;
+                B.P.ht.full = inner && static_cast<uint64_t>(d.n_dim) == range ? 1 : 0;
                 B.P.ht.coherent = 1;
-                sz[i].pay = up(range * 4);
+                sz[i].pay = inner ? up(range * 4) : 0;      // a key set is its bitmap alone
                 sz[i].bm = up(((range + 31) / 32) * 4);
                 B.nbuild = static_cast<int32_t>(qe_ceil_div(d.n_dim, BUILD_ROWS));
             }
@@ -399,9 +405,11 @@ extern "C" qe_status qe_batch_create(qe_ctx *ctx, const qe_pipeline_desc *descs,
         if (sz[i].pay) {
             B.ht_pay = reinterpret_cast<int32_t *>(base + nzo);
             nzo += sz[i].pay;
+            B.P.ht.payload = B.ht_pay;
+        }
+        if (sz[i].bm) {
             B.ht_bm = reinterpret_cast<uint32_t *>(base + zo);
             zo += sz[i].bm;
-            B.P.ht.payload = B.ht_pay;
             B.P.ht.bitmap = B.ht_bm;
         }
         if (sz[i].gd) {

@@ -43,6 +43,8 @@ struct qe_ctx {
     int tune_star_items = 0;        // 0: default
     int tune_force_generic = 0;
     int tune_part_general = 0;      // partition: skip the write-combining scatter
+    int tune_part_interleave = 0;   // partition: one pass over interleaved short ranges
+    int tune_part_one_pass_log2f = 9;   // partition: largest fan-out (log2) scattered in one pass
     bool profiling = false;
     std::mutex prof_mu;
     std::map<std::string, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>> prof;
@@ -340,6 +342,24 @@ __device__ __forceinline__ bool ht_lookup(const HtView &h, int32_t key, int32_t 
     return false;
 }
 
+// Membership only: the payload is not read (a key set has none).
+__device__ __forceinline__ bool ht_contains(const HtView &h, int32_t key)
+{
+    if (h.layout == QE_HT_DENSE) {
+        uint32_t s = static_cast<uint32_t>(key) - static_cast<uint32_t>(h.key_min);
+        if (s >= h.range) return false;
+        return h.full || ((ht_ld(h, h.bitmap + (s >> 5)) >> (s & 31)) & 1u);
+    }
+    uint32_t i = dev_fmix32(static_cast<uint32_t>(key)) & h.mask;
+    for (uint32_t probes = 0; probes <= h.mask; probes++) {
+        const int32_t k = static_cast<int32_t>(ht_ld(h, h.slots + i) >> 32);
+        if (k == key) return true;
+        if (k == HT_EMPTY_KEY) return false;
+        i = (i + 1) & h.mask;
+    }
+    return false;
+}
+
 // ---------------------------------------------- group tables
 // Keys are stored as key ^ INT64_MIN so that an all-zero slot is empty
 // (INT64_MIN itself is reserved).  Aggregates are stored so that zero is
@@ -596,11 +616,13 @@ struct qe_hash_table {
     int64_t slots = 0;
     void *mem = nullptr;
     size_t bytes = 0;
-    int32_t *payload = nullptr;
+    int32_t *payload = nullptr;       // NULL for a key set
     uint32_t *bitmap = nullptr;
     unsigned long long *open = nullptr;
+    int32_t set = 0;                  // key set: membership only, keys may repeat
 };
 
 HtView ht_view(const qe_hash_table *ht);
+// key_set: membership only (repeated keys allowed, payload ignored and not stored).
 qe_status join_build_impl(qe_ctx *ctx, const int32_t *keys, const int32_t *payload, int64_t nrows,
-                          const qe_build_opts *opts, qe_hash_table **out, cudaStream_t s);
+                          const qe_build_opts *opts, bool key_set, qe_hash_table **out, cudaStream_t s);

@@ -31,16 +31,18 @@ HtView ht_view(const qe_hash_table *ht)
 
 namespace {
 
-// Min and max of the build keys and of the payloads: mm = {kmin, kmax, pmin, pmax}.
+// Min and max of the build keys and of the payloads: mm = {kmin, kmax, pmin,
+// pmax}; without payloads (a key set) the payload half stays empty.
 __global__ void __launch_bounds__(256) k_minmax(const int32_t *keys, const int32_t *pay, int64_t n, int32_t *mm)
 {
     int32_t lo = INT_MAX, hi = INT_MIN, plo = INT_MAX, phi = INT_MIN;
     for (int64_t i = blockIdx.x * 256ll + threadIdx.x; i < n; i += static_cast<int64_t>(gridDim.x) * 256) {
-        const int32_t k = __ldcs(keys + i), p = __ldcs(pay + i);
+        const int32_t k = __ldcs(keys + i);
+        const int32_t p = pay ? __ldcs(pay + i) : INT_MAX;
         lo = min(lo, k);
         hi = max(hi, k);
         plo = min(plo, p);
-        phi = max(phi, p);
+        phi = pay ? max(phi, p) : phi;
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
@@ -65,6 +67,7 @@ __global__ void k_minmax_init(int32_t *mm)
     mm[3] = INT_MIN;
 }
 
+// payload == NULL: a key set (repeated keys are not an error).
 __global__ void __launch_bounds__(256) k_build_dense(const int32_t *keys, const int32_t *pay, int64_t n,
                                                      int32_t key_min, uint32_t range, int32_t *payload,
                                                      uint32_t *bitmap, qe_dev_status *st)
@@ -78,6 +81,7 @@ __global__ void __launch_bounds__(256) k_build_dense(const int32_t *keys, const 
         }
         const uint32_t bit = 1u << (s & 31);
         const uint32_t old = atomicOr(bitmap + (s >> 5), bit);
+        if (!payload) continue;
         if (old & bit) {
             dev_report(st, QE_ERR_DUPLICATE_KEY, 0);
             continue;
@@ -91,6 +95,7 @@ __global__ void __launch_bounds__(256) k_fill_u64(unsigned long long *p, int64_t
     for (int64_t i = blockIdx.x * 256ll + threadIdx.x; i < n; i += static_cast<int64_t>(gridDim.x) * 256) p[i] = v;
 }
 
+// pay == NULL: a key set (payload word 0, repeated keys are not an error).
 __global__ void __launch_bounds__(256) k_build_open(const int32_t *keys, const int32_t *pay, int64_t n,
                                                     unsigned long long *slots, uint32_t mask, qe_dev_status *st)
 {
@@ -101,7 +106,7 @@ __global__ void __launch_bounds__(256) k_build_open(const int32_t *keys, const i
             continue;
         }
         const unsigned long long w = (static_cast<unsigned long long>(static_cast<uint32_t>(k)) << 32) |
-                                     static_cast<uint32_t>(__ldcs(pay + i));
+                                     (pay ? static_cast<uint32_t>(__ldcs(pay + i)) : 0u);
         uint32_t h = dev_fmix32(static_cast<uint32_t>(k)) & mask;
         bool done = false;
         for (uint32_t probes = 0; probes <= mask && !done; probes++) {
@@ -109,7 +114,7 @@ __global__ void __launch_bounds__(256) k_build_open(const int32_t *keys, const i
             if (old == HT_EMPTY_SLOT) {
                 done = true;
             } else if (static_cast<int32_t>(old >> 32) == k) {
-                dev_report(st, QE_ERR_DUPLICATE_KEY, 0);
+                if (pay) dev_report(st, QE_ERR_DUPLICATE_KEY, 0);
                 done = true;
             } else {
                 h = (h + 1) & mask;
@@ -182,11 +187,58 @@ struct ProbeOp {
     }
 };
 
+// Semi- / anti-join as a stable compaction: position i keeps row sel[i] (or
+// i) when its key's membership differs from `anti`.
+struct SemiOp {
+    HtView ht;
+    const int32_t *keys;
+    const int32_t *sel;
+    int32_t *out_row;
+    int32_t anti;
+
+    struct Slot {
+        int32_t row[PROBE_ITEMS];
+    };
+    struct Pre {
+        int32_t row[PROBE_ITEMS];
+    };
+
+    template <int ITEMS>
+    __device__ __forceinline__ void load(int64_t pos0, const bool (&in)[ITEMS], Pre &p) const
+    {
+#pragma unroll
+        for (int k = 0; k < ITEMS; k++) {
+            int64_t i = pos0 + 32 * k;
+            p.row[k] = in[k] ? (sel ? __ldcs(sel + i) : static_cast<int32_t>(i)) : 0;
+        }
+    }
+
+    template <int ITEMS>
+    __device__ __forceinline__ void eval(int64_t, bool (&ok)[ITEMS], const Pre &pre, Slot &s) const
+    {
+        int32_t key[ITEMS];
+#pragma unroll
+        for (int k = 0; k < ITEMS; k++) {
+            s.row[k] = pre.row[k];
+            key[k] = ok[k] ? __ldg(keys + s.row[k]) : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < ITEMS; k++)
+            if (ok[k]) ok[k] = ht_contains(ht, key[k]) != static_cast<bool>(anti);
+    }
+
+    __device__ __forceinline__ void emit(int64_t o, int64_t, int k, const Slot &s) const
+    {
+        __stcs(out_row + o, s.row[k]);
+    }
+};
+
 }  // namespace
 
 qe_status join_build_impl(qe_ctx *ctx, const int32_t *keys, const int32_t *payload, int64_t nrows,
-                          const qe_build_opts *opts, qe_hash_table **out, cudaStream_t s)
+                          const qe_build_opts *opts, bool key_set, qe_hash_table **out, cudaStream_t s)
 {
+    if (key_set) payload = nullptr;   // the build kernels read no payloads for a key set
     qe_build_opts o{};
     if (opts) o = *opts;
     if (o.layout < QE_HT_AUTO || o.layout > QE_HT_OPEN) return qe_fail(ctx, QE_ERR_INVALID_ARG, "build: bad layout");
@@ -213,7 +265,7 @@ qe_status join_build_impl(qe_ctx *ctx, const int32_t *keys, const int32_t *paylo
             if (e != cudaSuccess) return qe_cuda_fail(ctx, e, "build: key range");
             kmin = host[0];
             kmax = host[1];
-            have_pay = 1;
+            have_pay = key_set ? 0 : 1;
             pay_min = host[2];
             pay_max = host[3];
         }
@@ -233,10 +285,11 @@ qe_status join_build_impl(qe_ctx *ctx, const int32_t *keys, const int32_t *paylo
     ht->pay_min = pay_min;
     ht->pay_max = pay_max;
     ht->nkeys = nrows;
+    ht->set = key_set ? 1 : 0;
     qe_status st;
     if (layout == QE_HT_DENSE) {
         ht->slots = static_cast<int64_t>(range);
-        const size_t pay_bytes = ((range * 4 + 255) / 256) * 256;
+        const size_t pay_bytes = key_set ? 0 : ((range * 4 + 255) / 256) * 256;
         const size_t bm_bytes = ((range + 31) / 32) * 4;
         ht->bytes = pay_bytes + bm_bytes;
         st = qe_alloc(ctx, &ht->mem, ht->bytes, s);
@@ -244,9 +297,10 @@ qe_status join_build_impl(qe_ctx *ctx, const int32_t *keys, const int32_t *paylo
             delete ht;
             return st;
         }
-        ht->payload = static_cast<int32_t *>(ht->mem);
+        ht->payload = key_set ? nullptr : static_cast<int32_t *>(ht->mem);
         ht->bitmap = reinterpret_cast<uint32_t *>(static_cast<char *>(ht->mem) + pay_bytes);
-        ht->full = static_cast<uint64_t>(nrows) == range ? 1 : 0;
+        // a key set may repeat keys, so its row count says nothing about occupancy
+        ht->full = !key_set && static_cast<uint64_t>(nrows) == range ? 1 : 0;
         cudaError_t e = cudaMemsetAsync(ht->bitmap, 0, bm_bytes, s);
         if (e == cudaSuccess && nrows > 0) {
             ProfScope prof(ctx, "build", s);
@@ -302,7 +356,38 @@ extern "C" qe_status qe_join_build(qe_ctx *ctx, const int32_t *keys, const int32
         !qe_aligned(keys, 4) || !qe_aligned(payload, 4))
         return qe_fail(ctx, QE_ERR_INVALID_ARG, "build: bad argument");
     cudaSetDevice(ctx->device);
-    return join_build_impl(ctx, keys, payload, nrows, opts, out, static_cast<cudaStream_t>(stream));
+    return join_build_impl(ctx, keys, payload, nrows, opts, false, out, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" qe_status qe_join_build_set(qe_ctx *ctx, const int32_t *keys, int64_t nrows, const qe_build_opts *opts,
+                                       qe_hash_table **out, void *stream)
+{
+    if (!ctx) return QE_ERR_INVALID_ARG;
+    if (!out || nrows < 0 || nrows >= (int64_t(1) << 31) || (nrows > 0 && !keys) || !qe_aligned(keys, 4))
+        return qe_fail(ctx, QE_ERR_INVALID_ARG, "build set: bad argument");
+    cudaSetDevice(ctx->device);
+    return join_build_impl(ctx, keys, nullptr, nrows, opts, true, out, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" qe_status qe_join_semi(qe_ctx *ctx, const qe_hash_table *ht, const int32_t *probe_keys,
+                                  const int32_t *sel, int64_t n, int anti, int32_t *out_rows, int64_t capacity,
+                                  int64_t *out_count, void *stream)
+{
+    if (!ctx) return QE_ERR_INVALID_ARG;
+    if (!ht || n < 0 || n >= (int64_t(1) << 31) || !out_count || capacity < 0 || (capacity > 0 && !out_rows) ||
+        (n > 0 && !probe_keys) || (anti != 0 && anti != 1))
+        return qe_fail(ctx, QE_ERR_INVALID_ARG, "semi-join: bad argument");
+    cudaSetDevice(ctx->device);
+    SemiOp op{};
+    op.ht = ht_view(ht);
+    op.keys = probe_keys;
+    op.sel = sel;
+    op.out_row = out_rows;
+    op.anti = anti;
+    const char *name = anti ? "anti_join" : "semi_join";
+    if (n >= PROBE_TWO_PASS_ROWS)
+        return launch_two_pass<PROBE_ITEMS>(ctx, name, n, capacity, out_count, op, static_cast<cudaStream_t>(stream));
+    return launch_compact<PROBE_ITEMS>(ctx, name, n, capacity, out_count, op, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" qe_status qe_join_probe(qe_ctx *ctx, const qe_hash_table *ht, const int32_t *probe_keys,
@@ -313,6 +398,7 @@ extern "C" qe_status qe_join_probe(qe_ctx *ctx, const qe_hash_table *ht, const i
     if (!ht || n < 0 || n >= (int64_t(1) << 31) || !out_count || capacity < 0 ||
         (capacity > 0 && (!out_probe_row || !out_build_payload)) || (n > 0 && !probe_keys))
         return qe_fail(ctx, QE_ERR_INVALID_ARG, "probe: bad argument");
+    if (ht->set) return qe_fail(ctx, QE_ERR_INVALID_ARG, "probe: a key set has no payloads (use qe_join_semi)");
     cudaSetDevice(ctx->device);
     ProbeOp op{};
     op.ht = ht_view(ht);
@@ -338,7 +424,7 @@ extern "C" qe_status qe_join_info(const qe_hash_table *ht, qe_ht_info *info)
     info->have_payload_range = ht->have_pay;
     info->payload_min = ht->pay_min;
     info->payload_max = ht->pay_max;
-    info->pad = 0;
+    info->key_set = ht->set;
     return QE_OK;
 }
 

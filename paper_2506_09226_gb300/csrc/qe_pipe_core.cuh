@@ -50,6 +50,7 @@ struct PipeSpec {
     int32_t p0_lo, p0_hi, p0_neg, s_h8;
     int32_t s_hmin, s_lmin;
     uint32_t s_hspan, s_lspan, s_ns;
+    int32_t join_kind;                  // qe_join_kind
 };
 
 // Where a block aggregates.
@@ -149,6 +150,18 @@ __device__ __forceinline__ bool probe(const HtView &h, int32_t key, int32_t &pay
         if (!h.full && !((ht_ld(h, h.bitmap + (s >> 5)) >> (s & 31)) & 1u)) return false;
         return true;
     }
+    return ht_lookup_open_ni(h, key, &pay);
+}
+
+// Membership of a key (semi- and anti-join): probe() without the payload,
+// open addressing out of line.
+__device__ __forceinline__ bool member(const HtView &h, int32_t key)
+{
+    if (h.layout == QE_HT_DENSE) {
+        const uint32_t s = static_cast<uint32_t>(key) - static_cast<uint32_t>(h.key_min);
+        return s < h.range && (h.full || ((ht_ld(h, h.bitmap + (s >> 5)) >> (s & 31)) & 1u));
+    }
+    int32_t pay;
     return ht_lookup_open_ni(h, key, &pay);
 }
 
@@ -267,9 +280,16 @@ __device__ __forceinline__ bool row_probe(const PipeSpec &P, const RowVals &v, i
     hi = v.hi;
     lo = v.key_a;
     if (P.has_join) {
-        int32_t pay = 0;
-        if (!probe(P.ht, static_cast<int32_t>(v.key_a), pay)) return false;
-        lo = P.lo_slot == QE_JOIN_PAYLOAD ? static_cast<int64_t>(pay) : v.lo;
+        const int32_t key = static_cast<int32_t>(v.key_a);
+        if (P.join_kind != QE_JOIN_INNER) {
+            // the semi-join keeps rows with a match, the anti-join rows without one
+            if (member(P.ht, key) == (P.join_kind == QE_JOIN_ANTI)) return false;
+            lo = v.lo;
+        } else {
+            int32_t pay = 0;
+            if (!probe(P.ht, key, pay)) return false;
+            lo = P.lo_slot == QE_JOIN_PAYLOAD ? static_cast<int64_t>(pay) : v.lo;
+        }
     }
     return true;
 }
@@ -438,7 +458,7 @@ static inline void star_predicate(PipeSpec &P)
 static inline bool star_shape(const PipeSpec &P, const TableCfg &T)
 {
     return (T.mode == TM_SMEM_DENSE || T.mode == TM_GLOBAL_DENSE) && P.npreds == 1 && P.type[P.pslot[0]] == QE_I32 &&
-           P.has_join && P.ht.layout == QE_HT_DENSE && P.lo_slot == QE_JOIN_PAYLOAD && P.hi_slot >= 0 &&
+           P.has_join && P.join_kind == QE_JOIN_INNER && P.ht.layout == QE_HT_DENSE && P.lo_slot == QE_JOIN_PAYLOAD && P.hi_slot >= 0 &&
            (P.type[P.hi_slot] == QE_I8 || P.type[P.hi_slot] == QE_I32) && P.ops.n == 4 && P.ops.op[0] == QE_SUM &&
            P.src[0] == SRC_XY && P.ops.op[1] == QE_COUNT && P.ops.op[2] == QE_MIN && P.src[2] == SRC_X &&
            P.ops.op[3] == QE_MAX && P.src[3] == SRC_X && P.type[P.x_slot] == QE_I64 && P.type[P.y_slot] == QE_I32 &&

@@ -148,6 +148,13 @@ qe_status pipeline_prepare(qe_ctx *ctx, const qe_pipeline_desc *d, PipeSpec &P)
     } else if (d->fk_col != -1) {
         return qe_fail(ctx, QE_ERR_INVALID_ARG, "pipeline: bad join column");
     }
+    if (d->join_kind < QE_JOIN_INNER || d->join_kind > QE_JOIN_ANTI)
+        return qe_fail(ctx, QE_ERR_INVALID_ARG, "pipeline: bad join kind");
+    if (d->join_kind != QE_JOIN_INNER && !P.has_join)
+        return qe_fail(ctx, QE_ERR_INVALID_ARG, "pipeline: a semi- or anti-join needs a join column");
+    if (d->join_kind != QE_JOIN_INNER && d->key_lo_col == QE_JOIN_PAYLOAD)
+        return qe_fail(ctx, QE_ERR_INVALID_ARG, "pipeline: a semi- or anti-join has no payload to group by");
+    P.join_kind = d->join_kind;
     P.hi_slot = -1;
     if (d->key_hi_col != -1) {
         if (!colok(d->key_hi_col)) return qe_fail(ctx, QE_ERR_INVALID_ARG, "pipeline: bad key_hi");
@@ -283,12 +290,16 @@ extern "C" qe_status qe_pipeline(qe_ctx *ctx, const qe_pipeline_desc *desc, cons
     qe_hash_table *built = nullptr;
     if (P.has_join) {
         const qe_hash_table *ht = desc->ht;
+        const bool inner = P.join_kind == QE_JOIN_INNER;
         if (!ht) {
-            if (desc->n_dim < 0 || (desc->n_dim > 0 && (!desc->dim_key || !desc->dim_payload)))
+            if (desc->n_dim < 0 || (desc->n_dim > 0 && (!desc->dim_key || (inner && !desc->dim_payload))))
                 return qe_fail(ctx, QE_ERR_INVALID_ARG, "pipeline: bad dimension columns");
-            st = join_build_impl(ctx, desc->dim_key, desc->dim_payload, desc->n_dim, &desc->build, &built, s);
+            // a semi- or anti-join builds a key set (repeated keys allowed)
+            st = join_build_impl(ctx, desc->dim_key, desc->dim_payload, desc->n_dim, &desc->build, !inner, &built, s);
             if (st != QE_OK) return st;
             ht = built;
+        } else if (inner && ht->set) {
+            return qe_fail(ctx, QE_ERR_INVALID_ARG, "pipeline: an inner join needs a table with payloads");
         }
         P.ht = ht_view(ht);
     }

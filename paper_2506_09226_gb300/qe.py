@@ -1,10 +1,11 @@
 """Python binding of libqe (include/qe.h): argument marshalling only.
 
 Every entry point of the C ABI is exposed under its own name (qe_create,
-qe_filter, qe_partition, qe_join_build, qe_join_probe, qe_groupby,
-qe_pipeline, qe_batch_*) and takes torch CUDA tensors, whose device pointers
-are passed straight to the library; torch provides device memory and streams
-only.  All operator work runs in the library's CUDA kernels.  Importing this
+qe_filter, qe_partition, qe_join_build, qe_join_build_set, qe_join_probe,
+qe_join_semi, qe_groupby, qe_pipeline, qe_batch_*) and takes torch CUDA
+tensors, whose device pointers are passed straight to the library; torch
+provides device memory and streams only.  The exchange planner (qe_plan_*)
+is host arithmetic and takes plain numbers and numpy arrays.  All operator work runs in the library's CUDA kernels.  Importing this
 module does not load the library; the first call does, and raises QeError
 when libqe.so has not been built or no sm_103a device is present (there is
 no CPU fallback).
@@ -35,6 +36,8 @@ PART_HASH, PART_RADIX = 0, 1
 HT_AUTO, HT_DENSE, HT_OPEN = 0, 1, 2
 GB_AUTO, GB_SMEM, GB_HBM = 0, 1, 2
 JOIN_PAYLOAD = -2
+# qe_join_kind
+INNER, SEMI, ANTI = 0, 1, 2
 MAX_COLS, MAX_PREDS, MAX_AGGS = 8, 4, 4
 
 _TYPE_OF = {torch.int8: I8, torch.int32: I32, torch.int64: I64}
@@ -68,7 +71,7 @@ class qe_ht_info(ctypes.Structure):
     _fields_ = [("layout", ctypes.c_int32), ("full", ctypes.c_int32), ("nkeys", ctypes.c_int64),
                 ("slots", ctypes.c_int64), ("bytes", ctypes.c_int64), ("key_min", ctypes.c_int32),
                 ("key_max", ctypes.c_int32), ("have_payload_range", ctypes.c_int32),
-                ("payload_min", ctypes.c_int32), ("payload_max", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("payload_min", ctypes.c_int32), ("payload_max", ctypes.c_int32), ("key_set", ctypes.c_int32)]
 
 
 class qe_agg(ctypes.Structure):
@@ -86,7 +89,7 @@ class qe_pipeline_desc(ctypes.Structure):
                 ("aggs", qe_agg_spec * MAX_AGGS), ("dim_key", ctypes.c_void_p), ("dim_payload", ctypes.c_void_p),
                 ("n_dim", ctypes.c_int64), ("ht", ctypes.c_void_p), ("build", qe_build_opts),
                 ("expected_groups", ctypes.c_int64), ("est_selectivity", ctypes.c_double),
-                ("have_key_range", ctypes.c_int32), ("pad2", ctypes.c_int32), ("key_hi_min", ctypes.c_int64),
+                ("have_key_range", ctypes.c_int32), ("join_kind", ctypes.c_int32), ("key_hi_min", ctypes.c_int64),
                 ("key_hi_max", ctypes.c_int64), ("key_lo_min", ctypes.c_int64), ("key_lo_max", ctypes.c_int64)]
 
 
@@ -141,6 +144,12 @@ _SIGS = {
     "qe_join_probe": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                      ctypes.c_void_p, ctypes.c_void_p]),
+    "qe_join_build_set": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                         ctypes.POINTER(qe_build_opts), ctypes.POINTER(ctypes.c_void_p),
+                                         ctypes.c_void_p]),
+    "qe_join_semi": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                    ctypes.c_void_p]),
     "qe_join_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(qe_ht_info)]),
     "qe_join_destroy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "qe_groupby": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, qe_col, qe_col,
@@ -377,6 +386,36 @@ def qe_join_probe(ctx: Context, ht: HashTable, probe_keys, sel=None, n=None, cap
     return out_rows, out_payload, out_count
 
 
+def qe_join_build_set(ctx: Context, keys, layout=HT_AUTO, key_range=None, stream=None, check=True):
+    """Key set for the semi- and anti-join (keys may repeat, no payloads)."""
+    h = ctypes.c_void_p()
+    o = build_opts(layout, key_range)
+    ctx.check(ctx.lib.qe_join_build_set(ctx.h, _ptr(keys), keys.numel(), ctypes.byref(o), ctypes.byref(h),
+                                        _stream(stream)))
+    if check:
+        ctx.sync_status(stream)
+    return HashTable(ctx, h)
+
+
+def qe_join_semi(ctx: Context, ht: HashTable, probe_keys, sel=None, n=None, anti=False, capacity=None,
+                 out_rows=None, out_count=None, stream=None, check=True):
+    """Rows (in probe order) whose key is (semi) or is not (anti) in the table."""
+    if n is None:
+        n = sel.numel() if sel is not None else probe_keys.numel()
+    dev = probe_keys.device
+    if capacity is None:
+        capacity = max(n, 1)
+    if out_rows is None:
+        out_rows = torch.empty(max(capacity, 1), dtype=torch.int32, device=dev)
+    if out_count is None:
+        out_count = torch.empty(1, dtype=torch.int64, device=dev)
+    ctx.check(ctx.lib.qe_join_semi(ctx.h, ht.h, _ptr(probe_keys), _ptr(sel), n, int(bool(anti)), _ptr(out_rows),
+                                   capacity, _ptr(out_count), _stream(stream)))
+    if check:
+        ctx.sync_status(stream)
+    return out_rows, out_count
+
+
 @dataclass
 class Groups:
     keys: torch.Tensor
@@ -423,8 +462,9 @@ def qe_groupby(ctx: Context, key_lo, aggs, key_hi=None, rows=None, n=None, capac
 
 def pipeline_desc(fact, preds, fk_col=-1, dim_key=None, dim_payload=None, ht: HashTable | None = None,
                   key_hi_col=-1, key_lo_col=JOIN_PAYLOAD, aggs=(), dim_key_range=None, layout=HT_AUTO,
-                  expected_groups=0, est_selectivity=0.0, key_range=None) -> qe_pipeline_desc:
-    """fact: list of tensors; preds: (col, op, lo[, hi]); aggs: (op, a, b) column indices."""
+                  expected_groups=0, est_selectivity=0.0, key_range=None, join_kind=INNER) -> qe_pipeline_desc:
+    """fact: list of tensors; preds: (col, op, lo[, hi]); aggs: (op, a, b) column indices;
+    join_kind: INNER, SEMI or ANTI (the latter two take no dim_payload)."""
     d = qe_pipeline_desc()
     d.n_fact = fact[0].numel() if fact else 0
     for i, t in enumerate(fact):
@@ -444,6 +484,7 @@ def pipeline_desc(fact, preds, fk_col=-1, dim_key=None, dim_payload=None, ht: Ha
     d.build = build_opts(layout, dim_key_range)
     d.expected_groups = expected_groups
     d.est_selectivity = est_selectivity
+    d.join_kind = join_kind
     if key_range is not None:
         # ((hi_min, hi_max), (lo_min, lo_max)) column statistics; lo None takes
         # the join payload's range from the join table

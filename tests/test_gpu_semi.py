@@ -1,0 +1,209 @@
+"""GPU parity of the semi- and anti-join against the CPU oracle (bit-exact).
+
+qe_join_semi over key sets (repeated keys) and over unique-key tables, both
+layouts, with and without a selection vector, one- and two-pass; pipelines
+whose join is a semi- or anti-join (built in the call, or against a
+prebuilt key set; dense and open layouts; grouped by fact columns); and the
+same pipelines inside a batch, each equal to its solo run and the oracle.
+Edge cases: empty sides, repeated keys, INT32_MIN, the output capacity, and
+the argument errors (a probe of a key set, a payload key of a semi-join).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2506_09226_gb300 import datagen
+from paper_2506_09226_gb300 import qe
+
+pytestmark = pytest.mark.gpu
+
+COLS = ("fk", "date", "price", "qty", "flag")
+AGGS = [(qe.SUM, 2, 3), (qe.COUNT, -1, -1), (qe.MIN, 2, -1), (qe.MAX, 2, -1)]
+O_AGGS = [(O.SUM, 2, 3), (O.COUNT, -1, -1), (O.MIN, 2, -1), (O.MAX, 2, -1)]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = qe.Context(0)
+    yield c
+    c.close()
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _check_semi(ctx, ht, pk, sel, bk, anti):
+    rows, cnt = qe.qe_join_semi(ctx, ht, cuda(pk), cuda(sel) if sel is not None else None, anti=anti)
+    ref = O.semi_join(bk, pk, sel, anti)
+    c = int(cnt.item())
+    assert c == len(ref)
+    assert np.array_equal(rows[:c].cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("layout", [qe.HT_DENSE, qe.HT_OPEN, qe.HT_AUTO])
+@pytest.mark.parametrize("with_sel", [False, True])
+def test_semi_anti_key_set(ctx, layout, with_sel):
+    rng = np.random.default_rng(layout * 2 + with_sel + 40)
+    nb, npr = 50_000, 200_001
+    bk = rng.integers(-40_000, 40_000, nb).astype(np.int32)            # repeats
+    pk = rng.integers(-60_000, 60_000, npr).astype(np.int32)
+    sel = np.sort(rng.choice(npr, 77_777, replace=False)).astype(np.int32) if with_sel else None
+    ht = qe.qe_join_build_set(ctx, cuda(bk), layout=layout)
+    info = ht.info()
+    assert info.key_set == 1 and info.full == 0
+    assert info.layout == (qe.HT_DENSE if layout == qe.HT_AUTO else layout)
+    if info.layout == qe.HT_DENSE:
+        assert info.bytes == (info.slots + 31) // 32 * 4               # the bitmap alone
+    for anti in (False, True):
+        _check_semi(ctx, ht, pk, sel, bk, anti)
+    ht.destroy()
+
+
+@pytest.mark.parametrize("layout", [qe.HT_DENSE, qe.HT_OPEN])
+def test_semi_anti_unique_table_and_two_pass(ctx, layout):
+    """A table from qe_join_build serves the semi-join too; 9M positions take
+    the two-pass compaction."""
+    rng = np.random.default_rng(50 + layout)
+    nb, npr = 300_000, 9_000_007
+    bk = rng.choice(np.arange(-500_000, 500_000), nb, replace=False).astype(np.int32)
+    pk = rng.integers(-600_000, 600_000, npr).astype(np.int32)
+    sel = np.sort(rng.choice(npr, 5_000_000, replace=False)).astype(np.int32)
+    ht = qe.qe_join_build(ctx, cuda(bk), cuda(np.zeros(nb, np.int32)), layout=layout)
+    for s in (None, sel):
+        for anti in (False, True):
+            _check_semi(ctx, ht, pk, s, bk, anti)
+    ht.destroy()
+
+
+def test_semi_edges_and_errors(ctx):
+    e32 = torch.empty(0, dtype=torch.int32, device="cuda")
+    # empty key set: the semi-join keeps nothing, the anti-join everything
+    ht = qe.qe_join_build_set(ctx, e32)
+    pk = np.array([3, -2 ** 31, 7], np.int32)
+    _check_semi(ctx, ht, pk, None, np.empty(0, np.int32), False)
+    _check_semi(ctx, ht, pk, None, np.empty(0, np.int32), True)
+    rows, cnt = qe.qe_join_semi(ctx, ht, e32)
+    assert int(cnt.item()) == 0
+    ht.destroy()
+    # INT32_MIN is an ordinary key of a dense set; the open layout reserves it
+    bk = np.array([-2 ** 31, -2 ** 31, -2 ** 31 + 2], np.int32)
+    ht = qe.qe_join_build_set(ctx, cuda(bk), layout=qe.HT_DENSE)
+    _check_semi(ctx, ht, np.array([-2 ** 31 + 2, 0, -2 ** 31, -2 ** 31 + 1], np.int32), None, bk, False)
+    # a key set has no payloads to probe
+    with pytest.raises(qe.QeError) as e:
+        qe.qe_join_probe(ctx, ht, cuda(pk))
+    assert e.value.status == qe.ERR_INVALID_ARG
+    ht.destroy()
+    with pytest.raises(qe.QeError) as e:
+        qe.qe_join_build_set(ctx, cuda(bk), layout=qe.HT_OPEN)
+    assert e.value.status == qe.ERR_RESERVED_KEY
+    # too small an output: nothing past the capacity, the required count reported
+    ht = qe.qe_join_build_set(ctx, cuda(np.arange(100, dtype=np.int32)))
+    out = torch.full((10,), -5, dtype=torch.int32, device="cuda")
+    with pytest.raises(qe.QeError) as e:
+        qe.qe_join_semi(ctx, ht, cuda(np.arange(50, dtype=np.int32)), capacity=4, out_rows=out)
+    assert e.value.status == qe.ERR_CAPACITY
+    assert out[4:].cpu().tolist() == [-5] * 6
+    ht.destroy()
+
+
+# ---------------------------------------------------------------- pipelines
+def _semi_case(seed, n_fact, n_dimkeys, key_span):
+    """Fact rows whose foreign keys fall partly outside a multiset of dim keys."""
+    rng = np.random.default_rng(seed)
+    fact = datagen.star_fact(n_fact, key_span, seed=seed)
+    dk = rng.integers(0, key_span, n_dimkeys).astype(np.int32)
+    return fact, dk
+
+
+def _run(ctx, fact, dk, kind, layout=qe.HT_AUTO, ht=None, key_lo=4, capacity=64):
+    f = [fact[c].cuda() for c in COLS]
+    d = qe.pipeline_desc(f, [(1, qe.LT, 1278)], fk_col=0, dim_key=cuda(dk) if ht is None else None, ht=ht,
+                         key_hi_col=-1, key_lo_col=key_lo, aggs=AGGS, layout=layout, join_kind=kind)
+    return qe.qe_pipeline(ctx, d, capacity), d
+
+
+def _oracle(fact, dk, kind, key_lo=4, dp=None):
+    q = O.Query(preds=[O.Pred(1, O.LT, 1278)], fk_col=0, key_hi_col=-1, key_lo_col=key_lo, aggs=O_AGGS,
+                join_kind=kind)
+    if kind == O.INNER and dp is None:
+        dp = np.zeros(len(dk), np.int32)
+    return O.pipeline([fact[c].numpy() for c in COLS], q, dk, dp)
+
+
+def _assert_groups(g, ref):
+    k, a = g.to_host()
+    o = np.argsort(k.numpy(), kind="stable")
+    assert np.array_equal(k.numpy()[o], ref["keys"])
+    for x, y in zip(a, ref["aggs"]):
+        assert np.array_equal(x.numpy()[o], y)
+
+
+@pytest.mark.parametrize("kind", [qe.SEMI, qe.ANTI])
+@pytest.mark.parametrize("layout", [qe.HT_DENSE, qe.HT_OPEN])
+def test_pipeline_semi_anti(ctx, kind, layout):
+    fact, dk = _semi_case(60 + kind + layout, 300_007, 40_000, 60_000)
+    g, _ = _run(ctx, fact, dk, kind, layout)
+    ref = _oracle(fact, dk, kind)
+    assert 0 < ref["njoin"] < ref["nsel"]
+    _assert_groups(g, ref)
+    # grouped by the int32 foreign key itself (many groups, HBM table)
+    g, _ = _run(ctx, fact, dk, kind, layout, key_lo=0, capacity=70_000)
+    _assert_groups(g, _oracle(fact, dk, kind, key_lo=0))
+
+
+@pytest.mark.parametrize("kind", [qe.SEMI, qe.ANTI])
+def test_pipeline_semi_anti_prebuilt_set(ctx, kind):
+    fact, dk = _semi_case(70 + kind, 100_000, 5_000, 20_000)
+    ht = qe.qe_join_build_set(ctx, cuda(dk))
+    g, _ = _run(ctx, fact, dk, kind, ht=ht)
+    _assert_groups(g, _oracle(fact, dk, kind))
+    # an inner join cannot use a key set
+    f = [fact[c].cuda() for c in COLS]
+    with pytest.raises(qe.QeError) as e:
+        qe.qe_pipeline(ctx, qe.pipeline_desc(f, [], fk_col=0, ht=ht, key_hi_col=-1, key_lo_col=4, aggs=AGGS), 64)
+    assert e.value.status == qe.ERR_INVALID_ARG
+    ht.destroy()
+    # a semi- or anti-join has no payload to group by
+    with pytest.raises(qe.QeError) as e:
+        _run(ctx, fact, dk, kind, key_lo=qe.JOIN_PAYLOAD)
+    assert e.value.status == qe.ERR_INVALID_ARG
+
+
+def test_batch_semi_anti_mixed(ctx):
+    """Inner, semi and anti pipelines in one batch (dimension built inside the
+    kernel from a key range, or a prebuilt key set), each equal to its solo
+    run and to the oracle."""
+    cases = []
+    for i, (kind, n) in enumerate([(qe.INNER, 70_001), (qe.SEMI, 123_457), (qe.ANTI, 5_000), (qe.SEMI, 1),
+                                   (qe.ANTI, 200_000), (qe.SEMI, 0)]):
+        fact, dk = _semi_case(80 + i, n, max(1, n // 4), max(2, n // 2))
+        if kind == qe.INNER:
+            dk = np.unique(dk)
+        cases.append((kind, fact, dk))
+    descs, groups, outs, keep, refs = [], [], [], [], []
+    for i, (kind, fact, dk) in enumerate(cases):
+        f = [fact[c].cuda() for c in COLS]
+        span = (0, int(fact["fk"].max().item()) if len(fact["fk"]) else 0)
+        span = (0, max(span[1], int(dk.max())))
+        ht = qe.qe_join_build_set(ctx, cuda(dk)) if (kind != qe.INNER and i % 2) else None
+        dkt = cuda(dk)
+        dpt = cuda(np.arange(len(dk), dtype=np.int32) % 7) if kind == qe.INNER else None
+        d = qe.pipeline_desc(f, [(1, qe.LT, 1278)], fk_col=0, dim_key=dkt, dim_payload=dpt, ht=ht, key_hi_col=-1,
+                             key_lo_col=4, aggs=AGGS, dim_key_range=span, join_kind=kind)
+        g, o = qe.alloc_groups(64, 4, torch.device("cuda"))
+        descs.append(d)
+        outs.append(o)
+        groups.append(g)
+        keep.append((f, dkt, dpt, ht))
+        refs.append(_oracle(fact, dk, kind))
+    qe.qe_batch_run(ctx, descs, outs, opts=qe.qe_batch_opts(0, 1 << 15, 0, 0))
+    for d, g, r in zip(descs, groups, refs):
+        _assert_groups(g, r)
+        solo = qe.qe_pipeline(ctx, d, 64)
+        _assert_groups(solo, r)
+    for k in keep:
+        if k[3] is not None:
+            k[3].destroy()
