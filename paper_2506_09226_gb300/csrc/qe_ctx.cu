@@ -112,11 +112,7 @@ extern "C" qe_status qe_set_tuning(qe_ctx *ctx, const char *name, int64_t value)
         ctx->tune_force_generic = value != 0;
     } else if (n == "part_general") {
         ctx->tune_part_general = value != 0;
-    } else if (n == "part_interleave") {
-        ctx->tune_part_interleave = value != 0;
-    } else if (n == "part_one_pass_log2f") {
-        if (value < 0 || value > 10) return qe_fail(ctx, QE_ERR_INVALID_ARG, "part_one_pass_log2f must be in [0, 10]");
-        ctx->tune_part_one_pass_log2f = static_cast<int>(value);
+
     } else {
         return qe_fail(ctx, QE_ERR_INVALID_ARG, "unknown tuning knob " + n);
     }

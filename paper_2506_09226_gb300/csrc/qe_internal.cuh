@@ -43,8 +43,6 @@ struct qe_ctx {
     int tune_star_items = 0;        // 0: default
     int tune_force_generic = 0;
     int tune_part_general = 0;      // partition: skip the write-combining scatter
-    int tune_part_interleave = 0;   // partition: one pass over interleaved short ranges
-    int tune_part_one_pass_log2f = 9;   // partition: largest fan-out (log2) scattered in one pass
     bool profiling = false;
     std::mutex prof_mu;
     std::map<std::string, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>> prof;
