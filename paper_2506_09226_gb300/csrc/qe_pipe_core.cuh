@@ -331,11 +331,68 @@ __device__ __forceinline__ void table_flush(const PipeSpec &P, const TableCfg &T
 // stride, ... below r1; all columns of the next tile are loaded into
 // registers while the current tile is processed, so the register file holds
 // the loads in flight.
+// The row work of one star tile: predicate, dense lookup, direct-array
+// (or spilled hash) update of the ITEMS rows a thread holds; bit k of cin
+// marks row k as inside the range.
+template <bool GLOBAL, int ITEMS>
+__device__ __forceinline__ void star_rows(const PipeSpec &P, unsigned long long *sm, const int (&cd)[ITEMS],
+                                          const int (&cf)[ITEMS], const int (&ch)[ITEMS], const int (&cq)[ITEMS],
+                                          const long long (&cx)[ITEMS], unsigned cin)
+{
+    bool ok[ITEMS];
+    int32_t pay[ITEMS];
+#pragma unroll
+    for (int k = 0; k < ITEMS; k++) {
+        const uint32_t ks = static_cast<uint32_t>(cf[k]) - static_cast<uint32_t>(P.ht.key_min);
+        const bool pass = (cd[k] >= P.p0_lo && cd[k] <= P.p0_hi) != static_cast<bool>(P.p0_neg);
+        const bool hit = ((cin >> k) & 1u) && pass && ks < P.ht.range;
+        pay[k] = hit ? ht_ld(P.ht, P.ht.payload + ks) : 0;
+        ok[k] = hit && (P.ht.full || ((ht_ld(P.ht, P.ht.bitmap + (ks >> 5)) >> (ks & 31)) & 1u));
+    }
+#pragma unroll
+    for (int k = 0; k < ITEMS; k++) {
+        if (!ok[k]) continue;
+        const uint32_t hh = static_cast<uint32_t>(ch[k]) - static_cast<uint32_t>(P.s_hmin);
+        const uint32_t ll = static_cast<uint32_t>(pay[k]) - static_cast<uint32_t>(P.s_lmin);
+        const unsigned long long v = static_cast<unsigned long long>(cx[k]) * static_cast<unsigned long long>(cq[k]);
+        const unsigned long long emin = ~(static_cast<unsigned long long>(cx[k]) ^ GB_SIGN);
+        const unsigned long long emax = static_cast<unsigned long long>(cx[k]) ^ GB_SIGN;
+        if (hh < P.s_hspan && ll < P.s_lspan) {
+            const uint32_t idx = hh * P.s_lspan + ll;
+            if (GLOBAL) {
+                unsigned long long *cell = P.gdense + static_cast<uint64_t>(idx) * 4;
+                atomicAdd(cell, v);
+                atomicAdd(cell + 1, 1ull);
+                if (cell[2] < emin) atomicMax(cell + 2, emin);
+                if (cell[3] < emax) atomicMax(cell + 3, emax);
+            } else {
+                atomicAdd(sm + idx, v);
+                atomicAdd(sm + P.s_ns + idx, 1ull);
+                if (sm[2 * P.s_ns + idx] < emin) atomicMax(sm + 2 * P.s_ns + idx, emin);
+                if (sm[3 * P.s_ns + idx] < emax) atomicMax(sm + 3 * P.s_ns + idx, emax);
+            }
+        } else {
+            const int64_t key = static_cast<int64_t>((static_cast<uint64_t>(static_cast<int64_t>(ch[k])) << 32) |
+                                                     static_cast<uint32_t>(pay[k]));
+            const unsigned long long kx = static_cast<unsigned long long>(key) ^ GB_SIGN;
+            if (kx == 0) {
+                dev_report(P.g.st, QE_ERR_RESERVED_KEY, 0);
+            } else {
+                const unsigned long long e[QE_MAX_AGGS] = {v, 1ull, emin, emax};
+                gt_fold_row(P.g, P.ops, kx, e);
+            }
+        }
+    }
+}
+
+// Star row loop: one block processes the tiles of THREADS x ITEMS rows
+// starting at r0, r0 + stride, ... below r1; all columns of the next tile are
+// loaded into registers while the current one is processed, so the register
+// file holds the loads in flight.
 template <bool GLOBAL, int ITEMS, int THREADS>
 __device__ __forceinline__ void star_range(const PipeSpec &P, unsigned long long *sm, int64_t r0, int64_t r1,
                                            int64_t stride)
 {
-    constexpr int TR = THREADS * ITEMS;
     int d[ITEMS], f[ITEMS], h[ITEMS], q[ITEMS];
     long long x[ITEMS];
     unsigned inmask = 0;
@@ -370,50 +427,7 @@ __device__ __forceinline__ void star_range(const PipeSpec &P, unsigned long long
             cx[k] = x[k];
         }
         load(t0 + stride);   // next tile's loads overlap this tile's work
-        bool ok[ITEMS];
-        int32_t pay[ITEMS];
-#pragma unroll
-        for (int k = 0; k < ITEMS; k++) {
-            const uint32_t ks = static_cast<uint32_t>(cf[k]) - static_cast<uint32_t>(P.ht.key_min);
-            const bool pass = (cd[k] >= P.p0_lo && cd[k] <= P.p0_hi) != static_cast<bool>(P.p0_neg);
-            const bool hit = ((cin >> k) & 1u) && pass && ks < P.ht.range;
-            pay[k] = hit ? ht_ld(P.ht, P.ht.payload + ks) : 0;
-            ok[k] = hit && (P.ht.full || ((ht_ld(P.ht, P.ht.bitmap + (ks >> 5)) >> (ks & 31)) & 1u));
-        }
-#pragma unroll
-        for (int k = 0; k < ITEMS; k++) {
-            if (!ok[k]) continue;
-            const uint32_t hh = static_cast<uint32_t>(ch[k]) - static_cast<uint32_t>(P.s_hmin);
-            const uint32_t ll = static_cast<uint32_t>(pay[k]) - static_cast<uint32_t>(P.s_lmin);
-            const unsigned long long v = static_cast<unsigned long long>(cx[k]) * static_cast<unsigned long long>(cq[k]);
-            const unsigned long long emin = ~(static_cast<unsigned long long>(cx[k]) ^ GB_SIGN);
-            const unsigned long long emax = static_cast<unsigned long long>(cx[k]) ^ GB_SIGN;
-            if (hh < P.s_hspan && ll < P.s_lspan) {
-                const uint32_t idx = hh * P.s_lspan + ll;
-                if (GLOBAL) {
-                    unsigned long long *cell = P.gdense + static_cast<uint64_t>(idx) * 4;
-                    atomicAdd(cell, v);
-                    atomicAdd(cell + 1, 1ull);
-                    if (cell[2] < emin) atomicMax(cell + 2, emin);
-                    if (cell[3] < emax) atomicMax(cell + 3, emax);
-                } else {
-                    atomicAdd(sm + idx, v);
-                    atomicAdd(sm + P.s_ns + idx, 1ull);
-                    if (sm[2 * P.s_ns + idx] < emin) atomicMax(sm + 2 * P.s_ns + idx, emin);
-                    if (sm[3 * P.s_ns + idx] < emax) atomicMax(sm + 3 * P.s_ns + idx, emax);
-                }
-            } else {
-                const int64_t key = static_cast<int64_t>((static_cast<uint64_t>(static_cast<int64_t>(ch[k])) << 32) |
-                                                         static_cast<uint32_t>(pay[k]));
-                const unsigned long long kx = static_cast<unsigned long long>(key) ^ GB_SIGN;
-                if (kx == 0) {
-                    dev_report(P.g.st, QE_ERR_RESERVED_KEY, 0);
-                } else {
-                    const unsigned long long e[QE_MAX_AGGS] = {v, 1ull, emin, emax};
-                    gt_fold_row(P.g, P.ops, kx, e);
-                }
-            }
-        }
+        star_rows<GLOBAL, ITEMS>(P, sm, cd, cf, ch, cq, cx, cin);
     }
 }
 
