@@ -142,14 +142,14 @@ constexpr int64_t STAR_TR = static_cast<int64_t>(BT) * 3;
 __device__ __noinline__ void item_star_smem(const PipeSpec &P, unsigned long long *sm, int64_t j, int64_t m, int64_t n)
 {
     for (int64_t t = j * STAR_TR; t < n; t += m * STAR_TR)
-        star_range<false, 3, BT>(P, sm, t, t + STAR_TR < n ? t + STAR_TR : n, STAR_TR);
+        star_range<false, 3, BT, true>(P, sm, t, t + STAR_TR < n ? t + STAR_TR : n, STAR_TR);
 }
 
 __device__ __noinline__ void item_star_global(const PipeSpec &P, unsigned long long *sm, int64_t j, int64_t m,
                                               int64_t n)
 {
     for (int64_t t = j * STAR_TR; t < n; t += m * STAR_TR)
-        star_range<true, 3, BT>(P, sm, t, t + STAR_TR < n ? t + STAR_TR : n, STAR_TR);
+        star_range<true, 3, BT, false>(P, sm, t, t + STAR_TR < n ? t + STAR_TR : n, STAR_TR);
 }
 
 __device__ __noinline__ void item_generic(const PipeSpec &P, const TableCfg T, unsigned long long *sm, int64_t j,
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(BT, 1) k_batch(BatchArgs A)
             else if (B.star) item_star_global(P, sm, I.row0, B.nprobe, I.row1);
             else item_generic(P, T, sm, I.row0, B.nprobe, I.row1);
             __syncthreads();
-            table_flush(P, T, sm);
+            table_flush(P, T, sm, B.star ? 2 : 0);   // star items: 32-bit COUNT and SUM halves
         }
         __syncthreads();
         if (threadIdx.x == 0) {

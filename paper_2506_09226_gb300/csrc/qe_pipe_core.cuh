@@ -204,13 +204,26 @@ __device__ __forceinline__ unsigned long long agg_value_enc(const PipeSpec &P, i
     return agg_encode(P.ops.op[a], val);
 }
 
-// Update of one shared-memory aggregate cell: ADD kinds are reductions with
-// no return value; MAX kinds read the cell first (a stale read can only
-// cause a redundant atomic, never a lost update, since cells only grow).
+// 64-bit add into a shared-memory cell as 32-bit atomics: the low half,
+// then the high half plus the carry out of the low half (read from the value
+// the first atomic replaced).  32-bit shared atomics cost far less than
+// 64-bit ones; the cell is read whole only after a barrier.
+__device__ __forceinline__ void smem_add64(unsigned long long *cell, unsigned long long e)
+{
+    unsigned *w = reinterpret_cast<unsigned *>(cell);   // little-endian: w[0] low, w[1] high
+    const uint32_t lo = static_cast<uint32_t>(e), hi = static_cast<uint32_t>(e >> 32);
+    const uint32_t old = atomicAdd(w, lo);
+    const uint32_t up = hi + (old + lo < old ? 1u : 0u);
+    if (up) atomicAdd(w + 1, up);
+}
+
+// Update of one shared-memory aggregate cell: ADD kinds add (in 32-bit
+// halves); MAX kinds read the cell first (a stale read can only cause a
+// redundant atomic, never a lost update, since cells only grow).
 __device__ __forceinline__ void st_update(unsigned long long *cell, int op, unsigned long long e)
 {
     if (op == QE_SUM || op == QE_COUNT) {
-        atomicAdd(cell, e);
+        smem_add64(cell, e);
     } else if (*cell < e) {
         atomicMax(cell, e);
     }
@@ -248,7 +261,7 @@ __device__ __forceinline__ void fold_row(const PipeSpec &P, const TableCfg &T, u
 #pragma unroll
                 for (int a = 0; a < QE_MAX_AGGS; a++)
                     if (a < P.ops.n) st_update(sm + a * ns + idx, P.ops.op[a], e[a]);
-                if (P.dk.hidden) atomicAdd(sm + P.ops.n * ns + idx, 1ull);
+                if (P.dk.hidden) smem_add64(sm + P.ops.n * ns + idx, 1ull);
             } else {
                 unsigned long long *cell = P.gdense + idx * P.dk.stride;
 #pragma unroll
@@ -302,21 +315,39 @@ __device__ __forceinline__ void table_zero(const PipeSpec &P, const TableCfg &T,
         for (uint64_t i = threadIdx.x; i < P.dk.nslots * P.dk.stride; i += blockDim.x) sm[i] = 0;
 }
 
-// Merge the block table into the HBM tables (after a __syncthreads()).
-__device__ __forceinline__ void table_flush(const PipeSpec &P, const TableCfg &T, unsigned long long *sm)
+// Merge the block table into the HBM tables (after a __syncthreads()).  In
+// a direct array word w of slot i is sm[w * nslots + i].  The star kernels
+// keep the COUNT word (word 1) as 32-bit counters (narrow >= 1) and, for
+// small arrays, the SUM word (word 0) as two 32-bit halves, low halves then
+// high halves (narrow == 2), each at the start of the word's region:
+// 32-bit shared-memory atomics cost much less than 64-bit ones.
+__device__ __forceinline__ unsigned long long dense_word(const unsigned long long *sm, uint64_t ns, int w, uint64_t i,
+                                                        int narrow)
+{
+    if (narrow == 2 && w == 0) {
+        const unsigned *h = reinterpret_cast<const unsigned *>(sm);
+        return static_cast<unsigned long long>(h[i]) | (static_cast<unsigned long long>(h[ns + i]) << 32);
+    }
+    if (narrow && w == 1) return reinterpret_cast<const unsigned *>(sm + ns)[i];
+    return sm[w * ns + i];
+}
+
+__device__ __forceinline__ void table_flush(const PipeSpec &P, const TableCfg &T, unsigned long long *sm,
+                                            int narrow = 0)
 {
     if (T.mode == TM_SMEM_HASH) st_flush(sm, T.S, P.ops, P.g);
     if (T.mode != TM_SMEM_DENSE) return;
     const uint64_t ns = P.dk.nslots;
     for (uint64_t i = threadIdx.x; i < ns; i += blockDim.x) {
-        if (sm[P.dk.occ * ns + i] == 0) continue;
+        if (dense_word(sm, ns, P.dk.occ, i, narrow) == 0) continue;
         if (P.gdense) {
             unsigned long long *cell = P.gdense + i * P.dk.stride;
-            for (int w = 0; w < P.dk.stride; w++) gd_update(cell + w, w < P.ops.n ? P.ops.op[w] : QE_COUNT, sm[w * ns + i]);
+            for (int w = 0; w < P.dk.stride; w++)
+                gd_update(cell + w, w < P.ops.n ? P.ops.op[w] : QE_COUNT, dense_word(sm, ns, w, i, narrow));
         } else {
             unsigned long long e[QE_MAX_AGGS];
 #pragma unroll
-            for (int a = 0; a < QE_MAX_AGGS; a++) e[a] = a < P.ops.n ? sm[a * ns + i] : 0;
+            for (int a = 0; a < QE_MAX_AGGS; a++) e[a] = a < P.ops.n ? dense_word(sm, ns, a, i, narrow) : 0;
             const unsigned long long kx = static_cast<unsigned long long>(dense_key(P.dk, i)) ^ GB_SIGN;
             gt_fold_row(P.g, P.ops, kx, e);
         }
@@ -331,10 +362,13 @@ __device__ __forceinline__ void table_flush(const PipeSpec &P, const TableCfg &T
 // stride, ... below r1; all columns of the next tile are loaded into
 // registers while the current tile is processed, so the register file holds
 // the loads in flight.
+// Largest direct array (slots) whose SUM the star kernels keep in 32-bit halves.
+constexpr uint64_t STAR_NSUM_SLOTS = 1024;
+
 // The row work of one star tile: predicate, dense lookup, direct-array
 // (or spilled hash) update of the ITEMS rows a thread holds; bit k of cin
 // marks row k as inside the range.
-template <bool GLOBAL, int ITEMS>
+template <bool GLOBAL, int ITEMS, bool NSUM>
 __device__ __forceinline__ void star_rows(const PipeSpec &P, unsigned long long *sm, const int (&cd)[ITEMS],
                                           const int (&cf)[ITEMS], const int (&ch)[ITEMS], const int (&cq)[ITEMS],
                                           const long long (&cx)[ITEMS], unsigned cin)
@@ -366,8 +400,19 @@ __device__ __forceinline__ void star_rows(const PipeSpec &P, unsigned long long 
                 if (cell[2] < emin) atomicMax(cell + 2, emin);
                 if (cell[3] < emax) atomicMax(cell + 3, emax);
             } else {
-                atomicAdd(sm + idx, v);
-                atomicAdd(sm + P.s_ns + idx, 1ull);
+                if (NSUM) {
+                    // SUM as 32-bit halves: the low half's carry, read from
+                    // the value the atomic replaced, goes into the high half
+                    unsigned *slo = reinterpret_cast<unsigned *>(sm);
+                    const uint32_t lo = static_cast<uint32_t>(v), hi = static_cast<uint32_t>(v >> 32);
+                    const uint32_t old = atomicAdd(slo + idx, lo);
+                    const uint32_t up = hi + (old + lo < old ? 1u : 0u);
+                    if (up) atomicAdd(slo + P.s_ns + idx, up);
+                } else {
+                    atomicAdd(sm + idx, v);
+                }
+                // COUNT as 32 bits: a block's table counts its share of the rows, far below 2^32
+                atomicAdd(reinterpret_cast<unsigned *>(sm + P.s_ns) + idx, 1u);
                 if (sm[2 * P.s_ns + idx] < emin) atomicMax(sm + 2 * P.s_ns + idx, emin);
                 if (sm[3 * P.s_ns + idx] < emax) atomicMax(sm + 3 * P.s_ns + idx, emax);
             }
@@ -389,7 +434,7 @@ __device__ __forceinline__ void star_rows(const PipeSpec &P, unsigned long long 
 // starting at r0, r0 + stride, ... below r1; all columns of the next tile are
 // loaded into registers while the current one is processed, so the register
 // file holds the loads in flight.
-template <bool GLOBAL, int ITEMS, int THREADS>
+template <bool GLOBAL, int ITEMS, int THREADS, bool NSUM>
 __device__ __forceinline__ void star_range(const PipeSpec &P, unsigned long long *sm, int64_t r0, int64_t r1,
                                            int64_t stride)
 {
@@ -427,7 +472,7 @@ __device__ __forceinline__ void star_range(const PipeSpec &P, unsigned long long
             cx[k] = x[k];
         }
         load(t0 + stride);   // next tile's loads overlap this tile's work
-        star_rows<GLOBAL, ITEMS>(P, sm, cd, cf, ch, cq, cx, cin);
+        star_rows<GLOBAL, ITEMS, NSUM>(P, sm, cd, cf, ch, cq, cx, cin);
     }
 }
 

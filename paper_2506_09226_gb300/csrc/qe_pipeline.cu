@@ -69,7 +69,9 @@ __global__ void __launch_bounds__(PT, 1) k_pipeline(PipeSpec P, TableCfg T)
 
 // Star shape (see the file comment).  GLOBAL: the direct array lives in HBM (AoS, 4 words per slot)
 // instead of shared memory (SoA).
-template <bool GLOBAL, int ITEMS>
+// NSUM: the shared-memory direct array keeps SUM as 32-bit halves (small
+// arrays, where many rows hit each slot and 64-bit atomics collide most).
+template <bool GLOBAL, int ITEMS, bool NSUM>
 __global__ void __launch_bounds__(PT, 1) k_pipeline_star(PipeSpec P, TableCfg T)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -78,9 +80,9 @@ __global__ void __launch_bounds__(PT, 1) k_pipeline_star(PipeSpec P, TableCfg T)
     __syncthreads();
     // grid-stride tiles: at any moment the blocks read neighbouring tiles
     constexpr int64_t TR = static_cast<int64_t>(PT) * ITEMS;
-    star_range<GLOBAL, ITEMS, PT>(P, sm, static_cast<int64_t>(blockIdx.x) * TR, P.n, TR * gridDim.x);
+    star_range<GLOBAL, ITEMS, PT, NSUM>(P, sm, static_cast<int64_t>(blockIdx.x) * TR, P.n, TR * gridDim.x);
     __syncthreads();
-    if (!GLOBAL) table_flush(P, T, sm);
+    if (!GLOBAL) table_flush(P, T, sm, NSUM ? 2 : 1);
 }
 
 template <class K>
@@ -269,10 +271,15 @@ qe_status pipeline_launch(qe_ctx *ctx, PipeSpec &P, const PipePlan &plan, const 
         // rows per thread: 3 by default, 2 when tuned so
         const bool two = ctx->tune_star_items == 2;
         if (plan.T.mode == TM_GLOBAL_DENSE)
-            return two ? launch(ctx, k_pipeline_star<true, 2>, P, plan.T, 0, PT * 2, s)
-                       : launch(ctx, k_pipeline_star<true, 3>, P, plan.T, 0, PT * 3, s);
-        return two ? launch(ctx, k_pipeline_star<false, 2>, P, plan.T, plan.table, PT * 2, s)
-                   : launch(ctx, k_pipeline_star<false, 3>, P, plan.T, plan.table, PT * 3, s);
+            return two ? launch(ctx, k_pipeline_star<true, 2, false>, P, plan.T, 0, PT * 2, s)
+                       : launch(ctx, k_pipeline_star<true, 3, false>, P, plan.T, 0, PT * 3, s);
+        // SUM in 32-bit halves up to STAR_NSUM_SLOTS slots: measured 2.89 against 4.38 ms for a
+        // batch of 300 pipelines of 75 groups, and 2.94 against 2.86 ms for 600M rows into 3,000
+        if (P.dk.nslots <= STAR_NSUM_SLOTS)
+            return two ? launch(ctx, k_pipeline_star<false, 2, true>, P, plan.T, plan.table, PT * 2, s)
+                       : launch(ctx, k_pipeline_star<false, 3, true>, P, plan.T, plan.table, PT * 3, s);
+        return two ? launch(ctx, k_pipeline_star<false, 2, false>, P, plan.T, plan.table, PT * 2, s)
+                   : launch(ctx, k_pipeline_star<false, 3, false>, P, plan.T, plan.table, PT * 3, s);
     }
     return launch(ctx, k_pipeline<2>, P, plan.T, plan.table, PT * 2, s);
 }

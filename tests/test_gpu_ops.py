@@ -454,6 +454,30 @@ def test_pipeline_dense_smem_each_shape(ctx, generic, items):
         ctx.set_tuning("star_items", 0)
 
 
+@pytest.mark.parametrize("n_attr", [25, 1000])
+def test_pipeline_star_wide_values(ctx, n_attr):
+    """SUM(price * qty) whose products need all 64 bits (negative and large
+    prices), into 75 groups (the star kernels keep SUM as 32-bit halves with
+    carries) and 3,000 groups (64-bit SUM), in the single pipeline and in a
+    batch (32-bit halves for both)."""
+    rng = np.random.default_rng(21)
+    dim = datagen.star_dim(20_000, n_attr, seed=21)
+    fact = dict(datagen.star_fact(700_001, 20_000, seed=21))
+    fact["price"] = torch.from_numpy(rng.integers(-2 ** 40, 2 ** 40, 700_001, dtype=np.int64))
+    fact["price"][::7] = 2 ** 62 + 12345                  # products wrap modulo 2^64
+    ref = oracle_star(fact, dim)
+    kr = ((0, 2), (0, n_attr - 1))
+    g = run_star_hint(ctx, fact, dim, kr, 3100)
+    assert_groups_equal(g, ref)
+    f = [fact[c].cuda() for c in COLS]
+    d = qe.pipeline_desc(f, [(1, qe.LT, 1278)], fk_col=0, dim_key=dim["key"].cuda(), dim_payload=dim["attr"].cuda(),
+                         key_hi_col=4, key_lo_col=qe.JOIN_PAYLOAD, aggs=STAR_AGGS, dim_key_range=(0, 19_999),
+                         key_range=kr, expected_groups=3 * n_attr)
+    gb, o = qe.alloc_groups(3100, 4, torch.device("cuda"))
+    qe.qe_batch_run(ctx, [d], [o], opts=qe.qe_batch_opts(0, 1 << 16, 0, 0))
+    assert_groups_equal(gb, ref)
+
+
 @pytest.mark.parametrize("generic", [False, True])
 def test_pipeline_dense_hint_too_narrow_spills(ctx, generic):
     ctx.set_tuning("force_generic", int(generic))
