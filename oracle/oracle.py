@@ -71,6 +71,8 @@ def lib():
         L.oracle_groupby.argtypes = [i64, vp, ci, vp, vp, vp, vp]
         L.oracle_group_key.restype = i64
         L.oracle_group_key.argtypes = [ci, i64, i64]
+        L.oracle_join_multi.restype = i64
+        L.oracle_join_multi.argtypes = [i64, vp, vp, i64, vp, vp, vp, vp, i64]
         L.oracle_semi_join.restype = i64
         L.oracle_semi_join.argtypes = [i64, vp, i64, vp, vp, ci, vp]
         L.oracle_pipeline.restype = i64
@@ -158,6 +160,20 @@ def join(build_keys, build_payload, probe_keys, sel=None):
     if st == DUPLICATE_KEY:
         raise ValueError("duplicate build key")
     return rows[:cnt.value].copy(), pay[:cnt.value].copy()
+
+
+def join_multi(build_keys, build_payload, probe_keys, sel=None):
+    """Many-to-many inner equi-join: (probe_rows, payloads), probe positions in
+    order and, within one, the build rows in ascending order."""
+    bk, bp = _c(build_keys, np.int32), _c(build_payload, np.int32)
+    pk = _c(probe_keys, np.int32)
+    s = None if sel is None else _c(sel, np.int32)
+    n = len(pk) if s is None else len(s)
+    total = lib().oracle_join_multi(len(bk), _p(bk), _p(bp), n, _p(pk), _p(s), None, None, 0)
+    rows = np.empty(max(total, 1), np.int32)
+    pay = np.empty(max(total, 1), np.int32)
+    lib().oracle_join_multi(len(bk), _p(bk), _p(bp), n, _p(pk), _p(s), _p(rows), _p(pay), total)
+    return rows[:total].copy(), pay[:total].copy()
 
 
 def semi_join(build_keys, probe_keys, sel=None, anti=False):

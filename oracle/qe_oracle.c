@@ -19,7 +19,8 @@
  *                 column);
  *   - join:       inner equi-join of a probe column against unique build
  *                 keys (Sec. 2.2, the local join after exchange), and the
- *                 semi- and anti-join (membership in the build keys);
+ *                 semi- and anti-join (membership in the build keys), and
+ *                 the many-to-many join (build keys may repeat);
  *   - group-by:   SUM / COUNT / MIN / MAX per distinct key (Sec. 2.3, the
  *                 aggregation kinds of the final reduction; Sec. 2.4, group
  *                 by in the compiled tensor program);
@@ -199,6 +200,50 @@ int oracle_join(int64_t nb, const int32_t *bkeys, const int32_t *bpay,
     free(b);
     *out_count = count;
     return OR_OK;
+}
+
+/*
+ * Many-to-many inner equi-join (the local join of Sec. 2.2 when build keys
+ * repeat).  For each probe position i in order (the row sel[i], or i when sel
+ * is NULL), every build row j with key_j == probe_key gives one output
+ * (probe row, payload_j), in ascending j.  Plain nested loop over a sorted
+ * copy: the build rows sorted by (key, j), then a binary search for the
+ * first row of the probe key.  When the output would exceed `capacity`,
+ * nothing past it is written; returns the full number of matches.
+ */
+static int cmp_build_row_stable(const void *a, const void *b)
+{
+    const build_row *x = (const build_row *)a, *y = (const build_row *)b;
+    if (x->key != y->key) return (x->key > y->key) - (x->key < y->key);
+    return (x->payload > y->payload) - (x->payload < y->payload);   /* payload holds j here */
+}
+
+int64_t oracle_join_multi(int64_t nb, const int32_t *bkeys, const int32_t *bpay,
+                          int64_t np, const int32_t *pkeys, const int32_t *sel,
+                          int32_t *out_row, int32_t *out_pay, int64_t capacity)
+{
+    build_row *b = (build_row *)malloc((size_t)(nb > 0 ? nb : 1) * sizeof(build_row));
+    for (int64_t j = 0; j < nb; j++) { b[j].key = bkeys[j]; b[j].payload = (int32_t)j; }
+    qsort(b, (size_t)nb, sizeof(build_row), cmp_build_row_stable);
+    int64_t count = 0;
+    for (int64_t i = 0; i < np; i++) {
+        int32_t row = sel ? sel[i] : (int32_t)i;
+        int32_t k = pkeys[row];
+        int64_t lo = 0, hi = nb;           /* first index with key >= k */
+        while (lo < hi) {
+            int64_t mid = lo + (hi - lo) / 2;
+            if (b[mid].key < k) lo = mid + 1; else hi = mid;
+        }
+        for (int64_t t = lo; t < nb && b[t].key == k; t++) {
+            if (count < capacity) {
+                out_row[count] = row;
+                out_pay[count] = bpay[b[t].payload];
+            }
+            count++;
+        }
+    }
+    free(b);
+    return count;
 }
 
 static int cmp_i32(const void *a, const void *b)

@@ -34,6 +34,10 @@ MUTANTS = {
                   "for (int p = 0; p + 1 < npreds; p++) {\n            int c = pred_col[p];\n            if (!pred_holds"),
     "payload_index": ("out_pay[count] = b[lo].payload;",
                       "out_pay[count] = b[lo > 0 ? lo - 1 : 0].payload;"),
+    "multi_unstable": ("    return (x->payload > y->payload) - (x->payload < y->payload);   /* payload holds j here */",
+                       "    return (x->payload < y->payload) - (x->payload > y->payload);   /* payload holds j here */"),
+    "multi_last_row": ("for (int64_t t = lo; t < nb && b[t].key == k; t++) {",
+                       "for (int64_t t = lo; t + 1 < nb && b[t].key == k; t++) {"),
     "semi_flip": ("if (found != (anti != 0)) out_row[count++] = row;",
                   "if (found == (anti != 0)) out_row[count++] = row;"),
     "semi_last_key": ("int found = lo < nb && b[lo] == k;", "int found = lo + 1 < nb && b[lo] == k;"),

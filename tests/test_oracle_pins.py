@@ -251,6 +251,48 @@ def test_join_fk_invariant():
     assert np.array_equal(pay, direct[fk[sel]])
 
 
+# ---------------------------------------------------------------- many-to-many join
+def bf_join_multi(bkeys, bpay, pkeys, sel):
+    """Nested loop: every (position, build row) pair with equal keys, build
+    rows in ascending order within a position."""
+    rows = range(len(pkeys)) if sel is None else [int(r) for r in sel]
+    return [(int(r), int(bpay[j])) for r in rows for j in range(len(bkeys)) if int(bkeys[j]) == int(pkeys[r])]
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_join_multi_matches_nested_loop(seed):
+    rng = np.random.default_rng(200 + seed)
+    nb = int(rng.integers(0, 200))
+    bkeys = rng.integers(-40, 40, nb).astype(np.int32)            # many repeats
+    bpay = rng.integers(-2 ** 31, 2 ** 31 - 1, nb).astype(np.int32)
+    pkeys = rng.integers(-50, 50, 300).astype(np.int32)
+    sel = np.sort(rng.choice(300, 100, replace=False)).astype(np.int32)
+    for s in (None, sel):
+        rows, pay = O.join_multi(bkeys, bpay, pkeys, s)
+        assert list(zip(rows.tolist(), pay.tolist())) == bf_join_multi(bkeys, bpay, pkeys, s)
+
+
+def test_join_multi_invariants():
+    rng = np.random.default_rng(31)
+    bkeys = rng.integers(0, 60, 500).astype(np.int32)
+    bpay = np.arange(500, dtype=np.int32)
+    pkeys = rng.integers(0, 80, 1000).astype(np.int32)
+    rows, pay = O.join_multi(bkeys, bpay, pkeys)
+    # one output per (position, equal build key); the kept positions are the semi-join's
+    per_key = np.bincount(bkeys, minlength=80)
+    assert len(rows) == int(per_key[pkeys].sum())
+    assert np.array_equal(np.unique(rows), O.semi_join(bkeys, pkeys))
+    assert np.all(bkeys[pay] == pkeys[rows])                      # payloads are build row ids here
+    # unique build keys: the inner join
+    ub, first = np.unique(bkeys, return_index=True)
+    r1, p1 = O.join_multi(ub, bpay[first], pkeys)
+    r2, p2 = O.join(ub, bpay[first], pkeys)
+    assert np.array_equal(r1, r2) and np.array_equal(p1, p2)
+    # empty sides
+    assert len(O.join_multi(np.empty(0, np.int32), np.empty(0, np.int32), pkeys)[0]) == 0
+    assert len(O.join_multi(bkeys, bpay, np.empty(0, np.int32))[0]) == 0
+
+
 # ---------------------------------------------------------------- semi- and anti-join
 def bf_semi(bkeys, pkeys, sel, anti):
     """Nested loop: position i keeps its row when any build key equals its key
