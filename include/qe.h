@@ -260,7 +260,8 @@ typedef struct {
     int32_t key_min, key_max;
     int32_t have_payload_range;   /* payload range known (read back with the key range) */
     int32_t payload_min, payload_max;
-    int32_t key_set;      /* built by qe_join_build_set: membership only */
+    int32_t key_set;      /* 1: built by qe_join_build_set (membership only);
+                             2: built by qe_join_build_multi (a multimap) */
 } qe_ht_info;
 
 /* Hash-join build (Sec. 2.2: the local join once both inputs are
@@ -310,6 +311,35 @@ qe_status qe_join_build_set(qe_ctx *ctx, const int32_t *keys, int64_t nrows, con
 qe_status qe_join_semi(qe_ctx *ctx, const qe_hash_table *ht, const int32_t *probe_keys, const int32_t *sel,
                        int64_t n, int anti, int32_t *out_rows, int64_t capacity, int64_t *out_count,
                        void *stream);
+
+/* Many-to-many build (Sec. 2.2's local join when build keys repeat): a
+ * multimap from key to the run of its build rows' payloads.  Every key
+ * counts its rows (a dense slot key - key_min, or an open-addressing slot
+ * holding the key and its count), a scan of the counts gives each key the
+ * start of its run in one payload array, and a second pass places the rows;
+ * the order of payloads inside a run is unspecified.  Layout and opts as for
+ * qe_join_build (AUTO: dense when the key range is at most 4x the row count).
+ * Memory: dense 12 bytes per key-range slot, open 20 bytes per slot (slots =
+ * the power of two >= 2 x rows), plus 4 bytes per row.  The open layout
+ * reserves INT32_MIN (QE_ERR_RESERVED_KEY).  A multimap serves only
+ * qe_join_probe_multi (the other probes and the pipelines return
+ * QE_ERR_INVALID_ARG for it). */
+qe_status qe_join_build_multi(qe_ctx *ctx, const int32_t *keys, const int32_t *payload, int64_t nrows,
+                              const qe_build_opts *opts, qe_hash_table **out, void *stream);
+
+/* Many-to-many probe.  For each probe position i < n in order, row r = sel ?
+ * sel[i] : i is looked up with key probe_keys[r]; each of the key's build
+ * rows gives one output (r, payload).  Positions come out in ascending
+ * order; the outputs of one position are in unspecified order.
+ *   out_probe_row, out_build_payload: device int32 [capacity];
+ *   *out_count (device int64): the number of outputs; past the capacity
+ *   nothing is written and QE_ERR_CAPACITY is recorded with that number.
+ * Two passes (count every position's matches per segment of 256 positions,
+ * scan, look up again and write), with scratch of 16 bytes per segment. */
+qe_status qe_join_probe_multi(qe_ctx *ctx, const qe_hash_table *ht, const int32_t *probe_keys,
+                              const int32_t *sel, int64_t n, int32_t *out_probe_row,
+                              int32_t *out_build_payload, int64_t capacity, int64_t *out_count,
+                              void *stream);
 
 qe_status qe_join_info(const qe_hash_table *ht, qe_ht_info *info);
 

@@ -618,9 +618,16 @@ struct qe_hash_table {
     uint32_t *bitmap = nullptr;
     unsigned long long *open = nullptr;
     int32_t set = 0;                  // key set: membership only, keys may repeat
+    int32_t multi = 0;                // multimap (qe_join_build_multi): payload = the runs of values
+    int64_t *mstart = nullptr;        // multimap: start of each key's run (per dense slot / open slot)
+    uint32_t *mcnt = nullptr;         // multimap: rows of each key
 };
 
 HtView ht_view(const qe_hash_table *ht);
+// Min and max of nrows build keys (and of the payloads when pay is not
+// NULL) into mm = {kmin, kmax, pmin, pmax}; synchronizes the stream.
+qe_status join_key_range(qe_ctx *ctx, const int32_t *keys, const int32_t *pay, int64_t nrows, int32_t mm[4],
+                         cudaStream_t s);
 // key_set: membership only (repeated keys allowed, payload ignored and not stored).
 qe_status join_build_impl(qe_ctx *ctx, const int32_t *keys, const int32_t *payload, int64_t nrows,
                           const qe_build_opts *opts, bool key_set, qe_hash_table **out, cudaStream_t s);

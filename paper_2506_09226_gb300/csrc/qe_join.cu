@@ -235,6 +235,24 @@ struct SemiOp {
 
 }  // namespace
 
+qe_status join_key_range(qe_ctx *ctx, const int32_t *keys, const int32_t *pay, int64_t nrows, int32_t host[4],
+                         cudaStream_t s)
+{
+    void *mm = nullptr;
+    qe_status st = qe_alloc(ctx, &mm, 16, s);
+    if (st != QE_OK) return st;
+    k_minmax_init<<<1, 1, 0, s>>>(static_cast<int32_t *>(mm));
+    QE_LAUNCHED(ctx);
+    k_minmax<<<grid_for(ctx, nrows), 256, 0, s>>>(keys, pay, nrows, static_cast<int32_t *>(mm));
+    QE_LAUNCHED(ctx);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host, mm, 16, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    qe_free(ctx, mm, s);
+    if (e != cudaSuccess) return qe_cuda_fail(ctx, e, "build: key range");
+    return QE_OK;
+}
+
 qe_status join_build_impl(qe_ctx *ctx, const int32_t *keys, const int32_t *payload, int64_t nrows,
                           const qe_build_opts *opts, bool key_set, qe_hash_table **out, cudaStream_t s)
 {
@@ -250,19 +268,9 @@ qe_status join_build_impl(qe_ctx *ctx, const int32_t *keys, const int32_t *paylo
             kmax = o.key_max;
             if (kmin > kmax) return qe_fail(ctx, QE_ERR_INVALID_ARG, "build: empty key range");
         } else {
-            void *mm = nullptr;
-            qe_status st = qe_alloc(ctx, &mm, 16, s);
-            if (st != QE_OK) return st;
             int32_t host[4];
-            k_minmax_init<<<1, 1, 0, s>>>(static_cast<int32_t *>(mm));
-            QE_LAUNCHED(ctx);
-            k_minmax<<<grid_for(ctx, nrows), 256, 0, s>>>(keys, payload, nrows, static_cast<int32_t *>(mm));
-            QE_LAUNCHED(ctx);
-            cudaError_t e = cudaGetLastError();
-            if (e == cudaSuccess) e = cudaMemcpyAsync(host, mm, 16, cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-            qe_free(ctx, mm, s);
-            if (e != cudaSuccess) return qe_cuda_fail(ctx, e, "build: key range");
+            const qe_status st = join_key_range(ctx, keys, payload, nrows, host, s);
+            if (st != QE_OK) return st;
             kmin = host[0];
             kmax = host[1];
             have_pay = key_set ? 0 : 1;
@@ -377,6 +385,7 @@ extern "C" qe_status qe_join_semi(qe_ctx *ctx, const qe_hash_table *ht, const in
     if (!ht || n < 0 || n >= (int64_t(1) << 31) || !out_count || capacity < 0 || (capacity > 0 && !out_rows) ||
         (n > 0 && !probe_keys) || (anti != 0 && anti != 1))
         return qe_fail(ctx, QE_ERR_INVALID_ARG, "semi-join: bad argument");
+    if (ht->multi) return qe_fail(ctx, QE_ERR_INVALID_ARG, "semi-join: takes a key set or a unique-key table");
     cudaSetDevice(ctx->device);
     SemiOp op{};
     op.ht = ht_view(ht);
@@ -399,6 +408,7 @@ extern "C" qe_status qe_join_probe(qe_ctx *ctx, const qe_hash_table *ht, const i
         (capacity > 0 && (!out_probe_row || !out_build_payload)) || (n > 0 && !probe_keys))
         return qe_fail(ctx, QE_ERR_INVALID_ARG, "probe: bad argument");
     if (ht->set) return qe_fail(ctx, QE_ERR_INVALID_ARG, "probe: a key set has no payloads (use qe_join_semi)");
+    if (ht->multi) return qe_fail(ctx, QE_ERR_INVALID_ARG, "probe: a multimap needs qe_join_probe_multi");
     cudaSetDevice(ctx->device);
     ProbeOp op{};
     op.ht = ht_view(ht);
@@ -424,7 +434,7 @@ extern "C" qe_status qe_join_info(const qe_hash_table *ht, qe_ht_info *info)
     info->have_payload_range = ht->have_pay;
     info->payload_min = ht->pay_min;
     info->payload_max = ht->pay_max;
-    info->key_set = ht->set;
+    info->key_set = ht->multi ? 2 : ht->set;
     return QE_OK;
 }
 

@@ -1,14 +1,15 @@
 """Python binding of libqe (include/qe.h): argument marshalling only.
 
 Every entry point of the C ABI is exposed under its own name (qe_create,
-qe_filter, qe_partition, qe_join_build, qe_join_build_set, qe_join_probe,
-qe_join_semi, qe_groupby, qe_pipeline, qe_batch_*) and takes torch CUDA
-tensors, whose device pointers are passed straight to the library; torch
-provides device memory and streams only.  The exchange planner (qe_plan_*)
-is host arithmetic and takes plain numbers and numpy arrays.  All operator work runs in the library's CUDA kernels.  Importing this
-module does not load the library; the first call does, and raises QeError
-when libqe.so has not been built or no sm_103a device is present (there is
-no CPU fallback).
+qe_filter, qe_partition, qe_join_build, qe_join_build_set,
+qe_join_build_multi, qe_join_probe, qe_join_semi, qe_join_probe_multi,
+qe_groupby, qe_pipeline, qe_batch_*) and takes torch CUDA tensors, whose
+device pointers are passed straight to the library; torch provides device
+memory and streams only.  The exchange planner (qe_plan_*) is host
+arithmetic and takes plain numbers and numpy arrays.  All operator work runs
+in the library's CUDA kernels.  Importing this module does not load the
+library; the first call does, and raises QeError when libqe.so has not been
+built or no sm_103a device is present (there is no CPU fallback).
 """
 from __future__ import annotations
 
@@ -150,6 +151,12 @@ _SIGS = {
     "qe_join_semi": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                     ctypes.c_void_p]),
+    "qe_join_build_multi": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                           ctypes.POINTER(qe_build_opts), ctypes.POINTER(ctypes.c_void_p),
+                                           ctypes.c_void_p]),
+    "qe_join_probe_multi": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                           ctypes.c_void_p, ctypes.c_void_p]),
     "qe_join_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(qe_ht_info)]),
     "qe_join_destroy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "qe_groupby": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, qe_col, qe_col,
@@ -381,6 +388,38 @@ def qe_join_probe(ctx: Context, ht: HashTable, probe_keys, sel=None, n=None, cap
         out_count = torch.empty(1, dtype=torch.int64, device=dev)
     ctx.check(ctx.lib.qe_join_probe(ctx.h, ht.h, _ptr(probe_keys), _ptr(sel), n, _ptr(out_rows),
                                     _ptr(out_payload), capacity, _ptr(out_count), _stream(stream)))
+    if check:
+        ctx.sync_status(stream)
+    return out_rows, out_payload, out_count
+
+
+def qe_join_build_multi(ctx: Context, keys, payload, layout=HT_AUTO, key_range=None, stream=None, check=True):
+    """Multimap for the many-to-many join (keys may repeat)."""
+    h = ctypes.c_void_p()
+    o = build_opts(layout, key_range)
+    ctx.check(ctx.lib.qe_join_build_multi(ctx.h, _ptr(keys), _ptr(payload), keys.numel(), ctypes.byref(o),
+                                          ctypes.byref(h), _stream(stream)))
+    if check:
+        ctx.sync_status(stream)
+    return HashTable(ctx, h)
+
+
+def qe_join_probe_multi(ctx: Context, ht: HashTable, probe_keys, sel=None, n=None, capacity=None, out_rows=None,
+                        out_payload=None, out_count=None, stream=None, check=True):
+    """Every (probe row, build payload) pair with equal keys, positions in order."""
+    if n is None:
+        n = sel.numel() if sel is not None else probe_keys.numel()
+    dev = probe_keys.device
+    if capacity is None:
+        capacity = max(n, 1)
+    if out_rows is None:
+        out_rows = torch.empty(max(capacity, 1), dtype=torch.int32, device=dev)
+    if out_payload is None:
+        out_payload = torch.empty(max(capacity, 1), dtype=torch.int32, device=dev)
+    if out_count is None:
+        out_count = torch.empty(1, dtype=torch.int64, device=dev)
+    ctx.check(ctx.lib.qe_join_probe_multi(ctx.h, ht.h, _ptr(probe_keys), _ptr(sel), n, _ptr(out_rows),
+                                          _ptr(out_payload), capacity, _ptr(out_count), _stream(stream)))
     if check:
         ctx.sync_status(stream)
     return out_rows, out_payload, out_count
