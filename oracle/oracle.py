@@ -71,6 +71,8 @@ def lib():
         L.oracle_groupby.argtypes = [i64, vp, ci, vp, vp, vp, vp]
         L.oracle_group_key.restype = i64
         L.oracle_group_key.argtypes = [ci, i64, i64]
+        L.oracle_join_pair.restype = ci
+        L.oracle_join_pair.argtypes = [i64, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp]
         L.oracle_join_multi.restype = i64
         L.oracle_join_multi.argtypes = [i64, vp, vp, i64, vp, vp, vp, vp, i64]
         L.oracle_semi_join.restype = i64
@@ -159,6 +161,23 @@ def join(build_keys, build_payload, probe_keys, sel=None):
                            ctypes.byref(cnt))
     if st == DUPLICATE_KEY:
         raise ValueError("duplicate build key")
+    return rows[:cnt.value].copy(), pay[:cnt.value].copy()
+
+
+def join_pair(build_hi, build_lo, build_payload, probe_hi, probe_lo, sel=None):
+    """Inner equi-join on a pair of key columns; returns (probe_rows,
+    payloads) in probe order.  Raises ValueError on a duplicate build pair."""
+    bh, bl, bp = _c(build_hi, np.int32), _c(build_lo, np.int32), _c(build_payload, np.int32)
+    ph, pl = _c(probe_hi, np.int32), _c(probe_lo, np.int32)
+    s = None if sel is None else _c(sel, np.int32)
+    n = len(ph) if s is None else len(s)
+    rows = np.empty(max(n, 1), np.int32)
+    pay = np.empty(max(n, 1), np.int32)
+    cnt = ctypes.c_int64(0)
+    st = lib().oracle_join_pair(len(bh), _p(bh), _p(bl), _p(bp), n, _p(ph), _p(pl), _p(s), _p(rows), _p(pay),
+                                ctypes.byref(cnt))
+    if st == DUPLICATE_KEY:
+        raise ValueError("duplicate build key pair")
     return rows[:cnt.value].copy(), pay[:cnt.value].copy()
 
 

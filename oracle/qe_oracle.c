@@ -20,7 +20,8 @@
  *   - join:       inner equi-join of a probe column against unique build
  *                 keys (Sec. 2.2, the local join after exchange), and the
  *                 semi- and anti-join (membership in the build keys), and
- *                 the many-to-many join (build keys may repeat);
+ *                 the many-to-many join (build keys may repeat), and the join
+ *                 on a pair of key columns;
  *   - group-by:   SUM / COUNT / MIN / MAX per distinct key (Sec. 2.3, the
  *                 aggregation kinds of the final reduction; Sec. 2.4, group
  *                 by in the compiled tensor program);
@@ -244,6 +245,54 @@ int64_t oracle_join_multi(int64_t nb, const int32_t *bkeys, const int32_t *bpay,
     }
     free(b);
     return count;
+}
+
+/*
+ * Inner equi-join on a pair of key columns: the composite keys of joins
+ * such as a (part, supplier) pair in the TPC-H queries the paper runs
+ * (Sec. 6.1), joined locally as in Sec. 2.2.  Build row j matches probe row
+ * r when bhi[j] == phi[r] and blo[j] == plo[r].  Build pairs must be unique
+ * (OR_DUPLICATE_KEY, nothing emitted).  Output as oracle_join: for each
+ * probe position in order, (probe row, payload) on a match.  The lookup is
+ * a binary search of the build rows sorted by (hi, lo).
+ */
+typedef struct { int32_t hi, lo, payload; } pair_row;
+
+static int cmp_pair_row(const void *a, const void *b)
+{
+    const pair_row *x = (const pair_row *)a, *y = (const pair_row *)b;
+    if (x->hi != y->hi) return (x->hi > y->hi) - (x->hi < y->hi);
+    return (x->lo > y->lo) - (x->lo < y->lo);
+}
+
+int oracle_join_pair(int64_t nb, const int32_t *bhi, const int32_t *blo, const int32_t *bpay,
+                     int64_t np, const int32_t *phi, const int32_t *plo, const int32_t *sel,
+                     int32_t *out_row, int32_t *out_pay, int64_t *out_count)
+{
+    pair_row *b = (pair_row *)malloc((size_t)(nb > 0 ? nb : 1) * sizeof(pair_row));
+    for (int64_t j = 0; j < nb; j++) { b[j].hi = bhi[j]; b[j].lo = blo[j]; b[j].payload = bpay[j]; }
+    qsort(b, (size_t)nb, sizeof(pair_row), cmp_pair_row);
+    for (int64_t j = 1; j < nb; j++)
+        if (b[j].hi == b[j - 1].hi && b[j].lo == b[j - 1].lo) { free(b); *out_count = 0; return OR_DUPLICATE_KEY; }
+    int64_t count = 0;
+    for (int64_t i = 0; i < np; i++) {
+        int32_t row = sel ? sel[i] : (int32_t)i;
+        pair_row key = { phi[row], plo[row], 0 };
+        int64_t lo = 0, hi = nb;           /* first index with (hi, lo) >= key */
+        while (lo < hi) {
+            int64_t mid = lo + (hi - lo) / 2;
+            if (cmp_pair_row(&b[mid], &key) < 0) lo = mid + 1; else hi = mid;
+        }
+        if (lo < nb && cmp_pair_row(&b[lo], &key) == 0) {
+            const pair_row *hit = &b[lo];
+            out_row[count] = row;
+            out_pay[count] = hit->payload;
+            count++;
+        }
+    }
+    free(b);
+    *out_count = count;
+    return OR_OK;
 }
 
 static int cmp_i32(const void *a, const void *b)

@@ -34,6 +34,7 @@ MUTANTS = {
                   "for (int p = 0; p + 1 < npreds; p++) {\n            int c = pred_col[p];\n            if (!pred_holds"),
     "payload_index": ("out_pay[count] = b[lo].payload;",
                       "out_pay[count] = b[lo > 0 ? lo - 1 : 0].payload;"),
+    "pair_drop_lo": ("    return (x->lo > y->lo) - (x->lo < y->lo);\n}", "    return 0;\n}"),
     "multi_unstable": ("    return (x->payload > y->payload) - (x->payload < y->payload);   /* payload holds j here */",
                        "    return (x->payload < y->payload) - (x->payload > y->payload);   /* payload holds j here */"),
     "multi_last_row": ("for (int64_t t = lo; t < nb && b[t].key == k; t++) {",

@@ -251,6 +251,54 @@ def test_join_fk_invariant():
     assert np.array_equal(pay, direct[fk[sel]])
 
 
+# ---------------------------------------------------------------- join on a pair of key columns
+def bf_join_pair(bhi, blo, bpay, phi, plo, sel):
+    rows = range(len(phi)) if sel is None else [int(r) for r in sel]
+    out = []
+    for r in rows:
+        m = [int(bpay[j]) for j in range(len(bhi)) if int(bhi[j]) == int(phi[r]) and int(blo[j]) == int(plo[r])]
+        assert len(m) <= 1
+        out += [(int(r), m[0])] if m else []
+    return out
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_join_pair_matches_nested_loop(seed):
+    rng = np.random.default_rng(400 + seed)
+    pairs = rng.choice(40 * 40, int(rng.integers(1, 300)), replace=False)
+    bhi, blo = (pairs // 40 - 20).astype(np.int32), (pairs % 40 - 20).astype(np.int32)
+    bpay = rng.integers(-2 ** 31, 2 ** 31 - 1, len(pairs)).astype(np.int32)
+    phi, plo = rng.integers(-22, 22, 500).astype(np.int32), rng.integers(-22, 22, 500).astype(np.int32)
+    sel = np.sort(rng.choice(500, 200, replace=False)).astype(np.int32)
+    for s in (None, sel):
+        rows, pay = O.join_pair(bhi, blo, bpay, phi, plo, s)
+        assert list(zip(rows.tolist(), pay.tolist())) == bf_join_pair(bhi, blo, bpay, phi, plo, s)
+
+
+def test_join_pair_invariants():
+    rng = np.random.default_rng(41)
+    bk = rng.choice(np.arange(-500, 500), 300, replace=False).astype(np.int32)
+    bp = rng.integers(0, 1000, 300).astype(np.int32)
+    pk = rng.integers(-600, 600, 2000).astype(np.int32)
+    # one key column constant: the single-column join
+    z = np.zeros_like(bk)
+    r1, p1 = O.join_pair(z, bk, bp, np.zeros_like(pk), pk)
+    r2, p2 = O.join(bk, bp, pk)
+    assert np.array_equal(r1, r2) and np.array_equal(p1, p2)
+    # the halves are not interchangeable: (a, b) does not match (b, a)
+    rows, _ = O.join_pair(np.array([1], np.int32), np.array([2], np.int32), np.array([9], np.int32),
+                          np.array([2, 1], np.int32), np.array([1, 2], np.int32))
+    assert rows.tolist() == [1]
+    # extreme values are ordinary keys; a repeated pair is an error, a repeated half is not
+    m = -2 ** 31
+    rows, pay = O.join_pair(np.array([m, m], np.int32), np.array([m, 7], np.int32), np.array([1, 2], np.int32),
+                            np.array([m, m, 0], np.int32), np.array([7, m, m], np.int32))
+    assert rows.tolist() == [0, 1] and pay.tolist() == [2, 1]
+    with pytest.raises(ValueError):
+        O.join_pair(np.array([3, 3], np.int32), np.array([4, 4], np.int32), np.array([1, 2], np.int32),
+                    np.array([3], np.int32), np.array([4], np.int32))
+
+
 # ---------------------------------------------------------------- many-to-many join
 def bf_join_multi(bkeys, bpay, pkeys, sel):
     """Nested loop: every (position, build row) pair with equal keys, build
