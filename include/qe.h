@@ -261,7 +261,8 @@ typedef struct {
     int32_t have_payload_range;   /* payload range known (read back with the key range) */
     int32_t payload_min, payload_max;
     int32_t key_set;      /* 1: built by qe_join_build_set (membership only);
-                             2: built by qe_join_build_multi (a multimap) */
+                             2: built by qe_join_build_multi (a multimap);
+                             3: built by qe_join_build_pair (pair keys) */
 } qe_ht_info;
 
 /* Hash-join build (Sec. 2.2: the local join once both inputs are
@@ -340,6 +341,22 @@ qe_status qe_join_probe_multi(qe_ctx *ctx, const qe_hash_table *ht, const int32_
                               const int32_t *sel, int64_t n, int32_t *out_probe_row,
                               int32_t *out_build_payload, int64_t capacity, int64_t *out_count,
                               void *stream);
+
+/* Join on a pair of int32 key columns: the composite keys of joins such as a
+ * (part, supplier) pair in the TPC-H queries the paper runs (Sec. 6.1),
+ * joined locally as in Sec. 2.2.  The pair is packed as (uint32)hi << 32 |
+ * (uint32)lo into an open-addressing table (load factor <= 0.5, 12 bytes
+ * per slot); (INT32_MIN, INT32_MIN) is the empty-slot marker and records
+ * QE_ERR_RESERVED_KEY.  Build pairs must be unique (QE_ERR_DUPLICATE_KEY).
+ * The probe matches row r = sel ? sel[i] : i on (probe_hi[r], probe_lo[r])
+ * and writes (r, payload) in ascending position order, as qe_join_probe
+ * (two passes from 4M positions on).  Pair-key tables serve only
+ * qe_join_probe_pair. */
+qe_status qe_join_build_pair(qe_ctx *ctx, const int32_t *key_hi, const int32_t *key_lo, const int32_t *payload,
+                             int64_t nrows, qe_hash_table **out, void *stream);
+qe_status qe_join_probe_pair(qe_ctx *ctx, const qe_hash_table *ht, const int32_t *probe_hi,
+                             const int32_t *probe_lo, const int32_t *sel, int64_t n, int32_t *out_probe_row,
+                             int32_t *out_build_payload, int64_t capacity, int64_t *out_count, void *stream);
 
 qe_status qe_join_info(const qe_hash_table *ht, qe_ht_info *info);
 

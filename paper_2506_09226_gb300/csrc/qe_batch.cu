@@ -308,9 +308,9 @@ extern "C" qe_status qe_batch_create(qe_ctx *ctx, const qe_pipeline_desc *descs,
         if (B.P.has_join) {
             const bool inner = B.P.join_kind == QE_JOIN_INNER;
             if (d.ht) {
-                if (d.ht->multi)
+                if (d.ht->multi || d.ht->pair)
                     return qe_fail(ctx, QE_ERR_INVALID_ARG,
-                                   "batch: pipeline " + std::to_string(i) + ": a multimap is not a pipeline table");
+                                   "batch: pipeline " + std::to_string(i) + ": a multimap or pair-key table is not a pipeline table");
                 if (inner && d.ht->set)
                     return qe_fail(ctx, QE_ERR_INVALID_ARG,
                                    "batch: pipeline " + std::to_string(i) + ": an inner join needs a table with payloads");

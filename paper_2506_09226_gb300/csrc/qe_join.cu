@@ -233,6 +233,114 @@ struct SemiOp {
     }
 };
 
+// ---------------------------------------------------------------- pair keys
+// A pair of int32 key columns packed as (uint32)hi << 32 | (uint32)lo; the
+// packed (INT32_MIN, INT32_MIN) is the empty slot (HT_EMPTY_SLOT).  Open
+// addressing over packed keys, with the payload in a parallel array.
+__device__ __forceinline__ unsigned long long pair_key(int32_t hi, int32_t lo)
+{
+    return (static_cast<unsigned long long>(static_cast<uint32_t>(hi)) << 32) | static_cast<uint32_t>(lo);
+}
+
+__global__ void __launch_bounds__(256) k_build_pair(const int32_t *khi, const int32_t *klo, const int32_t *pay,
+                                                    int64_t n, unsigned long long *keys, int32_t *vals, uint32_t mask,
+                                                    qe_dev_status *st)
+{
+    for (int64_t i = blockIdx.x * 256ll + threadIdx.x; i < n; i += static_cast<int64_t>(gridDim.x) * 256) {
+        const unsigned long long k = pair_key(__ldcs(khi + i), __ldcs(klo + i));
+        if (k == HT_EMPTY_SLOT) {
+            dev_report(st, QE_ERR_RESERVED_KEY, 0);
+            continue;
+        }
+        uint32_t h = static_cast<uint32_t>(dev_fmix64(k)) & mask;
+        bool done = false;
+        for (uint32_t probes = 0; probes <= mask && !done; probes++) {
+            const unsigned long long old = atomicCAS(keys + h, HT_EMPTY_SLOT, k);
+            if (old == HT_EMPTY_SLOT) {
+                vals[h] = __ldcs(pay + i);
+                done = true;
+            } else if (old == k) {
+                dev_report(st, QE_ERR_DUPLICATE_KEY, 0);
+                done = true;
+            } else {
+                h = (h + 1) & mask;
+            }
+        }
+        if (!done) dev_report(st, QE_ERR_CAPACITY, n);
+    }
+}
+
+struct PairView {
+    const unsigned long long *keys;
+    const int32_t *vals;
+    uint32_t mask;
+};
+
+__device__ __forceinline__ bool pair_lookup(const PairView &v, unsigned long long k, int32_t &pay)
+{
+    uint32_t h = static_cast<uint32_t>(dev_fmix64(k)) & v.mask;
+    for (uint32_t probes = 0; probes <= v.mask; probes++) {
+        const unsigned long long w = __ldg(v.keys + h);
+        if (w == k) {
+            pay = __ldg(v.vals + h);
+            return true;
+        }
+        if (w == HT_EMPTY_SLOT) return false;
+        h = (h + 1) & v.mask;
+    }
+    return false;
+}
+
+// Pair-key probe as a stable compaction: position i probes row sel[i] (or i).
+struct PairProbeOp {
+    PairView ht;
+    const int32_t *khi, *klo;
+    const int32_t *sel;
+    int32_t *out_row;
+    int32_t *out_pay;
+
+    struct Slot {
+        int32_t row[PROBE_ITEMS];
+        int32_t pay[PROBE_ITEMS];
+    };
+    struct Pre {
+        int32_t row[PROBE_ITEMS];
+    };
+
+    template <int ITEMS>
+    __device__ __forceinline__ void load(int64_t pos0, const bool (&in)[ITEMS], Pre &p) const
+    {
+#pragma unroll
+        for (int k = 0; k < ITEMS; k++) {
+            int64_t i = pos0 + 32 * k;
+            p.row[k] = in[k] ? (sel ? __ldcs(sel + i) : static_cast<int32_t>(i)) : 0;
+        }
+    }
+
+    template <int ITEMS>
+    __device__ __forceinline__ void eval(int64_t, bool (&ok)[ITEMS], const Pre &pre, Slot &s) const
+    {
+        unsigned long long key[ITEMS];
+#pragma unroll
+        for (int k = 0; k < ITEMS; k++) {
+            s.row[k] = pre.row[k];
+            key[k] = ok[k] ? pair_key(__ldg(khi + s.row[k]), __ldg(klo + s.row[k])) : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < ITEMS; k++) {
+            int32_t p = 0;
+            if (ok[k]) ok[k] = key[k] != HT_EMPTY_SLOT && pair_lookup(ht, key[k], p);
+            s.pay[k] = p;
+        }
+    }
+
+    __device__ __forceinline__ void emit(int64_t o, int64_t, int k, const Slot &s) const
+    {
+        __stcs(out_row + o, s.row[k]);
+        __stcs(out_pay + o, s.pay[k]);
+    }
+};
+
 }  // namespace
 
 qe_status join_key_range(qe_ctx *ctx, const int32_t *keys, const int32_t *pay, int64_t nrows, int32_t host[4],
@@ -367,6 +475,75 @@ extern "C" qe_status qe_join_build(qe_ctx *ctx, const int32_t *keys, const int32
     return join_build_impl(ctx, keys, payload, nrows, opts, false, out, static_cast<cudaStream_t>(stream));
 }
 
+extern "C" qe_status qe_join_build_pair(qe_ctx *ctx, const int32_t *key_hi, const int32_t *key_lo,
+                                        const int32_t *payload, int64_t nrows, qe_hash_table **out, void *stream)
+{
+    if (!ctx) return QE_ERR_INVALID_ARG;
+    if (!out || nrows < 0 || nrows >= (int64_t(1) << 31) || (nrows > 0 && (!key_hi || !key_lo || !payload)) ||
+        !qe_aligned(key_hi, 4) || !qe_aligned(key_lo, 4) || !qe_aligned(payload, 4))
+        return qe_fail(ctx, QE_ERR_INVALID_ARG, "build pair: bad argument");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint64_t slots = 64;
+    while (slots < static_cast<uint64_t>(2 * nrows)) slots <<= 1;
+    qe_hash_table *ht = new qe_hash_table();
+    ht->layout = QE_HT_OPEN;
+    ht->pair = 1;
+    ht->nkeys = nrows;
+    ht->slots = static_cast<int64_t>(slots);
+    const size_t kbytes = slots * 8;
+    ht->bytes = kbytes + slots * 4;
+    qe_status st = qe_alloc(ctx, &ht->mem, ht->bytes, s);
+    if (st != QE_OK) {
+        delete ht;
+        return st;
+    }
+    ht->open = static_cast<unsigned long long *>(ht->mem);
+    ht->payload = reinterpret_cast<int32_t *>(static_cast<char *>(ht->mem) + kbytes);
+    k_fill_u64<<<grid_for(ctx, static_cast<int64_t>(slots)), 256, 0, s>>>(ht->open, static_cast<int64_t>(slots),
+                                                                           HT_EMPTY_SLOT);
+    QE_LAUNCHED(ctx);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && nrows > 0) {
+        ProfScope prof(ctx, "build", s);
+        k_build_pair<<<grid_for(ctx, nrows), 256, 0, s>>>(key_hi, key_lo, payload, nrows, ht->open, ht->payload,
+                                                          static_cast<uint32_t>(slots - 1), ctx->dstat);
+        QE_LAUNCHED(ctx);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        qe_free(ctx, ht->mem, s);
+        delete ht;
+        return qe_cuda_fail(ctx, e, "build pair");
+    }
+    *out = ht;
+    return QE_OK;
+}
+
+extern "C" qe_status qe_join_probe_pair(qe_ctx *ctx, const qe_hash_table *ht, const int32_t *probe_hi,
+                                        const int32_t *probe_lo, const int32_t *sel, int64_t n, int32_t *out_probe_row,
+                                        int32_t *out_build_payload, int64_t capacity, int64_t *out_count, void *stream)
+{
+    if (!ctx) return QE_ERR_INVALID_ARG;
+    if (!ht || n < 0 || n >= (int64_t(1) << 31) || !out_count || capacity < 0 ||
+        (capacity > 0 && (!out_probe_row || !out_build_payload)) || (n > 0 && (!probe_hi || !probe_lo)))
+        return qe_fail(ctx, QE_ERR_INVALID_ARG, "probe pair: bad argument");
+    if (!ht->pair) return qe_fail(ctx, QE_ERR_INVALID_ARG, "probe pair: needs a table from qe_join_build_pair");
+    cudaSetDevice(ctx->device);
+    PairProbeOp op{};
+    op.ht.keys = ht->open;
+    op.ht.vals = ht->payload;
+    op.ht.mask = static_cast<uint32_t>(ht->slots - 1);
+    op.khi = probe_hi;
+    op.klo = probe_lo;
+    op.sel = sel;
+    op.out_row = out_probe_row;
+    op.out_pay = out_build_payload;
+    if (n >= PROBE_TWO_PASS_ROWS)
+        return launch_two_pass<PROBE_ITEMS>(ctx, "probe", n, capacity, out_count, op, static_cast<cudaStream_t>(stream));
+    return launch_compact<PROBE_ITEMS>(ctx, "probe", n, capacity, out_count, op, static_cast<cudaStream_t>(stream));
+}
+
 extern "C" qe_status qe_join_build_set(qe_ctx *ctx, const int32_t *keys, int64_t nrows, const qe_build_opts *opts,
                                        qe_hash_table **out, void *stream)
 {
@@ -385,7 +562,8 @@ extern "C" qe_status qe_join_semi(qe_ctx *ctx, const qe_hash_table *ht, const in
     if (!ht || n < 0 || n >= (int64_t(1) << 31) || !out_count || capacity < 0 || (capacity > 0 && !out_rows) ||
         (n > 0 && !probe_keys) || (anti != 0 && anti != 1))
         return qe_fail(ctx, QE_ERR_INVALID_ARG, "semi-join: bad argument");
-    if (ht->multi) return qe_fail(ctx, QE_ERR_INVALID_ARG, "semi-join: takes a key set or a unique-key table");
+    if (ht->multi || ht->pair)
+        return qe_fail(ctx, QE_ERR_INVALID_ARG, "semi-join: takes a key set or a unique-key table");
     cudaSetDevice(ctx->device);
     SemiOp op{};
     op.ht = ht_view(ht);
@@ -409,6 +587,7 @@ extern "C" qe_status qe_join_probe(qe_ctx *ctx, const qe_hash_table *ht, const i
         return qe_fail(ctx, QE_ERR_INVALID_ARG, "probe: bad argument");
     if (ht->set) return qe_fail(ctx, QE_ERR_INVALID_ARG, "probe: a key set has no payloads (use qe_join_semi)");
     if (ht->multi) return qe_fail(ctx, QE_ERR_INVALID_ARG, "probe: a multimap needs qe_join_probe_multi");
+    if (ht->pair) return qe_fail(ctx, QE_ERR_INVALID_ARG, "probe: a pair-key table needs qe_join_probe_pair");
     cudaSetDevice(ctx->device);
     ProbeOp op{};
     op.ht = ht_view(ht);
@@ -434,7 +613,7 @@ extern "C" qe_status qe_join_info(const qe_hash_table *ht, qe_ht_info *info)
     info->have_payload_range = ht->have_pay;
     info->payload_min = ht->pay_min;
     info->payload_max = ht->pay_max;
-    info->key_set = ht->multi ? 2 : ht->set;
+    info->key_set = ht->pair ? 3 : ht->multi ? 2 : ht->set;
     return QE_OK;
 }
 

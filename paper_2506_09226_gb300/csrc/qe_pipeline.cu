@@ -307,8 +307,8 @@ extern "C" qe_status qe_pipeline(qe_ctx *ctx, const qe_pipeline_desc *desc, cons
             ht = built;
         } else if (inner && ht->set) {
             return qe_fail(ctx, QE_ERR_INVALID_ARG, "pipeline: an inner join needs a table with payloads");
-        } else if (ht->multi) {
-            return qe_fail(ctx, QE_ERR_INVALID_ARG, "pipeline: takes a unique-key table or a key set, not a multimap");
+        } else if (ht->multi || ht->pair) {
+            return qe_fail(ctx, QE_ERR_INVALID_ARG, "pipeline: takes a unique-key table or a key set, not a multimap or pair-key table");
         }
         P.ht = ht_view(ht);
     }

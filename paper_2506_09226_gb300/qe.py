@@ -2,8 +2,8 @@
 
 Every entry point of the C ABI is exposed under its own name (qe_create,
 qe_filter, qe_partition, qe_join_build, qe_join_build_set,
-qe_join_build_multi, qe_join_probe, qe_join_semi, qe_join_probe_multi,
-qe_groupby, qe_pipeline, qe_batch_*) and takes torch CUDA tensors, whose
+qe_join_build_multi, qe_join_build_pair, qe_join_probe, qe_join_semi,
+qe_join_probe_multi, qe_join_probe_pair, qe_groupby, qe_pipeline, qe_batch_*) and takes torch CUDA tensors, whose
 device pointers are passed straight to the library; torch provides device
 memory and streams only.  The exchange planner (qe_plan_*) is host
 arithmetic and takes plain numbers and numpy arrays.  All operator work runs
@@ -157,6 +157,11 @@ _SIGS = {
     "qe_join_probe_multi": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                            ctypes.c_void_p, ctypes.c_void_p]),
+    "qe_join_build_pair": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_int64, ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]),
+    "qe_join_probe_pair": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "qe_join_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(qe_ht_info)]),
     "qe_join_destroy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "qe_groupby": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, qe_col, qe_col,
@@ -388,6 +393,36 @@ def qe_join_probe(ctx: Context, ht: HashTable, probe_keys, sel=None, n=None, cap
         out_count = torch.empty(1, dtype=torch.int64, device=dev)
     ctx.check(ctx.lib.qe_join_probe(ctx.h, ht.h, _ptr(probe_keys), _ptr(sel), n, _ptr(out_rows),
                                     _ptr(out_payload), capacity, _ptr(out_count), _stream(stream)))
+    if check:
+        ctx.sync_status(stream)
+    return out_rows, out_payload, out_count
+
+
+def qe_join_build_pair(ctx: Context, key_hi, key_lo, payload, stream=None, check=True):
+    """Table keyed on a pair of int32 columns (unique pairs)."""
+    h = ctypes.c_void_p()
+    ctx.check(ctx.lib.qe_join_build_pair(ctx.h, _ptr(key_hi), _ptr(key_lo), _ptr(payload), key_hi.numel(),
+                                         ctypes.byref(h), _stream(stream)))
+    if check:
+        ctx.sync_status(stream)
+    return HashTable(ctx, h)
+
+
+def qe_join_probe_pair(ctx: Context, ht: HashTable, probe_hi, probe_lo, sel=None, n=None, capacity=None,
+                       out_rows=None, out_payload=None, out_count=None, stream=None, check=True):
+    if n is None:
+        n = sel.numel() if sel is not None else probe_hi.numel()
+    dev = probe_hi.device
+    if capacity is None:
+        capacity = max(n, 1)
+    if out_rows is None:
+        out_rows = torch.empty(max(capacity, 1), dtype=torch.int32, device=dev)
+    if out_payload is None:
+        out_payload = torch.empty(max(capacity, 1), dtype=torch.int32, device=dev)
+    if out_count is None:
+        out_count = torch.empty(1, dtype=torch.int64, device=dev)
+    ctx.check(ctx.lib.qe_join_probe_pair(ctx.h, ht.h, _ptr(probe_hi), _ptr(probe_lo), _ptr(sel), n, _ptr(out_rows),
+                                         _ptr(out_payload), capacity, _ptr(out_count), _stream(stream)))
     if check:
         ctx.sync_status(stream)
     return out_rows, out_payload, out_count

@@ -1,4 +1,4 @@
-"""GPU parity of the many-to-many join against the CPU oracle.
+"""GPU parity of the many-to-many join and the pair-key join against the CPU oracle.
 
 The outputs of one probe position come out in unspecified order, so each
 position's (row, payload) pairs are compared as sorted lists; everything
@@ -154,4 +154,56 @@ def test_join_multi_edges_and_errors(ctx):
     assert e.value.status == qe.ERR_CAPACITY and e.value.required == 20
     assert out_r[5:].cpu().tolist() == [-5] * 3 and out_p[5:].cpu().tolist() == [-5] * 3
     assert out_r[:5].cpu().tolist() == [0] * 5
+    ht.destroy()
+
+
+# ---------------------------------------------------------------- pair keys
+@pytest.mark.parametrize("n_probe", [1, 4097, 300_001, 5_000_003])
+@pytest.mark.parametrize("with_sel", [False, True])
+def test_join_pair(ctx, n_probe, with_sel):
+    """Join on two key columns: unique build pairs whose halves repeat,
+    one- and two-pass probes, with and without a selection vector."""
+    rng = np.random.default_rng(n_probe % 997 + with_sel)
+    pairs = rng.choice(2_000 * 1_000, 400_000, replace=False)
+    bhi, blo = (pairs // 1_000 - 1_000).astype(np.int32), (pairs % 1_000 * 7 - 3_000).astype(np.int32)
+    bp = rng.integers(-2 ** 31, 2 ** 31 - 1, len(pairs)).astype(np.int32)
+    phi = rng.integers(-1_050, 1_050, n_probe).astype(np.int32)
+    plo = (rng.integers(0, 1_000, n_probe) * 7 - 3_000).astype(np.int32)
+    sel = np.sort(rng.choice(n_probe, n_probe // 2 + 1, replace=False)).astype(np.int32) if with_sel else None
+    ht = qe.qe_join_build_pair(ctx, cuda(bhi), cuda(blo), cuda(bp))
+    assert ht.info().key_set == 3
+    rows, pay, cnt = qe.qe_join_probe_pair(ctx, ht, cuda(phi), cuda(plo), cuda(sel) if with_sel else None)
+    rr, rp = O.join_pair(bhi, blo, bp, phi, plo, sel)
+    c = int(cnt.item())
+    assert c == len(rr)
+    assert np.array_equal(rows[:c].cpu().numpy(), rr) and np.array_equal(pay[:c].cpu().numpy(), rp)
+    ht.destroy()
+
+
+def test_join_pair_edges_and_errors(ctx):
+    m = -2 ** 31
+    # extreme halves are ordinary; only the packed (INT32_MIN, INT32_MIN) is reserved
+    bhi, blo = np.array([m, m, 2 ** 31 - 1], np.int32), np.array([7, 2 ** 31 - 1, m], np.int32)
+    bp = np.array([1, 2, 3], np.int32)
+    ht = qe.qe_join_build_pair(ctx, cuda(bhi), cuda(blo), cuda(bp))
+    phi, plo = np.array([m, 7, m, 2 ** 31 - 1, m], np.int32), np.array([7, m, 2 ** 31 - 1, m, m], np.int32)
+    rows, pay, cnt = qe.qe_join_probe_pair(ctx, ht, cuda(phi), cuda(plo))
+    rr, rp = O.join_pair(bhi, blo, bp, phi, plo)
+    c = int(cnt.item())
+    assert rows[:c].cpu().tolist() == rr.tolist() == [0, 2, 3] and pay[:c].cpu().tolist() == rp.tolist()
+    for call in (lambda: qe.qe_join_probe(ctx, ht, cuda(phi)), lambda: qe.qe_join_semi(ctx, ht, cuda(phi)),
+                 lambda: qe.qe_join_probe_multi(ctx, ht, cuda(phi))):
+        with pytest.raises(qe.QeError) as e:
+            call()
+        assert e.value.status == qe.ERR_INVALID_ARG
+    ht.destroy()
+    for hi, lo, code in (([3, 3], [4, 4], qe.ERR_DUPLICATE_KEY), ([m, 1], [m, 1], qe.ERR_RESERVED_KEY)):
+        with pytest.raises(qe.QeError) as e:
+            qe.qe_join_build_pair(ctx, cuda(np.array(hi, np.int32)), cuda(np.array(lo, np.int32)),
+                                  cuda(np.zeros(2, np.int32)))
+        assert e.value.status == code
+    e32 = torch.empty(0, dtype=torch.int32, device="cuda")
+    ht = qe.qe_join_build_pair(ctx, e32, e32, e32)
+    rows, pay, cnt = qe.qe_join_probe_pair(ctx, ht, cuda(phi), cuda(plo))
+    assert int(cnt.item()) == 0
     ht.destroy()
