@@ -447,9 +447,45 @@ def run_extras(args, qe, ctx, fact, dim, key, pay, okeys, opay, dev, stream, pea
                          "hbm_frac": round((BYTES_FACT_ROW * args.fact_rows + 12 * args.dim_rows) /
                                            (ms * 1e-3) / 1e9 / peak, 4)}
     ctx.sync_status()
-    del sel, rows, attr, dim25
+    del sel, rows, attr, dim25, g25, gout25
     torch.cuda.empty_cache()
+    out["skew_40m_groups"] = run_skew(args, qe, ctx, dev, stream, peak, it)
     return out
+
+
+def run_skew(args, qe, ctx, dev, stream, peak, it):
+    """Skewed, high-cardinality pipeline: 300M fact rows with Zipf(1.1) foreign
+    keys over a 50M-row dimension, grouped on ~40M distinct int64 keys (HBM
+    hash table), at 1 %, 50 % and 90 % selectivity.  hbm_frac counts the
+    28 bytes each fact row reads (fk, date, price, qty, int64 group key)."""
+    from paper_2506_09226_gb300 import datagen
+    n_fact = max(1, args.fact_rows // 2)
+    n_dim = max(1, args.dim_rows * 5 // 2)
+    t0 = time.time()
+    dim = datagen.star_dim(n_dim, 1000, seed=3, device=dev)
+    fact = datagen.star_fact(n_fact, n_dim, seed=3, device=dev, zipf_s=1.1, n_codes=1_000_000,
+                             n_gkeys=max(1, n_fact * 2 // 15))
+    log(f"skew workload generated in {time.time() - t0:.1f}s")
+    cols = [fact[c] for c in ("fk", "date", "price", "qty", "gkey")]
+    aggs = [(qe.SUM, 2, 3), (qe.COUNT, -1, -1), (qe.MIN, 2, -1), (qe.MAX, 2, -1)]
+    cap = max(1, n_fact * 2 // 15)
+    groups, gout = qe.alloc_groups(cap, 4, dev)
+    res = {"fact_rows": n_fact, "dim_rows": n_dim}
+    for sel in (0.01, 0.50, 0.90):
+        c = int(round(sel * datagen.DATE_SPAN))
+        d = qe.pipeline_desc(cols, [(1, qe.LT, c)], fk_col=0, dim_key=dim["key"], dim_payload=dim["attr"],
+                             key_hi_col=-1, key_lo_col=4, aggs=aggs, expected_groups=cap, est_selectivity=sel)
+        fn = lambda: qe.qe_pipeline(ctx, d, cap, check=False, out=(groups, gout))  # noqa: E731
+        fn()
+        ctx.sync_status()
+        ms = timed(fn, max(3, it // 3), stream)
+        res[f"{int(sel * 100)}%"] = {"ms": ms, "rows_per_s": n_fact / (ms * 1e-3),
+                                     "ngroups": int(groups.ngroups.item()),
+                                     "hbm_frac": round(28 * n_fact / (ms * 1e-3) / 1e9 / peak, 4)}
+    ctx.sync_status()
+    del dim, fact, cols, groups, gout
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_e2e(args, qe, ctx, fact, dim, key, pay, okeys, opay, offs, groups, gout, dev, stream):

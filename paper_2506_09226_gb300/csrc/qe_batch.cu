@@ -426,7 +426,6 @@ extern "C" qe_status qe_batch_create(qe_ctx *ctx, const qe_pipeline_desc *descs,
         B.P.g.words = gh;
         B.P.g.mask = B.hslots - 1;
         B.P.g.stride = 1 + B.P.ops.n;
-        B.P.g.nkeys = gh + B.hslots * B.P.g.stride;
         B.P.g.capacity = B.out.capacity;
         B.P.g.st = ctx->dstat;
         B.emitted = gh + B.hslots * B.P.g.stride + 1;

@@ -225,7 +225,7 @@ qe_status gt_create(qe_ctx *ctx, int64_t capacity, int naggs, GroupTableHost &t,
     while (slots < want) slots <<= 1;
     t.slots = slots;
     t.stride = 1 + naggs;
-    // table words, then two counters: distinct keys inserted, groups emitted
+    // table words, then a reserved word and the count of groups emitted
     t.bytes = (slots * t.stride + 2) * sizeof(unsigned long long);
     void *p = nullptr;
     qe_status st = qe_alloc(ctx, &p, t.bytes, s);

@@ -147,7 +147,6 @@ extern "C" qe_status qe_groupby(qe_ctx *ctx, int64_t n, const int32_t *rows, qe_
     A.g.words = t.words;
     A.g.mask = t.slots - 1;
     A.g.stride = t.stride;
-    A.g.nkeys = t.words + t.slots * t.stride;
     A.g.capacity = out->capacity;
     A.g.st = ctx->dstat;
     const size_t budget = ctx->smem_optin > 4096 ? ctx->smem_optin - 4096 : 0;

@@ -406,32 +406,32 @@ struct GTable {
     unsigned long long *words;
     uint64_t mask;                    // slots - 1
     int stride;                       // 1 + naggs
-    unsigned long long *nkeys;        // distinct keys inserted
     int64_t capacity;                 // caller's group capacity
     qe_dev_status *st;
 };
 
-// Returns the slot index of key kx (inserting it), or -1 when the caller's
-// capacity is exhausted (QE_ERR_CAPACITY recorded) or the table is full.
+// Longest probe chain before the table counts as overfull.  With at least
+// twice as many slots as the caller's capacity the load stays at or below
+// one half while the groups fit, where linear-probing chains stay short.
+#define GT_MAX_PROBE 4096
+
+// Returns the slot index of key kx (inserting it), or -1 when no slot turns
+// up within GT_MAX_PROBE probes (more groups than the capacity filled the
+// table; QE_ERR_CAPACITY recorded).  Groups are counted, and a count above
+// the capacity reported, when the table is compacted, so inserts share no
+// counter.  Slot keys only change from 0 to their key, so a stale read is
+// either 0 (the CAS then returns the key) or the final key.
 __device__ __forceinline__ int64_t gt_find_insert(const GTable &g, unsigned long long kx)
 {
     uint64_t i = gb_hash(kx) & g.mask;
-    for (uint64_t probes = 0; probes <= g.mask; probes++) {
+    const uint64_t limit = g.mask < GT_MAX_PROBE ? g.mask : GT_MAX_PROBE;
+    for (uint64_t probes = 0; probes <= limit; probes++) {
         unsigned long long *cell = g.words + i * g.stride;
-        unsigned long long cur = *reinterpret_cast<volatile unsigned long long *>(cell);
+        const unsigned long long cur = *reinterpret_cast<volatile unsigned long long *>(cell);
         if (cur == kx) return static_cast<int64_t>(i);
         if (cur == 0) {
-            if (static_cast<int64_t>(*reinterpret_cast<volatile unsigned long long *>(g.nkeys)) >= g.capacity) {
-                dev_report(g.st, QE_ERR_CAPACITY, g.capacity + 1);
-                return -1;
-            }
-            unsigned long long old = atomicCAS(cell, 0ull, kx);
-            if (old == 0) {
-                unsigned long long c = atomicAdd(g.nkeys, 1ull) + 1;
-                if (static_cast<int64_t>(c) > g.capacity) dev_report(g.st, QE_ERR_CAPACITY, static_cast<int64_t>(c));
-                return static_cast<int64_t>(i);
-            }
-            if (old == kx) return static_cast<int64_t>(i);
+            const unsigned long long old = atomicCAS(cell, 0ull, kx);
+            if (old == 0 || old == kx) return static_cast<int64_t>(i);
         }
         i = (i + 1) & g.mask;
     }

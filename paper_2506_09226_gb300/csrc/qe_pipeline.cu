@@ -262,7 +262,6 @@ qe_status pipeline_launch(qe_ctx *ctx, PipeSpec &P, const PipePlan &plan, const 
     P.g.words = t.words;
     P.g.mask = t.slots - 1;
     P.g.stride = t.stride;
-    P.g.nkeys = t.words + t.slots * t.stride;
     P.g.capacity = capacity;
     P.g.st = ctx->dstat;
     if (P.n == 0) return QE_OK;

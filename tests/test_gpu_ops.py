@@ -331,6 +331,10 @@ def test_groupby_gather_and_errors(ctx):
     with pytest.raises(qe.QeError) as e:
         qe.qe_groupby(ctx, cuda(np.arange(1000, dtype=np.int64)), [(qe.COUNT, None, None)], capacity=100)
     assert e.value.status == qe.ERR_CAPACITY and e.value.required > 100
+    # a few groups too many: the exact number of groups is reported
+    with pytest.raises(qe.QeError) as e:
+        qe.qe_groupby(ctx, cuda(np.arange(150, dtype=np.int64).repeat(3)), [(qe.COUNT, None, None)], capacity=100)
+    assert e.value.status == qe.ERR_CAPACITY and e.value.required == 150
     with pytest.raises(qe.QeError) as e:
         qe.qe_groupby(ctx, cuda(np.array([1, -2 ** 63], np.int64)), [(qe.COUNT, None, None)], capacity=8)
     assert e.value.status == qe.ERR_RESERVED_KEY
