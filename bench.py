@@ -364,6 +364,10 @@ def run_qe(args):
         del okeys, opay, dim, fact, key, pay, desc, groups, gout
         torch.cuda.empty_cache()
         forms = run_forms(args, qe, ctx, dev, stream, None, None, peak)
+    # the skewed, high-cardinality pipeline last: its multi-GB group table
+    # stays out of the way of the batch and serve forms
+    if "extras" in args.forms:
+        extras["skew_40m_groups"] = run_skew(args, qe, ctx, dev, stream, peak, max(3, args.steps // 2))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -449,7 +453,6 @@ def run_extras(args, qe, ctx, fact, dim, key, pay, okeys, opay, dev, stream, pea
     ctx.sync_status()
     del sel, rows, attr, dim25, g25, gout25
     torch.cuda.empty_cache()
-    out["skew_40m_groups"] = run_skew(args, qe, ctx, dev, stream, peak, it)
     return out
 
 
