@@ -390,12 +390,16 @@ __device__ __forceinline__ int64_t agg_decode(int op, unsigned long long s)
 }
 
 // Fold an encoded contribution into an aggregate cell (shared or global).
+// Fold one encoded value into an HBM aggregate cell.  The MAX-kind check
+// reads L2 (where the atomics land) without the ordering of a volatile
+// load, so independent rows' reads can overlap; a stale value can only
+// cause a redundant atomic, since cells only grow.
 __device__ __forceinline__ void agg_fold(unsigned long long *cell, int op, unsigned long long e)
 {
     if (op == QE_SUM || op == QE_COUNT) {
         if (e) atomicAdd(cell, e);
     } else {
-        if (*reinterpret_cast<volatile unsigned long long *>(cell) < e) atomicMax(cell, e);
+        if (__ldcg(cell) < e) atomicMax(cell, e);
     }
 }
 
@@ -419,15 +423,16 @@ struct GTable {
 // up within GT_MAX_PROBE probes (more groups than the capacity filled the
 // table; QE_ERR_CAPACITY recorded).  Groups are counted, and a count above
 // the capacity reported, when the table is compacted, so inserts share no
-// counter.  Slot keys only change from 0 to their key, so a stale read is
-// either 0 (the CAS then returns the key) or the final key.
+// counter.  Slot keys only change from 0 to their key, so a stale read
+// (plain L2 loads, no volatile ordering) is either 0 (the CAS then returns
+// the key) or the final key.
 __device__ __forceinline__ int64_t gt_find_insert(const GTable &g, unsigned long long kx)
 {
     uint64_t i = gb_hash(kx) & g.mask;
     const uint64_t limit = g.mask < GT_MAX_PROBE ? g.mask : GT_MAX_PROBE;
     for (uint64_t probes = 0; probes <= limit; probes++) {
         unsigned long long *cell = g.words + i * g.stride;
-        const unsigned long long cur = *reinterpret_cast<volatile unsigned long long *>(cell);
+        const unsigned long long cur = __ldcg(cell);
         if (cur == kx) return static_cast<int64_t>(i);
         if (cur == 0) {
             const unsigned long long old = atomicCAS(cell, 0ull, kx);

@@ -285,6 +285,45 @@ __device__ __forceinline__ void fold_row(const PipeSpec &P, const TableCfg &T, u
     spill_row_ni(P.g, P.ops, kx, e[0], e[1], e[2], e[3]);
 }
 
+static __device__ __noinline__ int64_t gt_find_insert_ni(const GTable g, unsigned long long kx)
+{
+    return gt_find_insert(g, kx);
+}
+
+// Fold ITEMS rows into the HBM hash table: every row's first probe is read
+// before any row is folded, so the rows' DRAM round trips overlap (a row
+// whose key is not in its home slot takes the out-of-line probe loop).
+template <int ITEMS>
+__device__ __forceinline__ void fold_rows_ghash(const PipeSpec &P, const bool (&ok)[ITEMS], const int64_t (&hi)[ITEMS],
+                                                const int64_t (&lo)[ITEMS], const RowVals (&v)[ITEMS])
+{
+    unsigned long long kx[ITEMS], cur[ITEMS];
+    uint64_t home[ITEMS];
+#pragma unroll
+    for (int k = 0; k < ITEMS; k++) {
+        int64_t key = lo[k];
+        if (P.hi_slot >= 0)
+            key = static_cast<int64_t>((static_cast<uint64_t>(hi[k]) << 32) | static_cast<uint32_t>(lo[k]));
+        kx[k] = static_cast<unsigned long long>(key) ^ GB_SIGN;
+        home[k] = gb_hash(kx[k]) & P.g.mask;
+        cur[k] = ok[k] ? __ldcg(P.g.words + home[k] * P.g.stride) : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < ITEMS; k++) {
+        if (!ok[k]) continue;
+        if (kx[k] == 0) {
+            dev_report(P.g.st, QE_ERR_RESERVED_KEY, 0);
+            continue;
+        }
+        const int64_t s = cur[k] == kx[k] ? static_cast<int64_t>(home[k]) : gt_find_insert_ni(P.g, kx[k]);
+        if (s < 0) continue;
+        unsigned long long *cell = P.g.words + s * P.g.stride + 1;
+#pragma unroll
+        for (int a = 0; a < QE_MAX_AGGS; a++)
+            if (a < P.ops.n) agg_fold(cell + a, P.ops.op[a], agg_value_enc(P, a, v[k]));
+    }
+}
+
 // Join probe of a loaded row; false when the row does not join.  Sets the
 // key parts.
 __device__ __forceinline__ bool row_probe(const PipeSpec &P, const RowVals &v, int64_t &hi, int64_t &lo)

@@ -59,9 +59,13 @@ __global__ void __launch_bounds__(PT, 1) k_pipeline(PipeSpec P, TableCfg T)
         bool ok[ITEMS];
 #pragma unroll
         for (int k = 0; k < ITEMS; k++) ok[k] = row_probe(P, v[k], hi[k], lo[k]);
+        if (T.mode == TM_GLOBAL_HASH) {
+            fold_rows_ghash<ITEMS>(P, ok, hi, lo, v);
+        } else {
 #pragma unroll
-        for (int k = 0; k < ITEMS; k++)
-            if (ok[k]) fold_row(P, T, sm, hi[k], lo[k], v[k]);
+            for (int k = 0; k < ITEMS; k++)
+                if (ok[k]) fold_row(P, T, sm, hi[k], lo[k], v[k]);
+        }
     }
     __syncthreads();
     table_flush(P, T, sm);
