@@ -581,7 +581,7 @@ def main():
     ap.add_argument("--serve-scale", type=float, default=1.0)
     ap.add_argument("--ref-sample", type=int, default=2_000_000,
                     help="fact rows (and pairs) per reference-arm step")
-    ap.add_argument("--cpu-sample", type=int, default=24_000_000,
+    ap.add_argument("--cpu-sample", type=int, default=32_000_000,
                     help="fact rows (and pairs) of the cpu_baseline sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
