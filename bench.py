@@ -364,8 +364,10 @@ def run_qe(args):
         del okeys, opay, dim, fact, key, pay, desc, groups, gout
         torch.cuda.empty_cache()
         forms = run_forms(args, qe, ctx, dev, stream, None, None, peak)
-    # the skewed, high-cardinality pipeline last: its multi-GB group table
-    # stays out of the way of the batch and serve forms
+    # the join variants and the skewed, high-cardinality pipeline last: their
+    # multi-GB tables stay out of the way of the batch and serve forms
+    if "variants" in args.forms:
+        extras["variants"] = run_variants(args, qe, ctx, dev, stream, peak, max(3, args.steps // 2))
     if "extras" in args.forms:
         extras["skew_40m_groups"] = run_skew(args, qe, ctx, dev, stream, peak, max(3, args.steps // 2))
 
@@ -491,6 +493,140 @@ def run_skew(args, qe, ctx, dev, stream, peak, it):
     return res
 
 
+def run_variants(args, qe, ctx, dev, stream, peak, it):
+    """The operator variants beside the inner join, on the step's fact table
+    (regenerated from its seed) and its filter date < DATE_LT (about half the
+    rows).  Each entry gives the whole call's time and its algorithmic bytes
+    over that time as a fraction of the HBM peak:
+      pipeline_semi / pipeline_anti: filter + semi- / anti-join against a key
+        set of half the dimension's keys + group-by flag (the set is built in
+        the call): 21 B per fact row + 4 B per set key;
+      single_table: filter + group-by flag, no join (fk_col = -1): 17 B per row;
+      semi_join / anti_join: stand-alone, over the filter's selection vector:
+        4 B selection + 4 B key + 4 B per output position;
+      multi_build / multi_probe: many-to-many join against a partsupp-shaped
+        build side (4 rows per key, 4x the dimension's rows): build 12 B per
+        row (key and payload in, payload placed); probe over the selection,
+        every position matching 4 rows: 4 B selection + 4 B key + 8 B per pair;
+      pair_build / pair_probe: join on (fk, a second key column) against unique
+        pairs (4 per first key, 4x the dimension's rows): build 12 B in + 12 B
+        out per row; probe 4 B selection + 8 B keys + 8 B per output, about
+        4 positions in 5 matching."""
+    from paper_2506_09226_gb300 import datagen
+    nd, n = args.dim_rows, args.fact_rows
+    t0 = time.time()
+    dim = datagen.star_dim(nd, 1000, seed=1, device=dev)
+    fact = datagen.star_fact(n, nd, seed=1, device=dev)
+    log(f"variant workload generated in {time.time() - t0:.1f}s")
+    cols = [fact[c] for c in COLS]
+    aggs = [(qe.SUM, 2, 3), (qe.COUNT, -1, -1), (qe.MIN, 2, -1), (qe.MAX, 2, -1)]
+    groups, gout = qe.alloc_groups(64, 4, dev)
+    res = {}
+
+    def entry(ms, units, nbytes, **kw):
+        return {"ms": ms, "rows_per_s": units / (ms * 1e-3),
+                "hbm_frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4), **kw}
+
+    def kernel_ms(fn, name):
+        ctx.profile(True)
+        ctx.profile_reset()
+        ms = timed(fn, it, stream)
+        c, tot = ctx.profile_read(name)
+        ctx.profile(False)
+        return ms, (tot / c if c else None)
+
+    # semi- and anti-join pipelines, and the single-table aggregation
+    half = dim["key"][: nd // 2].contiguous()
+    for name, kind in (("pipeline_semi", qe.SEMI), ("pipeline_anti", qe.ANTI)):
+        d = qe.pipeline_desc(cols, [(1, qe.LT, DATE_LT)], fk_col=0, dim_key=half, key_hi_col=-1, key_lo_col=4,
+                             aggs=aggs, expected_groups=3, est_selectivity=DATE_LT / datagen.DATE_SPAN,
+                             key_range=(None, (0, 2)), join_kind=kind)
+        fn = lambda: qe.qe_pipeline(ctx, d, 64, check=False, out=(groups, gout))  # noqa: E731
+        fn()
+        ctx.sync_status()
+        ms, kms = kernel_ms(fn, "pipeline")
+        res[name] = entry(ms, n, BYTES_FACT_ROW * n + 4 * half.numel(), kernel_ms=kms,
+                          kernel_hbm_frac=round(BYTES_FACT_ROW * n / (kms * 1e-3) / 1e9 / peak, 4) if kms else None,
+                          ngroups=int(groups.ngroups.item()))
+    d = qe.pipeline_desc(cols[1:], [(0, qe.LT, DATE_LT)], key_hi_col=-1, key_lo_col=3, aggs=[
+        (qe.SUM, 1, 2), (qe.COUNT, -1, -1), (qe.MIN, 1, -1), (qe.MAX, 1, -1)], expected_groups=3,
+        est_selectivity=DATE_LT / datagen.DATE_SPAN, key_range=(None, (0, 2)))
+    fn = lambda: qe.qe_pipeline(ctx, d, 64, check=False, out=(groups, gout))  # noqa: E731
+    fn()
+    ctx.sync_status()
+    ms, kms = kernel_ms(fn, "pipeline")
+    res["single_table"] = entry(ms, n, 17 * n, kernel_ms=kms, ngroups=int(groups.ngroups.item()))
+    del d
+
+    # the filter's selection vector, shared by the stand-alone joins
+    sel = torch.empty(n, dtype=torch.int32, device=dev)
+    cnt = torch.empty(1, dtype=torch.int64, device=dev)
+    qe.qe_filter(ctx, [fact["date"]], [(0, qe.LT, DATE_LT)], sel, cnt)
+    nsel = int(cnt.item())
+    out_rows = torch.empty(4 * nsel + 1, dtype=torch.int32, device=dev)
+    out_pay = torch.empty(4 * nsel + 1, dtype=torch.int32, device=dev)
+    ocnt = torch.empty(1, dtype=torch.int64, device=dev)
+
+    # stand-alone semi- and anti-join
+    hs = qe.qe_join_build_set(ctx, half)
+    for name, anti in (("semi_join", False), ("anti_join", True)):
+        fn = lambda: qe.qe_join_semi(ctx, hs, fact["fk"], sel, n=nsel, anti=anti, capacity=nsel,  # noqa: E731
+                                     out_rows=out_rows, out_count=ocnt, check=False)
+        fn()
+        ctx.sync_status()
+        ms = timed(fn, it, stream)
+        k = int(ocnt.item())
+        res[name] = entry(ms, nsel, 8 * nsel + 4 * k, outputs=k)
+    hs.destroy()
+    del half
+
+    # many-to-many join
+    md = datagen.multi_dim(nd, 4, 1000, seed=4, device=dev)
+    nb = md["key"].numel()
+
+    def mbuild():
+        qe.qe_join_build_multi(ctx, md["key"], md["attr"], check=False).destroy()
+    mbuild()
+    ctx.sync_status()
+    res["multi_build"] = entry(timed(mbuild, it, stream), nb, 12 * nb)
+    hm = qe.qe_join_build_multi(ctx, md["key"], md["attr"])
+    fn = lambda: qe.qe_join_probe_multi(ctx, hm, fact["fk"], sel, n=nsel, capacity=out_rows.numel(),  # noqa: E731
+                                        out_rows=out_rows, out_payload=out_pay, out_count=ocnt, check=False)
+    fn()
+    ctx.sync_status()
+    ms = timed(fn, it, stream)
+    k = int(ocnt.item())
+    res["multi_probe"] = entry(ms, nsel, 8 * nsel + 8 * k, outputs=k)
+    hm.destroy()
+    del md
+
+    # pair-key join
+    pd = datagen.pair_dim(nd, 4, seed=5, device=dev)
+    plo = datagen.pair_probe_lo(fact["fk"], pd["off"], 5, seed=5)
+    nb = pd["hi"].numel()
+
+    def pbuild():
+        qe.qe_join_build_pair(ctx, pd["hi"], pd["lo"], pd["payload"], check=False).destroy()
+    pbuild()
+    ctx.sync_status()
+    res["pair_build"] = entry(timed(pbuild, it, stream), nb, 24 * nb)
+    hp = qe.qe_join_build_pair(ctx, pd["hi"], pd["lo"], pd["payload"])
+    fn = lambda: qe.qe_join_probe_pair(ctx, hp, fact["fk"], plo, sel, n=nsel, capacity=nsel,  # noqa: E731
+                                       out_rows=out_rows, out_payload=out_pay, out_count=ocnt, check=False)
+    fn()
+    ctx.sync_status()
+    ms = timed(fn, it, stream)
+    k = int(ocnt.item())
+    res["pair_probe"] = entry(ms, nsel, 12 * nsel + 8 * k, outputs=k)
+    hp.destroy()
+    ctx.sync_status()
+    res["workload"] = (f"{n} fact rows, filter date < {DATE_LT} ({nsel} selected); key set of {nd // 2} keys; "
+                       f"build sides of {4 * nd} rows (4 per key)")
+    del pd, plo, sel, out_rows, out_pay, dim, fact, cols, groups, gout
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_e2e(args, qe, ctx, fact, dim, key, pay, okeys, opay, offs, groups, gout, dev, stream):
     """Same step through the public API with inputs copied from pinned host
     memory and the results read back, every step."""
@@ -575,7 +711,7 @@ def main():
     ap.add_argument("--dim-rows", type=int, default=20_000_000)
     ap.add_argument("--pairs", type=int, default=600_000_000)
     ap.add_argument("--log2f", type=int, default=10)
-    ap.add_argument("--forms", default="extras,batch,serve")
+    ap.add_argument("--forms", default="extras,variants,batch,serve")
     ap.add_argument("--batch-count", type=int, default=10_000)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-scale", type=float, default=1.0)

@@ -47,7 +47,9 @@ struct PipeSpec {
     const int32_t *s_pred, *s_fk, *s_y;
     const void *s_hi;
     const long long *s_x;
+    const void *s_lo;                   // key column of the fact-keyed star kinds
     int32_t p0_lo, p0_hi, p0_neg, s_h8;
+    int32_t s_l8, s_has_hi;
     int32_t s_hmin, s_lmin;
     uint32_t s_hspan, s_lspan, s_ns;
     int32_t join_kind;                  // qe_join_kind
@@ -404,23 +406,42 @@ __device__ __forceinline__ void table_flush(const PipeSpec &P, const TableCfg &T
 // Largest direct array (slots) whose SUM the star kernels keep in 32-bit halves.
 constexpr uint64_t STAR_NSUM_SLOTS = 1024;
 
+// Kinds of the star shape: the group key's low part is the inner join's
+// payload; or it is a fact column and the join is a semi- or anti-join
+// (membership in a dense key set), or there is no join.
+enum { STAR_INNER = 0, STAR_SEMI = 1, STAR_ANTI = 2, STAR_NONE = 3 };
+
 // The row work of one star tile: predicate, dense lookup, direct-array
 // (or spilled hash) update of the ITEMS rows a thread holds; bit k of cin
-// marks row k as inside the range.
-template <bool GLOBAL, int ITEMS, bool NSUM>
+// marks row k as inside the range.  cl holds the key column of the kinds
+// other than STAR_INNER.
+template <bool GLOBAL, int ITEMS, bool NSUM, int JK = STAR_INNER>
 __device__ __forceinline__ void star_rows(const PipeSpec &P, unsigned long long *sm, const int (&cd)[ITEMS],
-                                          const int (&cf)[ITEMS], const int (&ch)[ITEMS], const int (&cq)[ITEMS],
-                                          const long long (&cx)[ITEMS], unsigned cin)
+                                          const int (&cf)[ITEMS], const int (&ch)[ITEMS], const int (&cl)[ITEMS],
+                                          const int (&cq)[ITEMS], const long long (&cx)[ITEMS], unsigned cin)
 {
     bool ok[ITEMS];
     int32_t pay[ITEMS];
 #pragma unroll
     for (int k = 0; k < ITEMS; k++) {
-        const uint32_t ks = static_cast<uint32_t>(cf[k]) - static_cast<uint32_t>(P.ht.key_min);
         const bool pass = (cd[k] >= P.p0_lo && cd[k] <= P.p0_hi) != static_cast<bool>(P.p0_neg);
-        const bool hit = ((cin >> k) & 1u) && pass && ks < P.ht.range;
-        pay[k] = hit ? ht_ld(P.ht, P.ht.payload + ks) : 0;
-        ok[k] = hit && (P.ht.full || ((ht_ld(P.ht, P.ht.bitmap + (ks >> 5)) >> (ks & 31)) & 1u));
+        if constexpr (JK == STAR_INNER) {
+            const uint32_t ks = static_cast<uint32_t>(cf[k]) - static_cast<uint32_t>(P.ht.key_min);
+            const bool hit = ((cin >> k) & 1u) && pass && ks < P.ht.range;
+            pay[k] = hit ? ht_ld(P.ht, P.ht.payload + ks) : 0;
+            ok[k] = hit && (P.ht.full || ((ht_ld(P.ht, P.ht.bitmap + (ks >> 5)) >> (ks & 31)) & 1u));
+        } else if constexpr (JK == STAR_NONE) {
+            pay[k] = cl[k];
+            ok[k] = ((cin >> k) & 1u) && pass;
+        } else {
+            // membership: in the key range and (a full range or) its bit set
+            const uint32_t ks = static_cast<uint32_t>(cf[k]) - static_cast<uint32_t>(P.ht.key_min);
+            const bool live = ((cin >> k) & 1u) && pass;
+            const bool in = live && ks < P.ht.range &&
+                            (P.ht.full || ((ht_ld(P.ht, P.ht.bitmap + (ks >> 5)) >> (ks & 31)) & 1u));
+            pay[k] = cl[k];
+            ok[k] = live && (JK == STAR_SEMI ? in : !in);
+        }
     }
 #pragma unroll
     for (int k = 0; k < ITEMS; k++) {
@@ -456,8 +477,11 @@ __device__ __forceinline__ void star_rows(const PipeSpec &P, unsigned long long 
                 if (sm[3 * P.s_ns + idx] < emax) atomicMax(sm + 3 * P.s_ns + idx, emax);
             }
         } else {
-            const int64_t key = static_cast<int64_t>((static_cast<uint64_t>(static_cast<int64_t>(ch[k])) << 32) |
-                                                     static_cast<uint32_t>(pay[k]));
+            // the group key: (hi, lo) packed, or lo alone (sign-extended) without a hi part
+            const int64_t key = JK == STAR_INNER || P.s_has_hi
+                                    ? static_cast<int64_t>((static_cast<uint64_t>(static_cast<int64_t>(ch[k])) << 32) |
+                                                           static_cast<uint32_t>(pay[k]))
+                                    : static_cast<int64_t>(pay[k]);
             const unsigned long long kx = static_cast<unsigned long long>(key) ^ GB_SIGN;
             if (kx == 0) {
                 dev_report(P.g.st, QE_ERR_RESERVED_KEY, 0);
@@ -473,11 +497,11 @@ __device__ __forceinline__ void star_rows(const PipeSpec &P, unsigned long long 
 // starting at r0, r0 + stride, ... below r1; all columns of the next tile are
 // loaded into registers while the current one is processed, so the register
 // file holds the loads in flight.
-template <bool GLOBAL, int ITEMS, int THREADS, bool NSUM>
+template <bool GLOBAL, int ITEMS, int THREADS, bool NSUM, int JK = STAR_INNER>
 __device__ __forceinline__ void star_range(const PipeSpec &P, unsigned long long *sm, int64_t r0, int64_t r1,
                                            int64_t stride)
 {
-    int d[ITEMS], f[ITEMS], h[ITEMS], q[ITEMS];
+    int d[ITEMS], f[ITEMS], h[ITEMS], l[ITEMS], q[ITEMS];
     long long x[ITEMS];
     unsigned inmask = 0;
     auto load = [&](int64_t t0) {
@@ -488,10 +512,15 @@ __device__ __forceinline__ void star_range(const PipeSpec &P, unsigned long long
             const bool in = r < r1;
             inmask |= in ? (1u << k) : 0u;
             d[k] = in ? __ldcs(P.s_pred + r) : 0;
-            f[k] = in ? __ldcs(P.s_fk + r) : 0;
-            h[k] = in ? (P.s_h8 ? static_cast<int>(__ldcs(static_cast<const signed char *>(P.s_hi) + r))
-                                : __ldcs(static_cast<const int32_t *>(P.s_hi) + r))
-                      : 0;
+            f[k] = JK != STAR_NONE && in ? __ldcs(P.s_fk + r) : 0;
+            h[k] = (JK == STAR_INNER || P.s_has_hi) && in
+                       ? (P.s_h8 ? static_cast<int>(__ldcs(static_cast<const signed char *>(P.s_hi) + r))
+                                 : __ldcs(static_cast<const int32_t *>(P.s_hi) + r))
+                       : 0;
+            l[k] = JK != STAR_INNER && in
+                       ? (P.s_l8 ? static_cast<int>(__ldcs(static_cast<const signed char *>(P.s_lo) + r))
+                                 : __ldcs(static_cast<const int32_t *>(P.s_lo) + r))
+                       : 0;
             x[k] = in ? __ldcs(P.s_x + r) : 0;
             q[k] = in ? __ldcs(P.s_y + r) : 0;
         }
@@ -499,7 +528,7 @@ __device__ __forceinline__ void star_range(const PipeSpec &P, unsigned long long
     if (r0 >= r1) return;
     load(r0);
     for (int64_t t0 = r0; t0 < r1; t0 += stride) {
-        int cd[ITEMS], cf[ITEMS], ch[ITEMS], cq[ITEMS];
+        int cd[ITEMS], cf[ITEMS], ch[ITEMS], cl[ITEMS], cq[ITEMS];
         long long cx[ITEMS];
         const unsigned cin = inmask;
 #pragma unroll
@@ -507,11 +536,12 @@ __device__ __forceinline__ void star_range(const PipeSpec &P, unsigned long long
             cd[k] = d[k];
             cf[k] = f[k];
             ch[k] = h[k];
+            cl[k] = l[k];
             cq[k] = q[k];
             cx[k] = x[k];
         }
         load(t0 + stride);   // next tile's loads overlap this tile's work
-        star_rows<GLOBAL, ITEMS, NSUM>(P, sm, cd, cf, ch, cq, cx, cin);
+        star_rows<GLOBAL, ITEMS, NSUM, JK>(P, sm, cd, cf, ch, cl, cq, cx, cin);
     }
 }
 
@@ -540,9 +570,12 @@ static inline void star_predicate(PipeSpec &P)
     P.p0_hi = static_cast<int32_t>(b > INT32_MAX ? INT32_MAX : b);
     P.p0_neg = neg;
     P.s_pred = static_cast<const int32_t *>(P.col[P.pslot[0]]);
-    P.s_fk = static_cast<const int32_t *>(P.col[P.fk_slot]);
-    P.s_hi = P.col[P.hi_slot];
-    P.s_h8 = P.type[P.hi_slot] == QE_I8;
+    P.s_fk = P.has_join ? static_cast<const int32_t *>(P.col[P.fk_slot]) : nullptr;
+    P.s_has_hi = P.hi_slot >= 0;
+    P.s_hi = P.s_has_hi ? P.col[P.hi_slot] : nullptr;
+    P.s_h8 = P.s_has_hi && P.type[P.hi_slot] == QE_I8;
+    P.s_lo = P.lo_slot >= 0 ? P.col[P.lo_slot] : nullptr;
+    P.s_l8 = P.lo_slot >= 0 && P.type[P.lo_slot] == QE_I8;
     P.s_x = static_cast<const long long *>(P.col[P.x_slot]);
     P.s_y = static_cast<const int32_t *>(P.col[P.y_slot]);
     P.s_hmin = static_cast<int32_t>(P.dk.hi_min);
@@ -552,16 +585,36 @@ static inline void star_predicate(PipeSpec &P)
     P.s_ns = static_cast<uint32_t>(P.dk.nslots);
 }
 
-// The star specialisation applies (see k_pipeline_star).
+// The star kind of a pipeline (see k_pipeline_star), or -1 when the shape
+// is not a star: one int32 predicate column, the aggregates [SUM(x*y),
+// COUNT, MIN(x), MAX(x)] with x int64 and y int32, a direct array whose key
+// parts stay within int32, and either an inner join through a dense table
+// keyed (int8/int32 column, payload), or a key (optional int8/int32 column,
+// int8/int32 column) with a semi- or anti-join through a dense key set or
+// with no join.
+static inline int star_kind(const PipeSpec &P, const TableCfg &T)
+{
+    auto narrow = [&](int slot) { return P.type[slot] == QE_I8 || P.type[slot] == QE_I32; };
+    const bool common =
+        (T.mode == TM_SMEM_DENSE || T.mode == TM_GLOBAL_DENSE) && P.npreds == 1 && P.type[P.pslot[0]] == QE_I32 &&
+        P.ops.n == 4 && P.ops.op[0] == QE_SUM && P.src[0] == SRC_XY && P.ops.op[1] == QE_COUNT &&
+        P.ops.op[2] == QE_MIN && P.src[2] == SRC_X && P.ops.op[3] == QE_MAX && P.src[3] == SRC_X &&
+        P.type[P.x_slot] == QE_I64 && P.type[P.y_slot] == QE_I32 && P.dk.stride == 4 && P.dk.nslots < (1ull << 31) &&
+        P.dk.hi_min >= INT32_MIN && P.dk.hi_min + static_cast<int64_t>(P.dk.hi_span) <= INT32_MAX &&
+        P.dk.lo_min >= INT32_MIN && P.dk.lo_min + static_cast<int64_t>(P.dk.lo_span) <= INT32_MAX;
+    if (!common) return -1;
+    if (P.has_join && P.join_kind == QE_JOIN_INNER)
+        return P.ht.layout == QE_HT_DENSE && P.lo_slot == QE_JOIN_PAYLOAD && P.hi_slot >= 0 && narrow(P.hi_slot)
+                   ? STAR_INNER : -1;
+    if (P.lo_slot < 0 || !narrow(P.lo_slot) || (P.hi_slot >= 0 && !narrow(P.hi_slot))) return -1;
+    if (!P.has_join) return STAR_NONE;
+    if (P.ht.layout != QE_HT_DENSE) return -1;
+    return P.join_kind == QE_JOIN_SEMI ? STAR_SEMI : STAR_ANTI;
+}
+
+// The inner-join star (the one kind the batch kernel runs as a star item).
 static inline bool star_shape(const PipeSpec &P, const TableCfg &T)
 {
-    return (T.mode == TM_SMEM_DENSE || T.mode == TM_GLOBAL_DENSE) && P.npreds == 1 && P.type[P.pslot[0]] == QE_I32 &&
-           P.has_join && P.join_kind == QE_JOIN_INNER && P.ht.layout == QE_HT_DENSE && P.lo_slot == QE_JOIN_PAYLOAD && P.hi_slot >= 0 &&
-           (P.type[P.hi_slot] == QE_I8 || P.type[P.hi_slot] == QE_I32) && P.ops.n == 4 && P.ops.op[0] == QE_SUM &&
-           P.src[0] == SRC_XY && P.ops.op[1] == QE_COUNT && P.ops.op[2] == QE_MIN && P.src[2] == SRC_X &&
-           P.ops.op[3] == QE_MAX && P.src[3] == SRC_X && P.type[P.x_slot] == QE_I64 && P.type[P.y_slot] == QE_I32 &&
-           P.dk.stride == 4 && P.dk.nslots < (1ull << 31) && P.dk.hi_min >= INT32_MIN &&
-           P.dk.hi_min + static_cast<int64_t>(P.dk.hi_span) <= INT32_MAX && P.dk.lo_min >= INT32_MIN &&
-           P.dk.lo_min + static_cast<int64_t>(P.dk.lo_span) <= INT32_MAX;
+    return star_kind(P, T) == STAR_INNER;
 }
 

@@ -17,11 +17,12 @@
 // table in shared memory; a hash table in HBM.  Keys outside a direct
 // array's range go to the HBM hash table.
 //
-// The star shape (one int32 predicate, a dense int32 join, the key (column,
-// join payload) and [SUM(x*y), COUNT, MIN(x), MAX(x)]) has its own kernel:
-// all columns of the next tile are loaded into registers while the current
-// tile is processed, which keeps about 100 KB of loads in flight per SM from
-// the register file.  (A variant that staged tiles in shared memory with
+// The star shape (one int32 predicate, [SUM(x*y), COUNT, MIN(x), MAX(x)]
+// and a direct group array, with the key (column, join payload) of a dense
+// inner join, or a key of fact columns with a dense semi- / anti-join or no
+// join) has its own kernel: all columns of the next tile are loaded into
+// registers while the current tile is processed, which keeps about 100 KB of
+// loads in flight per SM from the register file.  (A variant that staged tiles in shared memory with
 // bulk TMA copies ran at half this speed: the stages shared the 227 KB with
 // the group table and a stage could only be refilled once every warp had
 // read it.)
@@ -75,7 +76,8 @@ __global__ void __launch_bounds__(PT, 1) k_pipeline(PipeSpec P, TableCfg T)
 // instead of shared memory (SoA).
 // NSUM: the shared-memory direct array keeps SUM as 32-bit halves (small
 // arrays, where many rows hit each slot and 64-bit atomics collide most).
-template <bool GLOBAL, int ITEMS, bool NSUM>
+// JK: the star kind (STAR_INNER, STAR_SEMI, STAR_ANTI, STAR_NONE).
+template <bool GLOBAL, int ITEMS, bool NSUM, int JK>
 __global__ void __launch_bounds__(PT, 1) k_pipeline_star(PipeSpec P, TableCfg T)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -84,7 +86,7 @@ __global__ void __launch_bounds__(PT, 1) k_pipeline_star(PipeSpec P, TableCfg T)
     __syncthreads();
     // grid-stride tiles: at any moment the blocks read neighbouring tiles
     constexpr int64_t TR = static_cast<int64_t>(PT) * ITEMS;
-    star_range<GLOBAL, ITEMS, PT, NSUM>(P, sm, static_cast<int64_t>(blockIdx.x) * TR, P.n, TR * gridDim.x);
+    star_range<GLOBAL, ITEMS, PT, NSUM, JK>(P, sm, static_cast<int64_t>(blockIdx.x) * TR, P.n, TR * gridDim.x);
     __syncthreads();
     if (!GLOBAL) table_flush(P, T, sm, NSUM ? 2 : 1);
 }
@@ -259,6 +261,17 @@ qe_status pipeline_plan(qe_ctx *ctx, PipeSpec &P, const qe_pipeline_desc *d, con
     return QE_OK;
 }
 
+// The star kinds other than the inner join: 3 rows per thread.
+template <int JK>
+qe_status launch_star_kind(qe_ctx *ctx, const PipeSpec &P, const PipePlan &plan, cudaStream_t s)
+{
+    if (plan.T.mode == TM_GLOBAL_DENSE)
+        return launch(ctx, k_pipeline_star<true, 3, false, JK>, P, plan.T, 0, PT * 3, s);
+    if (P.dk.nslots <= STAR_NSUM_SLOTS)
+        return launch(ctx, k_pipeline_star<false, 3, true, JK>, P, plan.T, plan.table, PT * 3, s);
+    return launch(ctx, k_pipeline_star<false, 3, false, JK>, P, plan.T, plan.table, PT * 3, s);
+}
+
 // Bind the HBM tables and launch the fused pass.
 qe_status pipeline_launch(qe_ctx *ctx, PipeSpec &P, const PipePlan &plan, const GroupTableHost &t, int64_t capacity,
                           cudaStream_t s)
@@ -269,20 +282,27 @@ qe_status pipeline_launch(qe_ctx *ctx, PipeSpec &P, const PipePlan &plan, const 
     P.g.capacity = capacity;
     P.g.st = ctx->dstat;
     if (P.n == 0) return QE_OK;
-    if (!ctx->tune_force_generic && star_shape(P, plan.T)) {
+    const int kind = ctx->tune_force_generic ? -1 : star_kind(P, plan.T);
+    if (kind == STAR_SEMI || kind == STAR_ANTI || kind == STAR_NONE) {
+        star_predicate(P);
+        return kind == STAR_SEMI   ? launch_star_kind<STAR_SEMI>(ctx, P, plan, s)
+               : kind == STAR_ANTI ? launch_star_kind<STAR_ANTI>(ctx, P, plan, s)
+                                   : launch_star_kind<STAR_NONE>(ctx, P, plan, s);
+    }
+    if (kind == STAR_INNER) {
         star_predicate(P);
         // rows per thread: 3 by default, 2 when tuned so
         const bool two = ctx->tune_star_items == 2;
         if (plan.T.mode == TM_GLOBAL_DENSE)
-            return two ? launch(ctx, k_pipeline_star<true, 2, false>, P, plan.T, 0, PT * 2, s)
-                       : launch(ctx, k_pipeline_star<true, 3, false>, P, plan.T, 0, PT * 3, s);
+            return two ? launch(ctx, k_pipeline_star<true, 2, false, STAR_INNER>, P, plan.T, 0, PT * 2, s)
+                       : launch(ctx, k_pipeline_star<true, 3, false, STAR_INNER>, P, plan.T, 0, PT * 3, s);
         // SUM in 32-bit halves up to STAR_NSUM_SLOTS slots: measured 2.89 against 4.38 ms for a
         // batch of 300 pipelines of 75 groups, and 2.94 against 2.86 ms for 600M rows into 3,000
         if (P.dk.nslots <= STAR_NSUM_SLOTS)
-            return two ? launch(ctx, k_pipeline_star<false, 2, true>, P, plan.T, plan.table, PT * 2, s)
-                       : launch(ctx, k_pipeline_star<false, 3, true>, P, plan.T, plan.table, PT * 3, s);
-        return two ? launch(ctx, k_pipeline_star<false, 2, false>, P, plan.T, plan.table, PT * 2, s)
-                   : launch(ctx, k_pipeline_star<false, 3, false>, P, plan.T, plan.table, PT * 3, s);
+            return two ? launch(ctx, k_pipeline_star<false, 2, true, STAR_INNER>, P, plan.T, plan.table, PT * 2, s)
+                       : launch(ctx, k_pipeline_star<false, 3, true, STAR_INNER>, P, plan.T, plan.table, PT * 3, s);
+        return two ? launch(ctx, k_pipeline_star<false, 2, false, STAR_INNER>, P, plan.T, plan.table, PT * 2, s)
+                   : launch(ctx, k_pipeline_star<false, 3, false, STAR_INNER>, P, plan.T, plan.table, PT * 3, s);
     }
     return launch(ctx, k_pipeline<2>, P, plan.T, plan.table, PT * 2, s);
 }

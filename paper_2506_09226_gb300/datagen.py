@@ -19,6 +19,9 @@ Column layout of the fact table (21 bytes per row):
     flag  int8   uniform in {0, 1, 2}
 Optional: code int32 (dictionary codes, uniform in [0, n_codes)),
           gkey int64 (drawn from a pool of n_gkeys random 64-bit keys).
+Build sides of the join variants: multi_dim (repeated keys, a fixed number
+of rows per key) and pair_dim (unique pairs of int32 keys), both shaped like
+TPC-H partsupp.
 Dimension table: key int32 = a seeded permutation of 0..n_dim-1,
                  attr int32 uniform in [0, n_attr).
 
@@ -105,6 +108,49 @@ def star_fact(n: int, n_dim: int, *, seed: int, device="cpu", zipf_s: float | No
         idx = _randint(0, n_gkeys - 1, n, torch.int32, g, device)
         cols["gkey"] = pool[idx.long()] if n else torch.empty(0, dtype=torch.int64, device=device)
     return cols
+
+
+def multi_dim(n_keys: int, per_key: int, n_attr: int, *, seed: int, device="cpu") -> dict:
+    """Build side of a many-to-many join, shaped like TPC-H partsupp (a fixed
+    number of supplier rows per part): each key of 0..n_keys-1 sits on exactly
+    per_key rows, the rows in random order; attr int32 uniform in [0, n_attr)."""
+    g = _gen(seed * 1000 + 6, device)
+    n = n_keys * per_key
+    key = torch.randperm(n, generator=g, device=device, dtype=torch.int32) // per_key \
+        if n > 0 else torch.empty(0, dtype=torch.int32, device=device)
+    attr = _randint(0, max(n_attr - 1, 0), n, torch.int32, g, device)
+    return {"key": key, "attr": attr}
+
+
+def pair_dim(n_keys: int, per_key: int, *, seed: int, device="cpu") -> dict:
+    """Build side of a join on two key columns, shaped like TPC-H partsupp
+    keyed on (part, supplier): row (k, j), for k < n_keys and j < per_key, has
+    hi = k and lo = off[k] + j, with off[k] uniform in [0, 2^30), so every
+    pair is unique while both halves repeat; rows in random order; payload
+    int32 uniform.  off is returned for pair_probe_lo."""
+    g = _gen(seed * 1000 + 7, device)
+    n = n_keys * per_key
+    off = _randint(0, (1 << 30) - 1, n_keys, torch.int32, g, device)
+    idx = torch.randperm(n, generator=g, device=device, dtype=torch.int32) \
+        if n > 0 else torch.empty(0, dtype=torch.int32, device=device)
+    hi = idx // per_key
+    lo = off[hi.long()] + idx % per_key if n > 0 else idx
+    del idx
+    pay = _randint(-2 ** 31, 2 ** 31 - 1, n, torch.int32, g, device)
+    return {"hi": hi, "lo": lo, "payload": pay, "off": off}
+
+
+def pair_probe_lo(hi: torch.Tensor, off: torch.Tensor, span: int, *, seed: int) -> torch.Tensor:
+    """Second key column of a pair-key probe whose first column is hi (keys
+    of pair_dim): off[hi] + j with j uniform in [0, span).  With span =
+    per_key + 1, about one row in span has no partner in the build."""
+    g = _gen(seed * 1000 + 8, hi.device)
+    out = torch.empty_like(hi)
+    for s in range(0, hi.numel(), CHUNK):
+        e = min(hi.numel(), s + CHUNK)
+        out[s:e] = off[hi[s:e].long()] + torch.randint(0, span, (e - s,), generator=g, device=hi.device,
+                                                       dtype=torch.int32)
+    return out
 
 
 def key_payload_pairs(n: int, *, seed: int, device="cpu"):

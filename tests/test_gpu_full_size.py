@@ -17,7 +17,15 @@ on the device:
   over 50M dimension keys, group-by on ~40M distinct int64 keys in HBM,
   selectivity 1 % / 50 % / 90 %; group-by on 10^6 dictionary codes):
   every group of 1000 sampled keys against the oracle run over exactly the
-  rows of those keys; the number of groups; sums of COUNT and SUM.
+  rows of those keys; the number of groups; sums of COUNT and SUM;
+* the join variants on the 600M-row fact table, in the launch configuration
+  bench.py times: the semi- / anti-join pipelines and the single-table
+  aggregation group by group against torch reductions over the rows they
+  keep (so semi + anti = single-table as well); the stand-alone semi- and
+  anti-join, the many-to-many join (4 build rows per key, 1.2 billion output
+  pairs) and the pair-key join against their full expected outputs built
+  with torch indexing, and sampled probe positions against the oracle run
+  over the build rows of their keys.
 """
 import numpy as np
 import pytest
@@ -229,3 +237,130 @@ def test_skew_pipeline_dictionary_codes(ctx, skew):
     assert got.total(1) == rows
     assert got.total(0) == s
     _check_sampled_groups(fact, dim, got, "code", None, [O.Pred(5, O.LT, k)], np.random.default_rng(5))
+
+
+# ---------------------------------------------------------------- join variants at scale
+@pytest.fixture(scope="module")
+def star600():
+    dev = torch.device("cuda", 0)
+    dim = datagen.star_dim(20_000_000, 1000, seed=1, device=dev)
+    fact = datagen.star_fact(600_000_000, 20_000_000, seed=1, device=dev)
+    half = dim["key"][: 10_000_000].contiguous()
+    member = torch.zeros(20_000_000, dtype=torch.bool, device=dev)
+    member[half.long()] = True
+    yield fact, dim, half, member
+    del fact, dim, half, member
+    torch.cuda.empty_cache()
+
+
+def test_semi_anti_single_table_600M(ctx, star600):
+    """Filter + semi- / anti-join against half the dimension's keys + group-by
+    flag, and the same filter + group-by with no join: every group's four
+    aggregates against torch reductions over exactly the rows kept."""
+    fact, dim, half, member = star600
+    cols = [fact[c] for c in COLS]
+    got = {}
+    for name, kind in (("semi", qe.SEMI), ("anti", qe.ANTI)):
+        d = qe.pipeline_desc(cols, [(1, qe.LT, DATE_LT)], fk_col=0, dim_key=half, key_hi_col=-1, key_lo_col=4,
+                             aggs=STAR_AGGS, expected_groups=3, est_selectivity=DATE_LT / 2557,
+                             key_range=(None, (0, 2)), join_kind=kind)
+        got[name] = _Groups(qe.qe_pipeline(ctx, d, 64))
+    d = qe.pipeline_desc(cols[1:], [(0, qe.LT, DATE_LT)], key_hi_col=-1, key_lo_col=3,
+                         aggs=[(qe.SUM, 1, 2), (qe.COUNT, -1, -1), (qe.MIN, 1, -1), (qe.MAX, 1, -1)],
+                         expected_groups=3, est_selectivity=DATE_LT / 2557, key_range=(None, (0, 2)))
+    got["single"] = _Groups(qe.qe_pipeline(ctx, d, 64))
+    keep = fact["date"] < DATE_LT
+    inset = member[fact["fk"].long()]
+    masks = {"single": keep, "semi": keep & inset, "anti": keep & ~inset}
+    for name, m in masks.items():
+        assert got[name].keys.tolist() == [0, 1, 2], name
+        for f in range(3):
+            ref = _filtered_totals(fact, m & (fact["flag"] == f))
+            g = got[name][f]
+            assert (g[1], g[0], g[2], g[3]) == ref, (name, f)
+    for f in range(3):
+        a, b, c = got["semi"][f], got["anti"][f], got["single"][f]
+        assert a[0] + b[0] == c[0] and a[1] + b[1] == c[1]
+        assert min(a[2], b[2]) == c[2] and max(a[3], b[3]) == c[3]
+
+
+def test_semi_multi_pair_joins_600M(ctx, star600):
+    """The stand-alone joins over the filter's 300M-position selection vector,
+    each against its complete expected output, and sampled positions of the
+    many-to-many and pair-key joins against the oracle."""
+    fact, dim, half, member = star600
+    dev = fact["fk"].device
+    n, nd = fact["fk"].numel(), 20_000_000
+    sel = torch.empty(n, dtype=torch.int32, device=dev)
+    cnt = torch.empty(1, dtype=torch.int64, device=dev)
+    qe.qe_filter(ctx, [fact["date"]], [(0, qe.LT, DATE_LT)], sel, cnt)
+    nsel = int(cnt.item())
+    sel = sel[:nsel]
+    assert torch.equal(sel, torch.nonzero(fact["date"] < DATE_LT).flatten().to(torch.int32))
+    fks = fact["fk"][sel.long()]
+    rng = np.random.default_rng(29)
+    sample = np.sort(rng.choice(nsel, 1000, replace=False))
+
+    # semi- and anti-join: the selected positions whose key is (not) in the set, in order
+    hs = qe.qe_join_build_set(ctx, half)
+    inset = member[fks.long()]
+    for anti, want in ((False, sel[inset]), (True, sel[~inset])):
+        rows, c = qe.qe_join_semi(ctx, hs, fact["fk"], sel, n=nsel, anti=anti, capacity=nsel)
+        assert int(c.item()) == want.numel()
+        assert torch.equal(rows[: want.numel()], want)
+    hs.destroy()
+    del inset
+
+    # many-to-many: every position meets the 4 build rows of its key
+    md = datagen.multi_dim(nd, 4, 1000, seed=4, device=dev)
+    hm = qe.qe_join_build_multi(ctx, md["key"], md["attr"])
+    rows, pay, c = qe.qe_join_probe_multi(ctx, hm, fact["fk"], sel, n=nsel, capacity=4 * nsel + 1)
+    assert int(c.item()) == 4 * nsel
+    assert torch.equal(rows[: 4 * nsel], sel.repeat_interleave(4))
+    o1 = torch.argsort(md["attr"], stable=True)
+    o2 = torch.argsort(md["key"][o1], stable=True)
+    by_key = md["attr"][o1][o2].view(nd, 4)
+    del o1, o2
+    got = pay[: 4 * nsel].view(nsel, 4).sort(dim=1).values
+    assert torch.equal(got, by_key[fks.long()])
+    del got, by_key
+    # sampled positions against the oracle, over the build rows of their keys
+    ts = torch.from_numpy(sample).to(dev)
+    pk = fks[ts]
+    brows = torch.isin(md["key"], pk)
+    rr, rp = O.join_multi(md["key"][brows].cpu().numpy(), md["attr"][brows].cpu().numpy(), pk.cpu().numpy())
+    assert np.array_equal(rr, np.repeat(np.arange(len(sample), dtype=np.int32), 4))
+    idx = torch.from_numpy(np.repeat(sample * 4, 4) + np.tile(np.arange(4), len(sample))).to(dev)
+    assert np.array_equal(rows[idx].cpu().numpy(), np.repeat(sel[ts].cpu().numpy(), 4))
+    gp = pay[idx].cpu().numpy()
+    assert np.array_equal(np.sort(gp.reshape(-1, 4), axis=1), np.sort(rp.reshape(-1, 4), axis=1))
+    hm.destroy()
+    del md, rows, pay
+
+    # pair keys: a position matches iff its second key is one of its first key's 4 partners
+    pd = datagen.pair_dim(nd, 4, seed=5, device=dev)
+    plo = datagen.pair_probe_lo(fact["fk"], pd["off"], 5, seed=5)
+    hp = qe.qe_join_build_pair(ctx, pd["hi"], pd["lo"], pd["payload"])
+    rows, pay, c = qe.qe_join_probe_pair(ctx, hp, fact["fk"], plo, sel, n=nsel, capacity=nsel)
+    j = plo[sel.long()] - pd["off"][fks.long()]
+    hit = j < 4
+    by_pair = torch.empty(4 * nd, dtype=torch.int32, device=dev)
+    by_pair[pd["hi"].long() * 4 + (pd["lo"] - pd["off"][pd["hi"].long()]).long()] = pd["payload"]
+    k = int(hit.sum().item())
+    assert int(c.item()) == k
+    assert torch.equal(rows[:k], sel[hit])
+    assert torch.equal(pay[:k], by_pair[fks[hit].long() * 4 + j[hit].long()])
+    del by_pair, j, hit
+    # sampled positions against the oracle, over the build rows of their first keys
+    pos = sel[torch.from_numpy(sample).to(dev)]
+    ph, pl = fact["fk"][pos.long()], plo[pos.long()]
+    brows = torch.isin(pd["hi"], ph)
+    rr, rp = O.join_pair(pd["hi"][brows].cpu().numpy(), pd["lo"][brows].cpu().numpy(),
+                         pd["payload"][brows].cpu().numpy(), ph.cpu().numpy(), pl.cpu().numpy())
+    assert 700 < len(rr) < 900
+    at = torch.searchsorted(rows[:k], pos)
+    found = (at < k) & (rows[:k][at.clamp(max=k - 1)] == pos)
+    f = found.cpu().numpy()
+    assert np.array_equal(np.nonzero(f)[0].astype(np.int32), rr)
+    assert np.array_equal(pay[:k][at[found]].cpu().numpy(), rp)
+    hp.destroy()

@@ -434,6 +434,22 @@ def test_pipeline_without_join_and_misses(ctx):
     assert_groups_equal(g, ref)
 
 
+@pytest.mark.parametrize("n", [1, 4097, 1_000_003])
+def test_single_table_aggregation(ctx, n):
+    """Filter + group-by with no join over the fact columns (a Q1-shaped
+    query: SUM(price * qty), COUNT, MIN, MAX per flag), with the flag's range
+    given as a column statistic, against the oracle."""
+    fact = datagen.star_fact(n, 1000, seed=n % 89)
+    f = [fact[c].cuda() for c in COLS[1:]]
+    aggs = [(qe.SUM, 1, 2), (qe.COUNT, -1, -1), (qe.MIN, 1, -1), (qe.MAX, 1, -1)]
+    d = qe.pipeline_desc(f, [(0, qe.LT, 1278)], key_hi_col=-1, key_lo_col=3, aggs=aggs, expected_groups=3,
+                         est_selectivity=0.5, key_range=(None, (0, 2)))
+    g = qe.qe_pipeline(ctx, d, 64)
+    q = O.Query(preds=[O.Pred(0, O.LT, 1278)], fk_col=-1, key_hi_col=-1, key_lo_col=3,
+                aggs=[(O.SUM, 1, 2), (O.COUNT, -1, -1), (O.MIN, 1, -1), (O.MAX, 1, -1)])
+    assert_groups_equal(g, O.pipeline([fact[c].numpy() for c in COLS[1:]], q))
+
+
 # ---------------------------------------------------------------- dense group layouts
 def run_star_hint(ctx, fact, dim, key_range, capacity, date_lt=1278, expected=0):
     f = [fact[c].cuda() for c in COLS]

@@ -155,6 +155,66 @@ def test_pipeline_semi_anti(ctx, kind, layout):
 
 
 @pytest.mark.parametrize("kind", [qe.SEMI, qe.ANTI])
+def test_pipeline_semi_anti_flag_groups(ctx, kind):
+    """The shape bench.py times: a key set of half of a permuted key range,
+    the flag's range given as a column statistic, three groups."""
+    fact = datagen.star_fact(1_000_003, 200_000, seed=80 + kind)
+    dk = datagen.star_dim(200_000, 1, seed=80 + kind)["key"][:100_000].numpy()
+    f = [fact[c].cuda() for c in COLS]
+    d = qe.pipeline_desc(f, [(1, qe.LT, 1278)], fk_col=0, dim_key=cuda(dk), key_hi_col=-1, key_lo_col=4,
+                         aggs=AGGS, expected_groups=3, est_selectivity=0.5, key_range=(None, (0, 2)),
+                         join_kind=kind)
+    g = qe.qe_pipeline(ctx, d, 64)
+    ref = _oracle(fact, dk, kind)
+    assert len(ref["keys"]) == 3
+    _assert_groups(g, ref)
+
+
+# Group keys of the star kinds without a join payload: (key_hi, key_lo, key
+# range) -- int8 flag alone (3 slots); (flag, int32 qty) (150 slots); the
+# int32 foreign key over 5,000 values (shared-memory array past the 32-bit
+# SUM halves) and over 60,000 values (array in HBM); a range that leaves
+# flag 2 out (those rows go to the HBM hash table).
+STAR_KEYS = {
+    "flag": (-1, 4, (None, (0, 2)), 5_000),
+    "flag_qty": (4, 3, ((0, 2), (1, 50)), 5_000),
+    "fk_5000": (-1, 0, (None, (0, 4_999)), 5_000),
+    "fk_60000": (-1, 0, (None, (0, 59_999)), 60_000),
+    "flag_spill": (-1, 4, (None, (0, 1)), 5_000),
+}
+
+
+@pytest.mark.parametrize("kind", [qe.SEMI, qe.ANTI, "none"])
+@pytest.mark.parametrize("shape", list(STAR_KEYS))
+def test_pipeline_star_kinds(ctx, kind, shape):
+    """The star kernel for semi- / anti-joins and for no join, against the
+    oracle and against the generic kernel, on 1M rows (several tiles per
+    block and a ragged tail) whose foreign keys partly fall outside the key
+    set's range."""
+    hi, lo, rng_, span = STAR_KEYS[shape]
+    seed = 90 + len(shape) + (3 if kind == "none" else kind)
+    fact = datagen.star_fact(1_000_003, span, seed=seed)
+    # keys below span/10 or from 9 span/10 up lie outside the key set's range
+    dk = np.random.default_rng(seed).integers(span // 10, span - span // 10, span // 2).astype(np.int32)
+    f = [fact[c].cuda() for c in COLS]
+    join = kind != "none"
+    d = qe.pipeline_desc(f, [(1, qe.LT, 1278)], fk_col=0 if join else -1, dim_key=cuda(dk) if join else None,
+                         key_hi_col=hi, key_lo_col=lo, aggs=AGGS, key_range=rng_,
+                         join_kind=kind if join else qe.INNER)
+    q = O.Query(preds=[O.Pred(1, O.LT, 1278)], fk_col=0 if join else -1, key_hi_col=hi, key_lo_col=lo, aggs=O_AGGS,
+                join_kind=kind if join else O.INNER)
+    ref = O.pipeline([fact[c].numpy() for c in COLS], q, dk if join else None, None)
+    if join:
+        assert 0 < ref["njoin"] < ref["nsel"]
+    _assert_groups(qe.qe_pipeline(ctx, d, 70_000), ref)
+    ctx.set_tuning("force_generic", 1)
+    try:
+        _assert_groups(qe.qe_pipeline(ctx, d, 70_000), ref)
+    finally:
+        ctx.set_tuning("force_generic", 0)
+
+
+@pytest.mark.parametrize("kind", [qe.SEMI, qe.ANTI])
 def test_pipeline_semi_anti_prebuilt_set(ctx, kind):
     fact, dk = _semi_case(70 + kind, 100_000, 5_000, 20_000)
     ht = qe.qe_join_build_set(ctx, cuda(dk))
