@@ -321,7 +321,8 @@ qe_status qe_join_semi(qe_ctx *ctx, const qe_hash_table *ht, const int32_t *prob
  * the order of payloads inside a run is unspecified.  Layout and opts as for
  * qe_join_build (AUTO: dense when the key range is at most 4x the row count).
  * Memory: dense 12 bytes per key-range slot, open 20 bytes per slot (slots =
- * the power of two >= 2 x rows), plus 4 bytes per row.  The open layout
+ * the power of two >= 2 x rows), plus 4 bytes per row; a probe reads one
+ * 8-byte word (run start and length) per key.  The open layout
  * reserves INT32_MIN (QE_ERR_RESERVED_KEY).  A multimap serves only
  * qe_join_probe_multi (the other probes and the pipelines return
  * QE_ERR_INVALID_ARG for it). */
@@ -335,8 +336,10 @@ qe_status qe_join_build_multi(qe_ctx *ctx, const int32_t *keys, const int32_t *p
  *   out_probe_row, out_build_payload: device int32 [capacity];
  *   *out_count (device int64): the number of outputs; past the capacity
  *   nothing is written and QE_ERR_CAPACITY is recorded with that number.
- * Two passes (count every position's matches per segment of 256 positions,
- * scan, look up again and write), with scratch of 16 bytes per segment. */
+ * Two passes: the first looks every position up once, keeps its run (start,
+ * length) and counts matches per segment of 256 positions; after a scan the
+ * second writes the runs, a warp's outputs as consecutive stores.  Scratch:
+ * 8 bytes per position plus 16 per segment. */
 qe_status qe_join_probe_multi(qe_ctx *ctx, const qe_hash_table *ht, const int32_t *probe_keys,
                               const int32_t *sel, int64_t n, int32_t *out_probe_row,
                               int32_t *out_build_payload, int64_t capacity, int64_t *out_count,
@@ -345,8 +348,9 @@ qe_status qe_join_probe_multi(qe_ctx *ctx, const qe_hash_table *ht, const int32_
 /* Join on a pair of int32 key columns: the composite keys of joins such as a
  * (part, supplier) pair in the TPC-H queries the paper runs (Sec. 6.1),
  * joined locally as in Sec. 2.2.  The pair is packed as (uint32)hi << 32 |
- * (uint32)lo into an open-addressing table (load factor <= 0.5, 12 bytes
- * per slot); (INT32_MIN, INT32_MIN) is the empty-slot marker and records
+ * (uint32)lo into an open-addressing table (load factor <= 0.5, 16-byte
+ * slots holding key and payload); (INT32_MIN, INT32_MIN) is the empty-slot
+ * marker and records
  * QE_ERR_RESERVED_KEY.  Build pairs must be unique (QE_ERR_DUPLICATE_KEY).
  * The probe matches row r = sel ? sel[i] : i on (probe_hi[r], probe_lo[r])
  * and writes (r, payload) in ascending position order, as qe_join_probe

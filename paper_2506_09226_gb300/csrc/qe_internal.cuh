@@ -625,7 +625,7 @@ struct qe_hash_table {
     int32_t set = 0;                  // key set: membership only, keys may repeat
     int32_t multi = 0;                // multimap (qe_join_build_multi): payload = the runs of values
     int32_t pair = 0;                 // pair keys (qe_join_build_pair): open = packed keys, payload per slot
-    int64_t *mstart = nullptr;        // multimap: start of each key's run (per dense slot / open slot)
+    int64_t *mstart = nullptr;        // multimap: each key's run (per dense slot / open slot), start << 32 | length
     uint32_t *mcnt = nullptr;         // multimap: rows of each key
 };
 

@@ -236,14 +236,15 @@ struct SemiOp {
 // ---------------------------------------------------------------- pair keys
 // A pair of int32 key columns packed as (uint32)hi << 32 | (uint32)lo; the
 // packed (INT32_MIN, INT32_MIN) is the empty slot (HT_EMPTY_SLOT).  Open
-// addressing over packed keys, with the payload in a parallel array.
+// addressing over 16-byte slots {packed key, payload, unused}: a probe that
+// finds its key has the payload in the same DRAM sector.
 __device__ __forceinline__ unsigned long long pair_key(int32_t hi, int32_t lo)
 {
     return (static_cast<unsigned long long>(static_cast<uint32_t>(hi)) << 32) | static_cast<uint32_t>(lo);
 }
 
 __global__ void __launch_bounds__(256) k_build_pair(const int32_t *khi, const int32_t *klo, const int32_t *pay,
-                                                    int64_t n, unsigned long long *keys, int32_t *vals, uint32_t mask,
+                                                    int64_t n, unsigned long long *slots, uint32_t mask,
                                                     qe_dev_status *st)
 {
     for (int64_t i = blockIdx.x * 256ll + threadIdx.x; i < n; i += static_cast<int64_t>(gridDim.x) * 256) {
@@ -255,9 +256,9 @@ __global__ void __launch_bounds__(256) k_build_pair(const int32_t *khi, const in
         uint32_t h = static_cast<uint32_t>(dev_fmix64(k)) & mask;
         bool done = false;
         for (uint32_t probes = 0; probes <= mask && !done; probes++) {
-            const unsigned long long old = atomicCAS(keys + h, HT_EMPTY_SLOT, k);
+            const unsigned long long old = atomicCAS(slots + 2 * static_cast<uint64_t>(h), HT_EMPTY_SLOT, k);
             if (old == HT_EMPTY_SLOT) {
-                vals[h] = __ldcs(pay + i);
+                reinterpret_cast<int32_t *>(slots + 2 * static_cast<uint64_t>(h) + 1)[0] = __ldcs(pay + i);
                 done = true;
             } else if (old == k) {
                 dev_report(st, QE_ERR_DUPLICATE_KEY, 0);
@@ -271,8 +272,7 @@ __global__ void __launch_bounds__(256) k_build_pair(const int32_t *khi, const in
 }
 
 struct PairView {
-    const unsigned long long *keys;
-    const int32_t *vals;
+    const unsigned long long *slots;   // 2 words per slot: key, payload (low half)
     uint32_t mask;
 };
 
@@ -280,12 +280,12 @@ __device__ __forceinline__ bool pair_lookup(const PairView &v, unsigned long lon
 {
     uint32_t h = static_cast<uint32_t>(dev_fmix64(k)) & v.mask;
     for (uint32_t probes = 0; probes <= v.mask; probes++) {
-        const unsigned long long w = __ldg(v.keys + h);
-        if (w == k) {
-            pay = __ldg(v.vals + h);
+        const ulonglong2 w = __ldg(reinterpret_cast<const ulonglong2 *>(v.slots) + h);
+        if (w.x == k) {
+            pay = static_cast<int32_t>(static_cast<uint32_t>(w.y));
             return true;
         }
-        if (w == HT_EMPTY_SLOT) return false;
+        if (w.x == HT_EMPTY_SLOT) return false;
         h = (h + 1) & v.mask;
     }
     return false;
@@ -491,22 +491,22 @@ extern "C" qe_status qe_join_build_pair(qe_ctx *ctx, const int32_t *key_hi, cons
     ht->pair = 1;
     ht->nkeys = nrows;
     ht->slots = static_cast<int64_t>(slots);
-    const size_t kbytes = slots * 8;
-    ht->bytes = kbytes + slots * 4;
+    ht->bytes = slots * 16;
     qe_status st = qe_alloc(ctx, &ht->mem, ht->bytes, s);
     if (st != QE_OK) {
         delete ht;
         return st;
     }
     ht->open = static_cast<unsigned long long *>(ht->mem);
-    ht->payload = reinterpret_cast<int32_t *>(static_cast<char *>(ht->mem) + kbytes);
-    k_fill_u64<<<grid_for(ctx, static_cast<int64_t>(slots)), 256, 0, s>>>(ht->open, static_cast<int64_t>(slots),
-                                                                           HT_EMPTY_SLOT);
+    // every word to the empty marker: the key words mark empty slots, the
+    // payload words are written before any probe reads them
+    const int64_t words = static_cast<int64_t>(2 * slots);
+    k_fill_u64<<<grid_for(ctx, words), 256, 0, s>>>(ht->open, words, HT_EMPTY_SLOT);
     QE_LAUNCHED(ctx);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && nrows > 0) {
         ProfScope prof(ctx, "build", s);
-        k_build_pair<<<grid_for(ctx, nrows), 256, 0, s>>>(key_hi, key_lo, payload, nrows, ht->open, ht->payload,
+        k_build_pair<<<grid_for(ctx, nrows), 256, 0, s>>>(key_hi, key_lo, payload, nrows, ht->open,
                                                           static_cast<uint32_t>(slots - 1), ctx->dstat);
         QE_LAUNCHED(ctx);
         e = cudaGetLastError();
@@ -531,8 +531,7 @@ extern "C" qe_status qe_join_probe_pair(qe_ctx *ctx, const qe_hash_table *ht, co
     if (!ht->pair) return qe_fail(ctx, QE_ERR_INVALID_ARG, "probe pair: needs a table from qe_join_build_pair");
     cudaSetDevice(ctx->device);
     PairProbeOp op{};
-    op.ht.keys = ht->open;
-    op.ht.vals = ht->payload;
+    op.ht.slots = ht->open;
     op.ht.mask = static_cast<uint32_t>(ht->slots - 1);
     op.khi = probe_hi;
     op.klo = probe_lo;

@@ -27,8 +27,7 @@ struct MmView {
     int32_t key_min;
     uint32_t range;                  // dense
     uint32_t mask;                   // open: slots - 1
-    const int64_t *start;
-    const uint32_t *cnt;
+    const unsigned long long *run;   // per slot: start of the run << 32 | its length
     const int32_t *vals;
     const unsigned long long *slots;
 };
@@ -40,8 +39,7 @@ MmView mm_view(const qe_hash_table *ht)
     v.key_min = ht->key_min;
     v.range = ht->layout == QE_HT_DENSE ? static_cast<uint32_t>(ht->slots) : 0;
     v.mask = ht->layout == QE_HT_OPEN ? static_cast<uint32_t>(ht->slots - 1) : 0;
-    v.start = ht->mstart;
-    v.cnt = ht->mcnt;
+    v.run = reinterpret_cast<const unsigned long long *>(ht->mstart);
     v.vals = ht->payload;
     v.slots = ht->open;
     return v;
@@ -60,8 +58,8 @@ __device__ __forceinline__ int64_t mm_open_find(const unsigned long long *slots,
     return -1;
 }
 
-// Matches of `key`: their number, and the start of their run in vals.
-__device__ __forceinline__ uint32_t mm_lookup(const MmView &v, int32_t key, int64_t &beg)
+// The run of `key` (start << 32 | number of matches), 0 when it has none.
+__device__ __forceinline__ unsigned long long mm_run(const MmView &v, int32_t key)
 {
     int64_t s;
     if (v.layout == QE_HT_DENSE) {
@@ -72,9 +70,7 @@ __device__ __forceinline__ uint32_t mm_lookup(const MmView &v, int32_t key, int6
         s = mm_open_find(v.slots, v.mask, key);
         if (s < 0) return 0;
     }
-    const uint32_t c = __ldg(v.cnt + s);
-    beg = c ? __ldg(v.start + s) : 0;
-    return c;
+    return __ldg(v.run + s);
 }
 
 // ---------------------------------------------------------------- build
@@ -156,6 +152,14 @@ __global__ void __launch_bounds__(256) k_mm_fill_open(const int32_t *keys, const
         if (s < 0) continue;                     // only after a reported capacity error
         vals[start[s] + atomicAdd(cur + s, 1u)] = __ldcs(pay + i);
     }
+}
+
+// After the fill: each slot's run as one word, start << 32 | length (both
+// below 2^31), so that a probe reads one word per key.
+__global__ void __launch_bounds__(256) k_mm_pack_runs(int64_t *start, const uint32_t *cnt, int64_t n)
+{
+    for (int64_t s = blockIdx.x * 256ll + threadIdx.x; s < n; s += static_cast<int64_t>(gridDim.x) * 256)
+        start[s] = static_cast<int64_t>((static_cast<unsigned long long>(start[s]) << 32) | cnt[s]);
 }
 
 // ---------------------------------------------------------------- scans
@@ -242,8 +246,10 @@ qe_status mm_scan(qe_ctx *ctx, const uint32_t *cnt, int64_t n, int64_t *start, i
 
 // ---------------------------------------------------------------- probe
 // Matches of the segment's positions, totalled per segment (one warp each).
+// Each position's run word is kept in runs[pos] for the write pass, which
+// then reads it in order instead of repeating the random lookups.
 __global__ void __launch_bounds__(256) k_mm_probe_count(MmView v, const int32_t *keys, const int32_t *sel, int64_t n,
-                                                        int64_t nseg, int64_t *seg_tot)
+                                                        int64_t nseg, int64_t *seg_tot, unsigned long long *runs)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warps = static_cast<int64_t>(gridDim.x) * 8;
@@ -254,8 +260,9 @@ __global__ void __launch_bounds__(256) k_mm_probe_count(MmView v, const int32_t 
             const int64_t pos = seg * MM_SEG + k * 32 + lane;
             if (pos < n) {
                 const int32_t row = sel ? __ldcs(sel + pos) : static_cast<int32_t>(pos);
-                int64_t beg;
-                tot += mm_lookup(v, __ldg(keys + row), beg);
+                const unsigned long long w = mm_run(v, __ldg(keys + row));
+                runs[pos] = w;
+                tot += static_cast<uint32_t>(w);
             }
         }
         tot = warp_incl_scan(tot);
@@ -264,10 +271,15 @@ __global__ void __launch_bounds__(256) k_mm_probe_count(MmView v, const int32_t 
 }
 
 // Each position's run, written at its offset: segment start, then the
-// matches of the segment's earlier positions (in position order).
-__global__ void __launch_bounds__(256) k_mm_probe_write(MmView v, const int32_t *keys, const int32_t *sel, int64_t n,
-                                                        int64_t nseg, const int64_t *loc, const int64_t *bsum,
-                                                        int32_t *out_row, int32_t *out_pay, int64_t capacity)
+// matches of the segment's earlier positions (in position order).  The
+// warp writes the runs of its 32 positions together, 32 consecutive outputs
+// per step: output j of the step belongs to the first lane whose inclusive
+// match count exceeds j (a binary search over the lanes' counts), so every
+// store is a coalesced warp store whatever the run lengths.
+__global__ void __launch_bounds__(256) k_mm_probe_write(MmView v, const int32_t *sel, int64_t n, int64_t nseg,
+                                                        const unsigned long long *runs, const int64_t *loc,
+                                                        const int64_t *bsum, int32_t *out_row, int32_t *out_pay,
+                                                        int64_t capacity)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warps = static_cast<int64_t>(gridDim.x) * 8;
@@ -281,16 +293,29 @@ __global__ void __launch_bounds__(256) k_mm_probe_write(MmView v, const int32_t 
             uint32_t c = 0;
             int64_t beg = 0;
             if (pos < n) {
+                const unsigned long long w = __ldcs(runs + pos);
+                c = static_cast<uint32_t>(w);
+                beg = static_cast<int64_t>(w >> 32);
                 row = sel ? __ldcs(sel + pos) : static_cast<int32_t>(pos);
-                c = mm_lookup(v, __ldg(keys + row), beg);
             }
             const int64_t inc = warp_incl_scan(static_cast<int64_t>(c));
-            const int64_t my = o + inc - c;
-            for (uint32_t t = 0; t < c && my + t < capacity; t++) {
-                __stcs(out_row + my + t, row);
-                __stcs(out_pay + my + t, __ldg(v.vals + beg + t));
+            const int64_t total = __shfl_sync(QE_FULL_MASK, inc, 31);
+            for (int64_t base = 0; base < total; base += 32) {
+                const int64_t j = base + lane;
+                int owner = 0;   // lanes whose inclusive count is <= j (at most 31 for j < total)
+#pragma unroll
+                for (int b = 16; b >= 1; b >>= 1)
+                    if (__shfl_sync(QE_FULL_MASK, inc, owner + b - 1) <= j) owner += b;
+                const int64_t end = __shfl_sync(QE_FULL_MASK, inc, owner);
+                const uint32_t cnt = __shfl_sync(QE_FULL_MASK, c, owner);
+                const int32_t r = __shfl_sync(QE_FULL_MASK, row, owner);
+                const int64_t b0 = __shfl_sync(QE_FULL_MASK, beg, owner);
+                if (j < total && o + j < capacity) {
+                    __stcs(out_row + o + j, r);
+                    __stcs(out_pay + o + j, __ldg(v.vals + b0 + (j - (end - cnt))));
+                }
             }
-            o += __shfl_sync(QE_FULL_MASK, inc, 31);
+            o += total;
         }
     }
 }
@@ -402,6 +427,13 @@ extern "C" qe_status qe_join_build_multi(qe_ctx *ctx, const int32_t *keys, const
         QE_LAUNCHED(ctx);
         e = cudaGetLastError();
     }
+    // 4. each run as one word (start, length): with no rows the lengths are the zeros set above
+    if (e == cudaSuccess && st == QE_OK) {
+        k_mm_pack_runs<<<grid_of(ctx, static_cast<int64_t>(nslots)), 256, 0, s>>>(ht->mstart, ht->mcnt,
+                                                                                   static_cast<int64_t>(nslots));
+        QE_LAUNCHED(ctx);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess || st != QE_OK) {
         qe_free(ctx, ht->mem, s);
         delete ht;
@@ -430,25 +462,28 @@ extern "C" qe_status qe_join_probe_multi(qe_ctx *ctx, const qe_hash_table *ht, c
     const MmView v = mm_view(ht);
     const int64_t nseg = qe_ceil_div(n, MM_SEG), nb = qe_ceil_div(nseg, TP_SCAN_B);
     auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
-    const size_t b_seg = up(static_cast<size_t>(nseg) * 8);
+    const size_t b_seg = up(static_cast<size_t>(nseg) * 8), b_bs = up(static_cast<size_t>(nb) * 8);
     void *scratch = nullptr;
-    qe_status st = qe_alloc(ctx, &scratch, 2 * b_seg + up(static_cast<size_t>(nb) * 8), s);
+    // segment totals and offsets, block sums, and one run word per position
+    qe_status st = qe_alloc(ctx, &scratch, 2 * b_seg + b_bs + static_cast<size_t>(n) * 8, s);
     if (st != QE_OK) return st;
-    int64_t *seg_tot = static_cast<int64_t *>(scratch);
-    int64_t *loc = reinterpret_cast<int64_t *>(static_cast<unsigned char *>(scratch) + b_seg);
-    int64_t *bsum = reinterpret_cast<int64_t *>(static_cast<unsigned char *>(scratch) + 2 * b_seg);
+    unsigned char *p = static_cast<unsigned char *>(scratch);
+    int64_t *seg_tot = reinterpret_cast<int64_t *>(p);
+    int64_t *loc = reinterpret_cast<int64_t *>(p + b_seg);
+    int64_t *bsum = reinterpret_cast<int64_t *>(p + 2 * b_seg);
+    unsigned long long *runs = reinterpret_cast<unsigned long long *>(p + 2 * b_seg + b_bs);
     int64_t g = qe_ceil_div(nseg, 8);
     if (g > static_cast<int64_t>(ctx->num_sms) * 8) g = static_cast<int64_t>(ctx->num_sms) * 8;
     {
         ProfScope prof(ctx, "probe", s);
-        k_mm_probe_count<<<static_cast<unsigned>(g), 256, 0, s>>>(v, probe_keys, sel, n, nseg, seg_tot);
+        k_mm_probe_count<<<static_cast<unsigned>(g), 256, 0, s>>>(v, probe_keys, sel, n, nseg, seg_tot, runs);
         QE_LAUNCHED(ctx);
         k_mm_scan_local_i64<<<static_cast<unsigned>(nb), 1024, 0, s>>>(seg_tot, loc, nseg, bsum);
         QE_LAUNCHED(ctx);
         k_tp_scan_top<<<1, 1024, 0, s>>>(bsum, static_cast<int>(nb), out_count, capacity, ctx->dstat);
         QE_LAUNCHED(ctx);
-        k_mm_probe_write<<<static_cast<unsigned>(g), 256, 0, s>>>(v, probe_keys, sel, n, nseg, loc, bsum,
-                                                                  out_probe_row, out_build_payload, capacity);
+        k_mm_probe_write<<<static_cast<unsigned>(g), 256, 0, s>>>(v, sel, n, nseg, runs, loc, bsum, out_probe_row,
+                                                                  out_build_payload, capacity);
         QE_LAUNCHED(ctx);
     }
     const cudaError_t e = cudaGetLastError();

@@ -171,7 +171,8 @@ def test_join_pair(ctx, n_probe, with_sel):
     plo = (rng.integers(0, 1_000, n_probe) * 7 - 3_000).astype(np.int32)
     sel = np.sort(rng.choice(n_probe, n_probe // 2 + 1, replace=False)).astype(np.int32) if with_sel else None
     ht = qe.qe_join_build_pair(ctx, cuda(bhi), cuda(blo), cuda(bp))
-    assert ht.info().key_set == 3
+    info = ht.info()
+    assert info.key_set == 3 and info.bytes == info.slots * 16        # {key, payload} slots
     rows, pay, cnt = qe.qe_join_probe_pair(ctx, ht, cuda(phi), cuda(plo), cuda(sel) if with_sel else None)
     rr, rp = O.join_pair(bhi, blo, bp, phi, plo, sel)
     c = int(cnt.item())
