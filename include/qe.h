@@ -281,9 +281,11 @@ qe_status qe_join_build(qe_ctx *ctx, const int32_t *keys, const int32_t *payload
  *   out_probe_row, out_build_payload: device int32 [capacity];
  *   *out_count (device int64): number of matches; past the capacity nothing
  *   is written and QE_ERR_CAPACITY is recorded.
- * From 4M positions on the probe runs in two passes (count per 256-position
- * segment, then write; every lookup is made twice), with scratch of about 8
- * bytes per 256 positions from the context's budget. */
+ * From 4M positions on the probe runs in two passes: the first looks every
+ * position up once, counts matches per 256-position segment and keeps each
+ * match's payload and every segment's match masks; the second writes them.
+ * Scratch from the context's budget: about 4.2 bytes per position (0.2 for
+ * qe_join_semi, which keeps the masks only). */
 qe_status qe_join_probe(qe_ctx *ctx, const qe_hash_table *ht, const int32_t *probe_keys,
                         const int32_t *sel, int64_t n, int32_t *out_probe_row,
                         int32_t *out_build_payload, int64_t capacity, int64_t *out_count,

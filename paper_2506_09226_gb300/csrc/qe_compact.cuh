@@ -195,14 +195,18 @@ qe_status launch_compact(qe_ctx *ctx, const char *name, int64_t n, int64_t capac
 // blocks (so as many tiles are in flight as occupancy allows; the price is
 // evaluating every row twice).  A warp segment is 32 lanes x ITEMS rows in
 // the tile order above (item k of lane l is position seg*32*ITEMS + 32k + l).
-// Pass 1 counts each segment's survivors; a two-level scan turns the counts
-// into offsets (blocks of TP_SCAN_B counts, then at most 4 * 1024 block
-// totals); pass 2 re-evaluates each segment and writes its survivors item by
-// item at the segment's offset.
+// Pass 1 counts each segment's survivors and keeps what pass 2 needs: the
+// survivor ballot of every item and, for ops with a payload (Op::kPay), each
+// survivor's payload word; a two-level scan turns the counts into offsets
+// (blocks of TP_SCAN_B counts, then at most 4 * 1024 block totals); pass 2
+// reads the selection rows again, restores the survivors from the kept
+// ballots and words (no second key gather or table lookup) and writes them
+// item by item at the segment's offset.
 constexpr int TP_SCAN_B = 4096;
 
 template <int ITEMS, class Op>
-__global__ void __launch_bounds__(256) k_tp_count(Op op, int64_t n, int64_t nseg, uint32_t *cnt)
+__global__ void __launch_bounds__(256) k_tp_count(Op op, int64_t n, int64_t nseg, uint32_t *cnt, uint32_t *masks,
+                                                 int32_t *words)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warps = static_cast<int64_t>(gridDim.x) * 8;
@@ -217,7 +221,14 @@ __global__ void __launch_bounds__(256) k_tp_count(Op op, int64_t n, int64_t nseg
         op.eval(pos0, ok, pre, slot);
         uint32_t c = 0;
 #pragma unroll
-        for (int k = 0; k < ITEMS; k++) c += __popc(__ballot_sync(QE_FULL_MASK, ok[k]));
+        for (int k = 0; k < ITEMS; k++) {
+            const unsigned m = __ballot_sync(QE_FULL_MASK, ok[k]);
+            c += __popc(m);
+            if (lane == 0) masks[seg * ITEMS + k] = m;
+            if constexpr (Op::kPay) {
+                if (ok[k]) words[pos0 + 32 * k] = op.word(k, slot);
+            }
+        }
         if (lane == 0) cnt[seg] = c;
     }
 }
@@ -290,7 +301,8 @@ static __global__ void __launch_bounds__(1024) k_tp_scan_top(int64_t *bsum, int 
 
 template <int ITEMS, class Op>
 __global__ void __launch_bounds__(256) k_tp_write(Op op, int64_t n, int64_t nseg, const uint32_t *loc,
-                                                 const int64_t *bsum, int64_t capacity)
+                                                 const int64_t *bsum, int64_t capacity, const uint32_t *masks,
+                                                 const int32_t *words)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1;
@@ -303,7 +315,14 @@ __global__ void __launch_bounds__(256) k_tp_write(Op op, int64_t n, int64_t nseg
         typename Op::Pre pre;
         typename Op::Slot slot;
         op.load(pos0, ok, pre);
-        op.eval(pos0, ok, pre, slot);
+        int32_t w[ITEMS];
+#pragma unroll
+        for (int k = 0; k < ITEMS; k++) {
+            ok[k] = (masks[seg * ITEMS + k] >> lane) & 1u;
+            w[k] = 0;
+            if constexpr (Op::kPay) w[k] = ok[k] ? words[pos0 + 32 * k] : 0;
+        }
+        op.restore(pre, w, slot);
         int64_t pos = bsum[seg / TP_SCAN_B] + loc[seg];
 #pragma unroll
         for (int k = 0; k < ITEMS; k++) {
@@ -327,12 +346,19 @@ qe_status launch_two_pass(qe_ctx *ctx, const char *name, int64_t n, int64_t capa
     const int64_t nblk = qe_ceil_div(nseg, TP_SCAN_B);
     if (nblk > 4 * 1024) return qe_fail(ctx, QE_ERR_INVALID_ARG, std::string(name) + ": too many rows");
     void *scratch = nullptr;
-    const size_t cnt_bytes = ((static_cast<size_t>(nseg) * 4 + 255) / 256) * 256;
-    qe_status st = qe_alloc(ctx, &scratch, 2 * cnt_bytes + static_cast<size_t>(nblk) * 8, s);
+    auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t cnt_bytes = up(static_cast<size_t>(nseg) * 4), bs_bytes = up(static_cast<size_t>(nblk) * 8),
+                 mask_bytes = up(static_cast<size_t>(nseg) * ITEMS * 4),
+                 word_bytes = Op::kPay ? static_cast<size_t>(nseg) * ITEMS * 32 * 4 : 0;
+    // counts, offsets, block sums, survivor ballots (4 bytes per 32 positions), payload words (4 per position)
+    qe_status st = qe_alloc(ctx, &scratch, 2 * cnt_bytes + bs_bytes + mask_bytes + word_bytes, s);
     if (st != QE_OK) return st;
-    uint32_t *cnt = static_cast<uint32_t *>(scratch);
-    uint32_t *loc = reinterpret_cast<uint32_t *>(static_cast<char *>(scratch) + cnt_bytes);
-    int64_t *bsum = reinterpret_cast<int64_t *>(static_cast<char *>(scratch) + 2 * cnt_bytes);
+    char *p = static_cast<char *>(scratch);
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(p);
+    uint32_t *loc = reinterpret_cast<uint32_t *>(p + cnt_bytes);
+    int64_t *bsum = reinterpret_cast<int64_t *>(p + 2 * cnt_bytes);
+    uint32_t *masks = reinterpret_cast<uint32_t *>(p + 2 * cnt_bytes + bs_bytes);
+    int32_t *words = Op::kPay ? reinterpret_cast<int32_t *>(p + 2 * cnt_bytes + bs_bytes + mask_bytes) : nullptr;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tp_write<ITEMS, Op>, 256, 0);
     if (per_sm < 1) per_sm = 1;
@@ -341,13 +367,14 @@ qe_status launch_two_pass(qe_ctx *ctx, const char *name, int64_t n, int64_t capa
     cudaError_t e;
     {
         ProfScope prof(ctx, name, s);
-        k_tp_count<ITEMS, Op><<<static_cast<unsigned>(grid), 256, 0, s>>>(op, n, nseg, cnt);
+        k_tp_count<ITEMS, Op><<<static_cast<unsigned>(grid), 256, 0, s>>>(op, n, nseg, cnt, masks, words);
         QE_LAUNCHED(ctx);
         k_tp_scan_local<<<static_cast<unsigned>(nblk), 1024, 0, s>>>(cnt, loc, nseg, bsum);
         QE_LAUNCHED(ctx);
         k_tp_scan_top<<<1, 1024, 0, s>>>(bsum, static_cast<int>(nblk), out_count, capacity, ctx->dstat);
         QE_LAUNCHED(ctx);
-        k_tp_write<ITEMS, Op><<<static_cast<unsigned>(grid), 256, 0, s>>>(op, n, nseg, loc, bsum, capacity);
+        k_tp_write<ITEMS, Op><<<static_cast<unsigned>(grid), 256, 0, s>>>(op, n, nseg, loc, bsum, capacity, masks,
+                                                                          words);
         QE_LAUNCHED(ctx);
         e = cudaGetLastError();
     }

@@ -185,6 +185,19 @@ struct ProbeOp {
         __stcs(out_row + o, s.row[k]);
         __stcs(out_pay + o, s.pay[k]);
     }
+    // two-pass probe: the payload word a survivor keeps between the passes,
+    // and a survivor restored from its row and that word
+    static constexpr bool kPay = true;
+    __device__ __forceinline__ int32_t word(int k, const Slot &s) const { return s.pay[k]; }
+    template <int ITEMS>
+    __device__ __forceinline__ void restore(const Pre &pre, const int32_t (&w)[ITEMS], Slot &s) const
+    {
+#pragma unroll
+        for (int k = 0; k < ITEMS; k++) {
+            s.row[k] = pre.row[k];
+            s.pay[k] = w[k];
+        }
+    }
 };
 
 // Semi- / anti-join as a stable compaction: position i keeps row sel[i] (or
@@ -230,6 +243,15 @@ struct SemiOp {
     __device__ __forceinline__ void emit(int64_t o, int64_t, int k, const Slot &s) const
     {
         __stcs(out_row + o, s.row[k]);
+    }
+    // two-pass: survivors keep no payload; a survivor is its row
+    static constexpr bool kPay = false;
+    __device__ __forceinline__ int32_t word(int, const Slot &) const { return 0; }
+    template <int ITEMS>
+    __device__ __forceinline__ void restore(const Pre &pre, const int32_t (&)[ITEMS], Slot &s) const
+    {
+#pragma unroll
+        for (int k = 0; k < ITEMS; k++) s.row[k] = pre.row[k];
     }
 };
 
@@ -338,6 +360,19 @@ struct PairProbeOp {
     {
         __stcs(out_row + o, s.row[k]);
         __stcs(out_pay + o, s.pay[k]);
+    }
+    // two-pass probe: the payload word a survivor keeps between the passes,
+    // and a survivor restored from its row and that word
+    static constexpr bool kPay = true;
+    __device__ __forceinline__ int32_t word(int k, const Slot &s) const { return s.pay[k]; }
+    template <int ITEMS>
+    __device__ __forceinline__ void restore(const Pre &pre, const int32_t (&w)[ITEMS], Slot &s) const
+    {
+#pragma unroll
+        for (int k = 0; k < ITEMS; k++) {
+            s.row[k] = pre.row[k];
+            s.pay[k] = w[k];
+        }
     }
 };
 
