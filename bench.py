@@ -502,6 +502,8 @@ def run_variants(args, qe, ctx, dev, stream, peak, it):
         set of half the dimension's keys + group-by flag (the set is built in
         the call): 21 B per fact row + 4 B per set key;
       single_table: filter + group-by flag, no join (fk_col = -1): 17 B per row;
+      inner_probe: stand-alone probe of the dimension's dense table over the
+        filter's selection vector: 4 B selection + 4 B key + 8 B per output;
       semi_join / anti_join: stand-alone, over the filter's selection vector:
         4 B selection + 4 B key + 4 B per output position;
       multi_build / multi_probe: many-to-many join against a partsupp-shaped
@@ -566,6 +568,17 @@ def run_variants(args, qe, ctx, dev, stream, peak, it):
     out_rows = torch.empty(4 * nsel + 1, dtype=torch.int32, device=dev)
     out_pay = torch.empty(4 * nsel + 1, dtype=torch.int32, device=dev)
     ocnt = torch.empty(1, dtype=torch.int64, device=dev)
+
+    # stand-alone inner probe against the dimension (unique keys)
+    hd = qe.qe_join_build(ctx, dim["key"], dim["attr"])
+    fn = lambda: qe.qe_join_probe(ctx, hd, fact["fk"], sel, n=nsel, capacity=nsel, out_rows=out_rows,  # noqa: E731
+                                  out_payload=out_pay, out_count=ocnt, check=False)
+    fn()
+    ctx.sync_status()
+    ms = timed(fn, it, stream)
+    k = int(ocnt.item())
+    res["inner_probe"] = entry(ms, nsel, 8 * nsel + 8 * k, outputs=k)
+    hd.destroy()
 
     # stand-alone semi- and anti-join
     hs = qe.qe_join_build_set(ctx, half)
