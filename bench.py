@@ -367,7 +367,11 @@ def run_qe(args):
     # the join variants and the skewed, high-cardinality pipeline last: their
     # multi-GB tables stay out of the way of the batch and serve forms
     if "variants" in args.forms:
-        extras["variants"] = run_variants(args, qe, ctx, dev, stream, peak, max(3, args.steps // 2))
+        try:
+            extras["variants"] = run_variants(args, qe, ctx, dev, stream, peak, max(3, args.steps // 2))
+        except qe.QeError as e:   # a library error in an extra leg is reported, not fatal to the line
+            extras["variants"] = {"error": str(e)}
+            torch.cuda.empty_cache()
     if "extras" in args.forms:
         extras["skew_40m_groups"] = run_skew(args, qe, ctx, dev, stream, peak, max(3, args.steps // 2))
 
