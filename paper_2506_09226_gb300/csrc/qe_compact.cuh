@@ -192,8 +192,8 @@ qe_status launch_compact(qe_ctx *ctx, const char *name, int64_t n, int64_t capac
 
 // ---------------------------------------------------------------------------
 // Two-pass stable compaction for large inputs, with no dependency between
-// blocks (so as many tiles are in flight as occupancy allows; the price is
-// evaluating every row twice).  A warp segment is 32 lanes x ITEMS rows in
+// blocks (so as many tiles are in flight as occupancy allows; the price is a
+// second pass over the selection rows and the survivors kept by the first).  A warp segment is 32 lanes x ITEMS rows in
 // the tile order above (item k of lane l is position seg*32*ITEMS + 32k + l).
 // Pass 1 counts each segment's survivors and keeps what pass 2 needs: the
 // survivor ballot of every item and, for ops with a payload (Op::kPay), each
