@@ -4,8 +4,9 @@ Each case applies one plausible mistake to a copy of oracle/qe_oracle.c (a
 boundary off by one, a dropped step of the hash, a wrong index, a flipped
 sign, swapped key halves, an unstable placement, a dropped predicate term, a
 wrong payload index, a flipped or shortened membership test, a swapped join
-kind), compiles it, and runs tests/test_oracle_pins.py against it; the pin
-suite must fail for every mutant.
+kind, a zero-extended group key), compiles it, and runs
+tests/test_oracle_pins.py against it; the pin suite must fail for every
+mutant.
 """
 import os
 import subprocess
@@ -43,6 +44,7 @@ MUTANTS = {
                   "if (found == (anti != 0)) out_row[count++] = row;"),
     "semi_last_key": ("int found = lo < nb && b[lo] == k;", "int found = lo + 1 < nb && b[lo] == k;"),
     "pipeline_kind": ("join_kind == 2, rows);", "join_kind == 1, rows);"),
+    "key_zero_extend": ("    if (!has_hi) return lo;", "    if (!has_hi) return (int64_t)(uint32_t)lo;"),
     "radix_shift": ("return (int64_t)(((uint64_t)key >> shift) & (fanout - 1));",
                     "return (int64_t)(((uint64_t)key >> (shift + 1)) & (fanout - 1));"),
 }

@@ -527,6 +527,26 @@ def test_pipeline_without_join():
         [ref[k] for k in sorted(ref)]
 
 
+def test_group_key_rule():
+    """The group key: the low part alone, sign-extended, without a high part;
+    (hi << 32) | (uint32)lo with one.  Checked directly and through join-free
+    pipelines grouped by a negative int32 column and by an int64 column."""
+    assert O.group_key(False, 0, -5) == -5
+    assert O.group_key(False, 0, -(1 << 40)) == -(1 << 40)
+    assert O.group_key(True, -1, -2) == -2
+    assert O.group_key(True, 2, -1) == (2 << 32) | 0xFFFFFFFF
+    assert O.group_key(True, -3, 7) == wrap64((-3 << 32) | 7)
+    rng = np.random.default_rng(5)
+    v = rng.integers(0, 100, 200).astype(np.int64)
+    for col in (rng.integers(-4, 4, 200).astype(np.int32),
+                (rng.integers(-3, 3, 200) * (1 << 40)).astype(np.int64)):
+        q = O.Query(preds=[], fk_col=-1, key_hi_col=-1, key_lo_col=0, aggs=[(O.SUM, 1, -1), (O.COUNT, -1, -1)])
+        r = O.pipeline([col, v], q)
+        ref = bf_groupby(col.tolist(), [(O.SUM, v), (O.COUNT, None)])
+        assert r["keys"].tolist() == sorted(ref)
+        assert [[int(a[i]) for a in r["aggs"]] for i in range(len(r["keys"]))] == [ref[k] for k in sorted(ref)]
+
+
 # ---------------------------------------------------------------- planted mistakes
 def test_pins_catch_planted_mistakes():
     """The brute-force pins reject plausible oracle mistakes: a dropped
