@@ -232,10 +232,23 @@ def run_reference(args):
             "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int64", "data": "synthetic", "impl": "reference",
             "config": workload_config(args),
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+                             **host_cores()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def host_cores() -> dict:
+    """The host's core count (os.cpu_count) and the cores this process may
+    run on (its affinity mask), reported beside the single-threaded oracle."""
+    try:
+        aff = sorted(os.sched_getaffinity(0))
+    except AttributeError:
+        aff = list(range(os.cpu_count() or 1))
+    return {"host_nproc": os.cpu_count(), "affinity_cores": len(aff),
+            "affinity": f"{aff[0]}-{aff[-1]}" if aff and aff == list(range(aff[0], aff[-1] + 1)) else
+            ",".join(map(str, aff))}
 
 
 def workload_config(args):
@@ -381,7 +394,7 @@ def run_qe(args):
         runs = [sample.run() for _ in range(2)]
         dt = sum(runs) / len(runs)
         cpu = {"value": sample.rows / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": sample.desc + f"; mean of 2 runs ({sum(runs):.1f} s of CPU work)"}
+               "sample": sample.desc + f"; mean of 2 runs ({sum(runs):.1f} s of CPU work)", **host_cores()}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

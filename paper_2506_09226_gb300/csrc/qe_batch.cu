@@ -161,7 +161,7 @@ __device__ __noinline__ void item_generic(const PipeSpec &P, const TableCfg T, u
 #pragma unroll
         for (int k = 0; k < B_ITEMS; k++) {
             const int64_t r = t0 + k * BT + threadIdx.x;
-            v[k] = row_load(P, nullptr, false, 0, r, r < r1);
+            v[k] = row_load(P, r, r < r1);
         }
         int64_t hi[B_ITEMS], lo[B_ITEMS];
         bool ok[B_ITEMS];

@@ -2,35 +2,32 @@
 // single-pipeline kernel (qe_pipeline.cu) and the batched persistent kernel
 // (qe_batch.cu).
 //
-// A tile is ITEMS x 1024 consecutive fact rows.  The columns a pipeline reads
-// are copied tile by tile into shared memory with the Tensor Memory
-// Accelerator (cp.async.bulk, completion on an mbarrier); each thread of a
-// 1024-thread block then owns ITEMS rows of the tile, 1024 rows apart.  Tiles
-// that are not full, or columns that are not 16-byte aligned, are read
-// straight from global memory.
+// A tile is ITEMS x THREADS consecutive fact rows.  Each thread of a block
+// owns ITEMS rows of the tile, THREADS rows apart, so every column read is a
+// coalesced warp access straight from global memory with an evict-first
+// (streaming) hint; the star-shape loop also loads the next tile's columns
+// into registers while the current tile is processed, which keeps the loads
+// in flight in the register file rather than in shared memory (shared memory
+// holds the group table).
 #pragma once
 
 #include <climits>
 #include <cstdlib>
 
 #include "qe_internal.cuh"
-#include "qe_tma.cuh"
 
 #define PIPE_THREADS 1024
 #define PIPE_WARPS (PIPE_THREADS / 32)
-#define PIPE_MAX_STAGE 8
 
 enum { SRC_NONE = 0, SRC_X = 1, SRC_Y = 2, SRC_XY = 3 };
 
-// Device view of one pipeline.  Column slots index the staged columns.
+// Device view of one pipeline.  Column slots index the columns it reads.
 struct PipeSpec {
     int64_t n;                          // fact rows
-    int32_t ncol;                       // staged columns
-    int32_t tma;                        // all staged columns 16-byte aligned
+    int32_t ncol;                       // columns read
+    int32_t pad0;
     const void *col[QE_MAX_COLS];
     int32_t type[QE_MAX_COLS];
-    uint32_t soff[QE_MAX_COLS];         // byte offset of the column in a stage
-    uint32_t stage_bytes;               // bytes of a full tile
     int32_t npreds;
     int32_t pslot[QE_MAX_PREDS], pop[QE_MAX_PREDS];
     int64_t plo[QE_MAX_PREDS], phi[QE_MAX_PREDS];
@@ -64,39 +61,10 @@ struct TableCfg {
     int log2S;
 };
 
-// Fill a stage with rows [row0, row0 + PIPE_TR) of every staged column, or,
-// for a partial tile or unaligned columns, just complete the barrier phase
-// (the consumers then read global memory).
-__device__ __forceinline__ void stage_issue(const PipeSpec &P, unsigned char *stage, unsigned long long *bar,
-                                            int64_t row0, uint64_t policy, int tr)
-{
-    if (P.tma && row0 + tr <= P.n) {
-        fence_proxy_async_smem();
-        mbar_arrive_expect_tx(bar, P.stage_bytes);
-        for (int c = 0; c < P.ncol; c++) {
-            const uint32_t sz = static_cast<uint32_t>(P.type[c]);
-            tma_load_1d(stage + P.soff[c], static_cast<const unsigned char *>(P.col[c]) + row0 * sz,
-                        static_cast<uint32_t>(tr) * sz, bar, policy);
-        }
-    } else {
-        mbar_arrive(bar);
-    }
-}
-
 // ------------------------------------------------------------ row values
-__device__ __forceinline__ int64_t ld_stage(const unsigned char *stage, uint32_t off, int type, int r)
+// Column slot value of fact row `grow` (streaming load, sign-extended).
+__device__ __forceinline__ int64_t ld_slot(const PipeSpec &P, int slot, int64_t grow)
 {
-    const unsigned char *p = stage + off;
-    if (type == QE_I32) return static_cast<int64_t>(reinterpret_cast<const int32_t *>(p)[r]);
-    if (type == QE_I64) return reinterpret_cast<const long long *>(p)[r];
-    return static_cast<int64_t>(reinterpret_cast<const signed char *>(p)[r]);
-}
-
-// Column slot value of a row, from the stage (smem) or global memory.
-__device__ __forceinline__ int64_t ld_slot(const PipeSpec &P, const unsigned char *stage, bool from_stage, int slot,
-                                           int r, int64_t grow)
-{
-    if (from_stage) return ld_stage(stage, P.soff[slot], P.type[slot], r);
     return dev_col_stream(P.col[slot], P.type[slot], grow);
 }
 
@@ -109,14 +77,13 @@ struct RowVals {
 };
 
 // Predicates and the columns a surviving row needs.
-__device__ __forceinline__ RowVals row_load(const PipeSpec &P, const unsigned char *stage, bool from_stage, int r,
-                                            int64_t grow, bool in_range)
+__device__ __forceinline__ RowVals row_load(const PipeSpec &P, int64_t grow, bool in_range)
 {
     RowVals v;
     bool ok = in_range;
 #pragma unroll
     for (int p = 0; p < QE_MAX_PREDS; p++)
-        if (p < P.npreds && ok) ok = dev_cmp(ld_slot(P, stage, from_stage, P.pslot[p], r, grow), P.pop[p], P.plo[p], P.phi[p]);
+        if (p < P.npreds && ok) ok = dev_cmp(ld_slot(P, P.pslot[p], grow), P.pop[p], P.plo[p], P.phi[p]);
     v.ok = ok;
     v.key_a = 0;
     v.lo = 0;
@@ -124,11 +91,11 @@ __device__ __forceinline__ RowVals row_load(const PipeSpec &P, const unsigned ch
     v.x = 0;
     v.y = 0;
     if (ok) {
-        v.key_a = ld_slot(P, stage, from_stage, P.has_join ? P.fk_slot : P.lo_slot, r, grow);
-        if (P.has_join && P.lo_slot >= 0) v.lo = ld_slot(P, stage, from_stage, P.lo_slot, r, grow);
-        if (P.hi_slot >= 0) v.hi = ld_slot(P, stage, from_stage, P.hi_slot, r, grow);
-        if (P.x_slot >= 0) v.x = ld_slot(P, stage, from_stage, P.x_slot, r, grow);
-        if (P.y_slot >= 0) v.y = ld_slot(P, stage, from_stage, P.y_slot, r, grow);
+        v.key_a = ld_slot(P, P.has_join ? P.fk_slot : P.lo_slot, grow);
+        if (P.has_join && P.lo_slot >= 0) v.lo = ld_slot(P, P.lo_slot, grow);
+        if (P.hi_slot >= 0) v.hi = ld_slot(P, P.hi_slot, grow);
+        if (P.x_slot >= 0) v.x = ld_slot(P, P.x_slot, grow);
+        if (P.y_slot >= 0) v.y = ld_slot(P, P.y_slot, grow);
     }
     return v;
 }

@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(PT, 1) k_pipeline(PipeSpec P, TableCfg T)
 #pragma unroll
         for (int k = 0; k < ITEMS; k++) {
             const int64_t r = tile * TR + k * PT + threadIdx.x;
-            v[k] = row_load(P, nullptr, false, 0, r, r < P.n);
+            v[k] = row_load(P, r, r < P.n);
         }
         int64_t hi[ITEMS], lo[ITEMS];
         bool ok[ITEMS];
@@ -205,7 +205,6 @@ qe_status pipeline_prepare(qe_ctx *ctx, const qe_pipeline_desc *d, PipeSpec &P)
     }
     P.x_slot = xc >= 0 ? use(xc) : -1;
     P.y_slot = yc >= 0 ? use(yc) : -1;
-    P.tma = 0;
     return QE_OK;
 }
 
