@@ -92,12 +92,24 @@ typedef enum { QE_SUM = 0, QE_COUNT = 1, QE_MIN = 2, QE_MAX = 3 } qe_agg_op;
  * `capacity` int64; *ngroups (device) receives the number of groups.  If the
  * groups exceed `capacity`, QE_ERR_CAPACITY is recorded with the number of
  * groups seen (a lower bound when the table overflowed) as the required
- * size, and only `capacity` rows are written. */
+ * size, and only `capacity` rows are written.
+ *
+ * Averages (Sec. 2.3 lists average among the aggregation kinds of the final
+ * reduction): avg[a] (nullable; device double [capacity]) asks for the
+ * average of aggregate a, which must be a SUM, over the group's row count,
+ * which some aggregate of the same call must provide as a COUNT:
+ *     avg[a][g] = (double)aggs[a][g] / (double)count[g]
+ * derived in FP64 from the exact int64 SUM and COUNT (one rounding of the
+ * sum to double, one IEEE division), so the average of rows split across
+ * blocks is exact to those two roundings.  A non-NULL avg[a] whose
+ * aggregate is not a SUM, or with no COUNT among the aggregates, returns
+ * QE_ERR_INVALID_ARG.  Entries a >= the number of aggregates must be NULL. */
 typedef struct {
     int64_t capacity;
     int64_t *keys;
     int64_t *aggs[QE_MAX_AGGS];
     int64_t *ngroups;
+    double *avg[QE_MAX_AGGS];
 } qe_groups_out;
 
 typedef struct qe_ctx qe_ctx;

@@ -69,6 +69,8 @@ def lib():
         L.oracle_join.argtypes = [i64, vp, vp, i64, vp, vp, vp, vp, vp]
         L.oracle_groupby.restype = i64
         L.oracle_groupby.argtypes = [i64, vp, ci, vp, vp, vp, vp]
+        L.oracle_avg.restype = None
+        L.oracle_avg.argtypes = [i64, vp, vp, vp]
         L.oracle_group_key.restype = i64
         L.oracle_group_key.argtypes = [ci, i64, i64]
         L.oracle_join_pair.restype = ci
@@ -217,6 +219,17 @@ def groupby(keys, aggs):
     ng = lib().oracle_groupby(n, _p(keys), len(aggs), _p(ops), _ptr_array(vals),
                               _p(out_k), _ptr_array(out_a))
     return out_k[:ng].copy(), [a[:ng].copy() for a in out_a]
+
+
+def avg(sums, counts) -> np.ndarray:
+    """Per-group average (double)sum / (double)count from the exact int64
+    SUM and COUNT of each group (oracle_avg, Sec. 2.3)."""
+    s, c = _c(sums, np.int64), _c(counts, np.int64)
+    if len(s) != len(c):
+        raise ValueError("sums and counts differ in length")
+    out = np.empty(max(len(s), 1), np.float64)
+    lib().oracle_avg(len(s), _p(s), _p(c), _p(out))
+    return out[:len(s)].copy()
 
 
 def group_key(has_hi: bool, hi: int, lo: int) -> int:

@@ -25,6 +25,9 @@
  *   - group-by:   SUM / COUNT / MIN / MAX per distinct key (Sec. 2.3, the
  *                 aggregation kinds of the final reduction; Sec. 2.4, group
  *                 by in the compiled tensor program);
+ *   - average:    AVG of a group derived from its exact integer SUM and
+ *                 COUNT (Sec. 2.3 lists average among the final aggregation
+ *                 kinds);
  *   - pipeline:   group-by(join(filter(fact), dim)), one tensor program per
  *                 GPU (Sec. 2.4).
  *
@@ -383,6 +386,21 @@ int64_t oracle_groupby(int64_t n, const int64_t *keys, int naggs,
     }
     free(r);
     return ng;
+}
+
+/*
+ * Average of each group (Sec. 2.3: average is one of the aggregation kinds
+ * of the final reduction).  Reading: decimals are fixed-point int64, so the
+ * exact aggregates are the int64 SUM and COUNT, and the average is derived
+ * from them in FP64 as (double)sum / (double)count -- one rounding of the
+ * sum to double, then one IEEE division.  Deriving it from SUM and COUNT
+ * (never averaging partial averages) keeps it exact up to those two
+ * roundings however the rows were split between blocks or GPUs.  A group
+ * with count 0 gets 0/0 (NaN); groups of a group-by always have count >= 1.
+ */
+void oracle_avg(int64_t n, const int64_t *sum, const int64_t *count, double *out)
+{
+    for (int64_t g = 0; g < n; g++) out[g] = (double)sum[g] / (double)count[g];
 }
 
 /*

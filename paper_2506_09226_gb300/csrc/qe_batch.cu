@@ -43,7 +43,8 @@ struct BatchPipe {
     unsigned long long *emitted;       // groups written to `out`
     unsigned *build_done, *probe_done;
     uint64_t hslots;                   // HBM hash table slots
-    int32_t star, pad;                 // star shape: the specialised row loop
+    int32_t star;                      // star shape: the specialised row loop
+    int32_t cnt;                       // COUNT aggregate of derived averages, or -1
 };
 
 static_assert(sizeof(PipeSpec) % 4 == 0, "the spec is copied to shared memory in 4-byte words");
@@ -101,6 +102,9 @@ __device__ void batch_finalize(const BatchPipe &B, qe_dev_status *st)
                     B.out.keys[pos] = dense_key(P.dk, i);
                     for (int a = 0; a < P.ops.n; a++)
                         B.out.aggs[a][pos] = agg_decode(P.ops.op[a], __ldcg(P.gdense + i * P.dk.stride + a));
+                    if (B.cnt >= 0)
+                        write_avgs(B.out, pos, P.ops.n, B.cnt,
+                                   [&](int a) { return agg_decode(P.ops.op[a], __ldcg(P.gdense + i * P.dk.stride + a)); });
                 }
             }
         }
@@ -119,6 +123,9 @@ __device__ void batch_finalize(const BatchPipe &B, qe_dev_status *st)
                 B.out.keys[pos] = static_cast<int64_t>(kx ^ GB_SIGN);
                 for (int a = 0; a < P.ops.n; a++)
                     B.out.aggs[a][pos] = agg_decode(P.ops.op[a], __ldcg(P.g.words + i * P.g.stride + 1 + a));
+                if (B.cnt >= 0)
+                    write_avgs(B.out, pos, P.ops.n, B.cnt,
+                               [&](int a) { return agg_decode(P.ops.op[a], __ldcg(P.g.words + i * P.g.stride + 1 + a)); });
             }
         }
     }
@@ -301,9 +308,12 @@ extern "C" qe_status qe_batch_create(qe_ctx *ctx, const qe_pipeline_desc *descs,
         BatchPipe &B = pipes[i];
         qe_status st = pipeline_prepare(ctx, &d, B.P);
         if (st != QE_OK) return st;
-        st = gt_check_out(ctx, &outs[i], d.n_aggs);
+        st = gt_check_out(ctx, &outs[i], B.P.ops);
         if (st != QE_OK) return st;
         B.out = outs[i];
+        B.cnt = -1;
+        for (int a = 0; a < QE_MAX_AGGS; a++)
+            if (B.out.avg[a]) B.cnt = agg_count_index(B.P.ops);
         int64_t pay_min = 1, pay_max = 0;
         if (B.P.has_join) {
             const bool inner = B.P.join_kind == QE_JOIN_INNER;

@@ -209,12 +209,28 @@ extern "C" qe_status qe_sync_status(qe_ctx *ctx, void *stream, int64_t *required
 
 // ------------------------------------------------------------ group tables
 
-qe_status gt_check_out(qe_ctx *ctx, const qe_groups_out *out, int naggs)
+// Index of the COUNT aggregate (the divisor of derived averages), or -1.
+int agg_count_index(const AggOps &ops)
+{
+    for (int a = 0; a < ops.n; a++)
+        if (ops.op[a] == QE_COUNT) return a;
+    return -1;
+}
+
+qe_status gt_check_out(qe_ctx *ctx, const qe_groups_out *out, const AggOps &ops)
 {
     if (!out || out->capacity < 0 || !out->ngroups) return qe_fail(ctx, QE_ERR_INVALID_ARG, "bad group output");
     if (out->capacity > 0 && !out->keys) return qe_fail(ctx, QE_ERR_INVALID_ARG, "group output keys missing");
-    for (int a = 0; a < naggs; a++)
+    for (int a = 0; a < ops.n; a++)
         if (out->capacity > 0 && !out->aggs[a]) return qe_fail(ctx, QE_ERR_INVALID_ARG, "group output aggs missing");
+    // derived averages: over a SUM, with a COUNT among the aggregates
+    for (int a = 0; a < QE_MAX_AGGS; a++) {
+        if (!out->avg[a]) continue;
+        if (a >= ops.n || ops.op[a] != QE_SUM)
+            return qe_fail(ctx, QE_ERR_INVALID_ARG, "group output: an average needs a SUM aggregate");
+        if (agg_count_index(ops) < 0)
+            return qe_fail(ctx, QE_ERR_INVALID_ARG, "group output: an average needs a COUNT aggregate");
+    }
     return QE_OK;
 }
 
@@ -239,6 +255,7 @@ struct CompactArgs {
     const unsigned long long *words;
     uint64_t slots;
     int stride;
+    int cnt;             // index of the COUNT aggregate (averages), or -1
     AggOps ops;
     qe_groups_out out;
     unsigned long long *emitted;
@@ -262,6 +279,8 @@ __global__ void __launch_bounds__(256) k_gt_compact(CompactArgs A)
                 A.out.keys[pos] = static_cast<int64_t>(kx ^ GB_SIGN);
                 _Pragma("unroll") for (int a = 0; a < QE_MAX_AGGS; a++) if (a < A.ops.n)
                     A.out.aggs[a][pos] = agg_decode(A.ops.op[a], A.words[i * A.stride + 1 + a]);
+                if (A.cnt >= 0)
+                    write_avgs(A.out, pos, A.ops.n, A.cnt, [&](int a) { return agg_decode(A.ops.op[a], A.words[i * A.stride + 1 + a]); });
             }
         }
     }
@@ -278,6 +297,7 @@ __global__ void k_gt_count(const unsigned long long *emitted, int64_t capacity, 
 struct DenseCompactArgs {
     const unsigned long long *dense;
     DenseKey d;
+    int cnt;             // index of the COUNT aggregate (averages), or -1
     AggOps ops;
     qe_groups_out out;
     unsigned long long *emitted;
@@ -301,6 +321,8 @@ __global__ void __launch_bounds__(256) k_gd_compact(DenseCompactArgs A)
                 A.out.keys[pos] = dense_key(A.d, i);
                 for (int a = 0; a < A.ops.n; a++)
                     A.out.aggs[a][pos] = agg_decode(A.ops.op[a], A.dense[i * A.d.stride + a]);
+                if (A.cnt >= 0)
+                    write_avgs(A.out, pos, A.ops.n, A.cnt, [&](int a) { return agg_decode(A.ops.op[a], A.dense[i * A.d.stride + a]); });
             }
         }
     }
@@ -312,6 +334,7 @@ qe_status gt_finalize_dense(qe_ctx *ctx, const GroupTableHost &t, const AggOps &
     DenseCompactArgs A;
     A.dense = dense;
     A.d = d;
+    A.cnt = agg_count_index(ops);
     A.ops = ops;
     A.out = *out;
     A.emitted = t.words + t.slots * t.stride + 1;
@@ -331,6 +354,7 @@ qe_status gt_finalize(qe_ctx *ctx, const GroupTableHost &t, const AggOps &ops, c
     A.words = t.words;
     A.slots = t.slots;
     A.stride = t.stride;
+    A.cnt = agg_count_index(ops);
     A.ops = ops;
     A.out = *out;
     A.emitted = t.words + t.slots * t.stride + 1;

@@ -117,8 +117,6 @@ extern "C" qe_status qe_groupby(qe_ctx *ctx, int64_t n, const int32_t *rows, qe_
     if (n < 0 || naggs < 0 || naggs > QE_MAX_AGGS || (naggs > 0 && !aggs) || placement < QE_GB_AUTO ||
         placement > QE_GB_HBM)
         return qe_fail(ctx, QE_ERR_INVALID_ARG, "groupby: bad argument");
-    qe_status st = gt_check_out(ctx, out, naggs);
-    if (st != QE_OK) return st;
     GroupbyArgs A{};
     A.n = n;
     A.rows = rows;
@@ -140,6 +138,8 @@ extern "C" qe_status qe_groupby(qe_ctx *ctx, int64_t n, const int32_t *rows, qe_
         A.a[a] = {g.a.data, g.a.type, g.a.gather};
         A.b[a] = {g.op == QE_COUNT ? nullptr : g.b.data, g.b.type, g.b.gather};
     }
+    qe_status st = gt_check_out(ctx, out, A.ops);
+    if (st != QE_OK) return st;
     cudaSetDevice(ctx->device);
     GroupTableHost t;
     st = gt_create(ctx, out->capacity, naggs, t, s);

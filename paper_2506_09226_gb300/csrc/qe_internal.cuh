@@ -587,7 +587,29 @@ qe_status gt_finalize(qe_ctx *ctx, const GroupTableHost &t, const AggOps &ops, c
 // (AoS, d.stride words per slot).
 qe_status gt_finalize_dense(qe_ctx *ctx, const GroupTableHost &t, const AggOps &ops, const DenseKey &d,
                             const unsigned long long *dense, const qe_groups_out *out, cudaStream_t s);
-qe_status gt_check_out(qe_ctx *ctx, const qe_groups_out *out, int naggs);
+// Checks the output arrays of a group-by with aggregates `ops`, including
+// the derived averages (each over a SUM, with a COUNT among the aggregates).
+qe_status gt_check_out(qe_ctx *ctx, const qe_groups_out *out, const AggOps &ops);
+int agg_count_index(const AggOps &ops);
+
+// Derived averages of one output group (Sec. 2.3 lists average among the
+// final aggregation kinds): for each aggregate a with out.avg[a] set,
+// avg = (double)SUM / (double)COUNT from the exact int64 values; value(a)
+// returns aggregate a of the group, cnt is the COUNT aggregate's index.
+template <class F>
+__device__ __forceinline__ void write_avgs(const qe_groups_out &out, int64_t pos, int naggs, int cnt, F value)
+{
+    double c = 0.0;
+    bool have_c = false;
+    for (int a = 0; a < naggs; a++) {
+        if (!out.avg[a]) continue;
+        if (!have_c) {
+            c = static_cast<double>(value(cnt));
+            have_c = true;
+        }
+        out.avg[a][pos] = static_cast<double>(value(a)) / c;
+    }
+}
 
 // Smem group-table sizing: slots for `groups` at <= 75% load, 0 when the
 // table would not fit `smem_budget` bytes.

@@ -313,7 +313,7 @@ extern "C" qe_status qe_pipeline(qe_ctx *ctx, const qe_pipeline_desc *desc, cons
     PipeSpec P;
     qe_status st = pipeline_prepare(ctx, desc, P);
     if (st != QE_OK) return st;
-    st = gt_check_out(ctx, out, desc->n_aggs);
+    st = gt_check_out(ctx, out, P.ops);
     if (st != QE_OK) return st;
     cudaSetDevice(ctx->device);
     qe_hash_table *built = nullptr;

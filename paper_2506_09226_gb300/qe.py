@@ -60,7 +60,8 @@ class qe_pred(ctypes.Structure):
 
 class qe_groups_out(ctypes.Structure):
     _fields_ = [("capacity", ctypes.c_int64), ("keys", ctypes.c_void_p),
-                ("aggs", ctypes.c_void_p * MAX_AGGS), ("ngroups", ctypes.c_void_p)]
+                ("aggs", ctypes.c_void_p * MAX_AGGS), ("ngroups", ctypes.c_void_p),
+                ("avg", ctypes.c_void_p * MAX_AGGS)]
 
 
 class qe_build_opts(ctypes.Structure):
@@ -496,29 +497,40 @@ class Groups:
     aggs: list
     ngroups: torch.Tensor
     capacity: int
+    avg: dict = None      # aggregate index -> float64 tensor of derived averages
 
     def to_host(self):
         """(keys, [aggs]) trimmed to ngroups, as CPU tensors."""
         n = min(int(self.ngroups.item()), self.capacity)
         return self.keys[:n].cpu(), [a[:n].cpu() for a in self.aggs]
 
+    def avg_host(self, a: int):
+        """The derived averages of aggregate a, trimmed to ngroups (CPU)."""
+        n = min(int(self.ngroups.item()), self.capacity)
+        return self.avg[a][:n].cpu()
 
-def alloc_groups(capacity: int, naggs: int, device) -> tuple:
+
+def alloc_groups(capacity: int, naggs: int, device, avg=()) -> tuple:
+    """Output buffers of a group-by; avg lists the SUM aggregates whose
+    derived FP64 average (over the call's COUNT aggregate) is also wanted."""
     keys = torch.empty(max(capacity, 1), dtype=torch.int64, device=device)
     aggs = [torch.empty(max(capacity, 1), dtype=torch.int64, device=device) for _ in range(naggs)]
     ng = torch.zeros(1, dtype=torch.int64, device=device)
+    avgs = {a: torch.full((max(capacity, 1),), float("nan"), dtype=torch.float64, device=device) for a in avg}
     out = qe_groups_out(capacity, keys.data_ptr(), (ctypes.c_void_p * MAX_AGGS)(*(
-        [a.data_ptr() for a in aggs] + [None] * (MAX_AGGS - naggs))), ng.data_ptr())
-    return Groups(keys, aggs, ng, capacity), out
+        [a.data_ptr() for a in aggs] + [None] * (MAX_AGGS - naggs))), ng.data_ptr(),
+        (ctypes.c_void_p * MAX_AGGS)(*[avgs[a].data_ptr() if a in avgs else None for a in range(MAX_AGGS)]))
+    return Groups(keys, aggs, ng, capacity, avgs), out
 
 
 def qe_groupby(ctx: Context, key_lo, aggs, key_hi=None, rows=None, n=None, capacity=1024, placement=GB_AUTO,
-               gather_lo=False, gather_hi=False, stream=None, check=True):
-    """aggs: list of (op, a, b, gather) with a/b tensors (or None)."""
+               gather_lo=False, gather_hi=False, stream=None, check=True, avg=()):
+    """aggs: list of (op, a, b, gather) with a/b tensors (or None); avg: the
+    SUM aggregates whose derived averages are wanted."""
     if n is None:
         n = rows.numel() if rows is not None else key_lo.numel()
     dev = key_lo.device
-    groups, out = alloc_groups(capacity, len(aggs), dev)
+    groups, out = alloc_groups(capacity, len(aggs), dev, avg)
     carr = []
     for ag in aggs:
         op, a, b = ag[0], ag[1], ag[2]
@@ -570,10 +582,11 @@ def pipeline_desc(fact, preds, fk_col=-1, dim_key=None, dim_payload=None, ht: Ha
     return d
 
 
-def qe_pipeline(ctx: Context, desc: qe_pipeline_desc, capacity: int, stream=None, check=True, out=None):
-    """out: (Groups or None, qe_groups_out) to write into existing buffers."""
+def qe_pipeline(ctx: Context, desc: qe_pipeline_desc, capacity: int, stream=None, check=True, out=None, avg=()):
+    """out: (Groups or None, qe_groups_out) to write into existing buffers;
+    avg: the SUM aggregates whose derived averages are wanted."""
     if out is None:
-        groups, cout = alloc_groups(capacity, desc.n_aggs, torch.device("cuda", ctx.device))
+        groups, cout = alloc_groups(capacity, desc.n_aggs, torch.device("cuda", ctx.device), avg)
     else:
         groups, cout = out
     ctx.check(ctx.lib.qe_pipeline(ctx.h, ctypes.byref(desc), ctypes.byref(cout), _stream(stream)))

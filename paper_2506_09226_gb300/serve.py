@@ -72,6 +72,7 @@ class Request:
     slot: int = -1
     admitted: float = -1.0
     done: float = -1.0
+    cancelled: bool = False
 
 
 @dataclass
@@ -82,42 +83,66 @@ class ServeStats:
     rounds: int = 0
     max_inflight: int = 0
     max_round: int = 0
+    cancelled: int = 0
 
     def summary(self) -> dict:
         lat = self.latencies_ms or [0.0]
         return {"requests": len(self.latencies_ms), "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99),
                 "mean_ms": float(np.mean(lat)), "rows_per_s": self.rows / max(self.makespan_s, 1e-9),
                 "makespan_s": self.makespan_s, "rounds": self.rounds, "max_inflight": self.max_inflight,
-                "max_round": self.max_round}
+                "max_round": self.max_round, "cancelled": self.cancelled}
 
 
 def serve_loop(trace, executor, admission: Admission, max_round: int = 4096, clock=time.perf_counter,
-               idle_sleep: float = 20e-6, row_cap: int | None = None) -> ServeStats:
+               idle_sleep: float = 20e-6, row_cap: int | None = None, cancel_at: dict | None = None) -> ServeStats:
     """Continuous batching over `trace` (Arrival list sorted by t).
 
     A round takes the oldest admitted requests until it holds max_round of
     them or row_cap fact rows (a request larger than row_cap goes alone), so
     rounds stay short and small requests are not held behind a large one.
     executor.launch(reqs) -> handle with .done() and .close(); executor.cost(req)
-    is the request's HBM share.  Works with any clock/executor (tests use fakes)."""
+    is the request's HBM share.  Works with any clock/executor (tests use fakes).
+
+    cancel_at maps a request id to the time (seconds after the start) at
+    which its client withdraws it.  A request cancelled before admission is
+    dropped; one admitted but not launched gives its output slot and HBM
+    share back at once, so a waiting request can take them; one whose round
+    is already on the device keeps them until that round completes (kernels
+    are never interrupted) and its result is discarded.  Cancelled requests
+    count in ServeStats.cancelled, not in the latencies or rows."""
     reqs = [Request(i, a.t, a.shape, a.offset, a.n, a.date_hi) for i, a in enumerate(trace)]
     pending = collections.deque(reqs)
     waiting = collections.deque()
     ready = []
     inflight = []          # (handle, [requests])
+    cancels = sorted(((t, rid) for rid, t in (cancel_at or {}).items()), reverse=True)
     st = ServeStats()
     t0 = clock()
     while pending or waiting or ready or inflight:
         now = clock() - t0
         while pending and pending[0].arrival <= now:
             waiting.append(pending.popleft())
+        while cancels and cancels[-1][0] <= now:
+            r = reqs[cancels.pop()[1]]
+            if r.cancelled or r.done >= 0:
+                continue
+            r.cancelled = True
+            st.cancelled += 1
+            if r in ready:                 # admitted, not launched: give the slot back now
+                ready.remove(r)
+                admission.release(r.slot, executor.cost(r))
+            elif r in waiting:
+                waiting.remove(r)
+            elif r in pending:
+                pending.remove(r)
         for h, rs in list(inflight):
             if h.done():
                 t = clock() - t0
                 for r in rs:
                     r.done = t
-                    st.latencies_ms.append((t - r.arrival) * 1e3)
-                    st.rows += r.n
+                    if not r.cancelled:
+                        st.latencies_ms.append((t - r.arrival) * 1e3)
+                        st.rows += r.n
                     admission.release(r.slot, executor.cost(r))
                 h.close()
                 inflight.remove((h, rs))

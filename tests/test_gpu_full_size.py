@@ -6,9 +6,13 @@ properties that hold at any size, with checks done by plain torch reductions
 on the device:
 
 * star pipeline at scale (fact 600M rows, dimension 20M rows, 3,000 groups),
-  in the launch configuration bench.py times: sampled groups against the
-  oracle over the full input; sum of COUNT = rows passing the filter; sum of
-  SUM(price*qty) and the global MIN / MAX over those rows;
+  in the launch configuration bench.py times: every group's four aggregates
+  against a plain torch group-by of the same rows on the device, and three
+  groups against the oracle run over the full input; the same for the
+  25,002-group variant (attr in [0, 8334): the direct array in HBM);
+* the batched form in the launch shape bench.py times (262,144-row work
+  items, shared-memory group tables, a CUDA graph): several hundred small
+  pipelines and two of 5M+ rows, every output against the oracle;
 * partition of 600M (int64 key, int64 payload) pairs at fan-out 256 / 1024 /
   4096: offsets, payloads a permutation of the row ids, key/payload pairs
   intact, input order inside every destination, and the destination of
@@ -80,37 +84,125 @@ def _filtered_totals(fact, mask):
 
 
 # ---------------------------------------------------------------- star pipeline at scale
-def test_star_pipeline_600M(ctx):
+@pytest.fixture(scope="module")
+def star600():
     dev = torch.device("cuda", 0)
-    n_fact, n_dim = 600_000_000, 20_000_000
-    dim = datagen.star_dim(n_dim, 1000, seed=1, device=dev)
-    fact = datagen.star_fact(n_fact, n_dim, seed=1, device=dev)
+    dim = datagen.star_dim(20_000_000, 1000, seed=1, device=dev)
+    fact = datagen.star_fact(600_000_000, 20_000_000, seed=1, device=dev)
+    half = dim["key"][: 10_000_000].contiguous()
+    member = torch.zeros(20_000_000, dtype=torch.bool, device=dev)
+    member[half.long()] = True
+    yield fact, dim, half, member
+    del fact, dim, half, member
+    torch.cuda.empty_cache()
+
+
+def _torch_star_groups(fact, dim, n_attr, date_lt=DATE_LT, chunk=100_000_000):
+    """Every group of group-by(flag, attr)(join(filter(fact), dim)) with
+    SUM(price*qty), COUNT, MIN(price), MAX(price), by plain torch reductions
+    on the device (index_add_, bincount, scatter_reduce), in ascending key
+    order.  The dimension's keys are a permutation of 0..n-1 (checked), so
+    attr of a foreign key is one gather."""
+    dev = fact["fk"].device
+    nd = dim["key"].numel()
+    assert torch.equal(torch.sort(dim["key"]).values, torch.arange(nd, dtype=torch.int32, device=dev))
+    attr_of = torch.empty(nd, dtype=torch.int64, device=dev)
+    attr_of[dim["key"].long()] = dim["attr"].long()
+    G = 3 * n_attr
+    s = torch.zeros(G, dtype=torch.int64, device=dev)
+    c = torch.zeros(G, dtype=torch.int64, device=dev)
+    mn = torch.full((G,), 2 ** 63 - 1, dtype=torch.int64, device=dev)
+    mx = torch.full((G,), -2 ** 63, dtype=torch.int64, device=dev)
+    n = fact["fk"].numel()
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        m = fact["date"][a:b] < date_lt
+        gid = fact["flag"][a:b][m].long() * n_attr + attr_of[fact["fk"][a:b][m].long()]
+        price = fact["price"][a:b][m]
+        s.index_add_(0, gid, price * fact["qty"][a:b][m].long())
+        c += torch.bincount(gid, minlength=G)
+        mn.scatter_reduce_(0, gid, price, "amin")
+        mx.scatter_reduce_(0, gid, price, "amax")
+        del m, gid, price
+    live = torch.nonzero(c).flatten()
+    keys = ((live // n_attr) << 32) | (live % n_attr)
+    return keys.cpu().numpy(), [x[live].cpu().numpy() for x in (s, c, mn, mx)]
+
+
+def _run_star600(ctx, fact, dim, expected):
     d = qe.pipeline_desc([fact[c] for c in COLS], [(1, qe.LT, DATE_LT)], fk_col=0, dim_key=dim["key"],
                          dim_payload=dim["attr"], key_hi_col=4, key_lo_col=qe.JOIN_PAYLOAD, aggs=STAR_AGGS,
-                         expected_groups=3000, est_selectivity=DATE_LT / 2557, key_range=((0, 2), None))
-    g = qe.qe_pipeline(ctx, d, 4096)
-    got = _Groups(g)
-    assert len(got) == 3000
+                         expected_groups=expected, est_selectivity=DATE_LT / 2557, key_range=((0, 2), None))
+    return _Groups(qe.qe_pipeline(ctx, d, 4096 if expected <= 4096 else 32768))
 
-    # properties over all rows (every foreign key has a dimension row)
-    mask = fact["date"] < DATE_LT
-    rows, s, mn, mx = _filtered_totals(fact, mask)
-    del mask
-    assert got.total(1) == rows
-    assert got.total(0) == s
-    assert int(got.aggs[2].min()) == mn
-    assert int(got.aggs[3].max()) == mx
 
+def _assert_all_groups(got, keys, aggs):
+    assert len(got) == len(keys)
+    assert np.array_equal(got.keys, keys)
+    for a, (x, y) in enumerate(zip(got.aggs, aggs)):
+        assert np.array_equal(x, y), a
+
+
+def test_star_pipeline_600M(ctx, star600):
+    """The step's pipeline (bench.py's launch configuration): all 3,000
+    groups exactly, and three against the oracle over the full input."""
+    fact, dim, _, _ = star600
+    got = _run_star600(ctx, fact, dim, 3000)
+    keys, aggs = _torch_star_groups(fact, dim, 1000)
+    assert len(keys) == 3000
+    _assert_all_groups(got, keys, aggs)
     # sampled groups against the oracle over the full input
     host = [fact[c].cpu().numpy() for c in COLS]
     dk, da = dim["key"].cpu().numpy(), dim["attr"].cpu().numpy()
     q = O.Query(preds=[O.Pred(1, O.LT, DATE_LT)], fk_col=0, key_hi_col=4, key_lo_col=O.JOIN_PAYLOAD, aggs=O_AGGS)
     rng = np.random.default_rng(11)
-    keys = got.keys
     for gk in [int(keys[0]), int(keys[-1]), int(keys[rng.integers(1, len(keys) - 1)])]:
         cnt, ref = O.pipeline_group(host, q, gk, dk, da)
         assert cnt == got[gk][1]
         assert tuple(int(x) for x in ref) == got[gk], gk
+
+
+def test_star_pipeline_600M_25k_groups(ctx, star600):
+    """bench.py's 25K-group variant: the same fact table against a 20M-row
+    dimension whose attr is in [0, 8334), 25,002 groups in an HBM direct
+    array; every group exactly."""
+    fact, _, _, _ = star600
+    dim25 = datagen.star_dim(20_000_000, 8334, seed=1, device=fact["fk"].device)
+    got = _run_star600(ctx, fact, dim25, 25002)
+    keys, aggs = _torch_star_groups(fact, dim25, 8334)
+    assert len(keys) == 25002
+    _assert_all_groups(got, keys, aggs)
+    del dim25
+
+
+# ---------------------------------------------------------------- batched form in the bench's shape
+def test_batch_bench_launch_shape(ctx):
+    """The batched form as bench.py launches it: 262,144-row work items,
+    shared-memory group tables, one CUDA graph; 400 pipelines of 1K-100K
+    fact rows (log-uniform) with a 5M- and a 7M-row pipeline among them,
+    dimension rows = fact rows / 10; every output against the oracle."""
+    from paper_2506_09226_gb300 import batch as B
+    sizes = datagen.log_uniform_sizes(400, 1e3, 1e5, seed=44)
+    sizes[37], sizes[251] = 5_000_000, 7_000_003
+    w = datagen.batch_star(sizes, B.N_ATTR, seed=44)
+    wd = {"fact": {c: t.cuda() for c, t in w["fact"].items()}, "dim": {c: t.cuda() for c, t in w["dim"].items()},
+          **{k: w[k] for k in ("fact_off", "dim_off", "sizes", "dim_sizes")}}
+    outs = B.BatchOutputs(len(sizes), B.CAPACITY, torch.device("cuda"))
+    descs = B.star_descs(wd)
+    b = qe.Batch(ctx, descs, outs.structs, qe.qe_batch_opts(0, 1 << 18, 0, 1))
+    b.launch()
+    ctx.sync_status()
+    b.destroy()
+    q = O.Query(preds=[O.Pred(1, O.LT, B.DATE_LT)], fk_col=0, key_hi_col=4, key_lo_col=O.JOIN_PAYLOAD, aggs=O_AGGS)
+    f, d = w["fact"], w["dim"]
+    for i, n in enumerate(sizes):
+        a, nd, bo = int(w["fact_off"][i]), int(w["dim_sizes"][i]), int(w["dim_off"][i])
+        ref = O.pipeline([f[c][a:a + int(n)].numpy() for c in COLS], q, d["key"][bo:bo + nd].numpy(),
+                         d["attr"][bo:bo + nd].numpy())
+        k, aggs = outs.groups(i)
+        assert np.array_equal(k, ref["keys"]), i
+        for x, y in zip(aggs, ref["aggs"]):
+            assert np.array_equal(x, y), i
 
 
 # ---------------------------------------------------------------- partition at scale
@@ -240,19 +332,6 @@ def test_skew_pipeline_dictionary_codes(ctx, skew):
 
 
 # ---------------------------------------------------------------- join variants at scale
-@pytest.fixture(scope="module")
-def star600():
-    dev = torch.device("cuda", 0)
-    dim = datagen.star_dim(20_000_000, 1000, seed=1, device=dev)
-    fact = datagen.star_fact(600_000_000, 20_000_000, seed=1, device=dev)
-    half = dim["key"][: 10_000_000].contiguous()
-    member = torch.zeros(20_000_000, dtype=torch.bool, device=dev)
-    member[half.long()] = True
-    yield fact, dim, half, member
-    del fact, dim, half, member
-    torch.cuda.empty_cache()
-
-
 def test_semi_anti_single_table_600M(ctx, star600):
     """Filter + semi- / anti-join against half the dimension's keys + group-by
     flag, and the same filter + group-by with no join: every group's four

@@ -4,7 +4,8 @@ Each case applies one plausible mistake to a copy of oracle/qe_oracle.c (a
 boundary off by one, a dropped step of the hash, a wrong index, a flipped
 sign, swapped key halves, an unstable placement, a dropped predicate term, a
 wrong payload index, a flipped or shortened membership test, a swapped join
-kind, a zero-extended group key), compiles it, and runs
+kind, a zero-extended group key, an integer or single-precision average),
+compiles it, and runs
 tests/test_oracle_pins.py against it; the pin suite must fail for every
 mutant.
 """
@@ -45,6 +46,10 @@ MUTANTS = {
     "semi_last_key": ("int found = lo < nb && b[lo] == k;", "int found = lo + 1 < nb && b[lo] == k;"),
     "pipeline_kind": ("join_kind == 2, rows);", "join_kind == 1, rows);"),
     "key_zero_extend": ("    if (!has_hi) return lo;", "    if (!has_hi) return (int64_t)(uint32_t)lo;"),
+    "avg_int_div": ("out[g] = (double)sum[g] / (double)count[g];", "out[g] = (double)(sum[g] / count[g]);"),
+    "avg_float": ("out[g] = (double)sum[g] / (double)count[g];", "out[g] = (float)sum[g] / (float)count[g];"),
+    "avg_count_index": ("out[g] = (double)sum[g] / (double)count[g];",
+                        "out[g] = (double)sum[g] / (double)count[g > 0 ? g - 1 : 0];"),
     "radix_shift": ("return (int64_t)(((uint64_t)key >> shift) & (fanout - 1));",
                     "return (int64_t)(((uint64_t)key >> (shift + 1)) & (fanout - 1));"),
 }

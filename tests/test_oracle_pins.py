@@ -547,6 +547,58 @@ def test_group_key_rule():
         assert [[int(a[i]) for a in r["aggs"]] for i in range(len(r["keys"]))] == [ref[k] for k in sorted(ref)]
 
 
+# ---------------------------------------------------------------- derived averages
+def test_avg_golden():
+    """oracle_avg against hand-worked cases (exact rational arithmetic):
+    halves, thirds, negative sums, sums past 2^53 that round before the
+    division, a count-1 group with a sum near 2^62."""
+    g = json.load(open(os.path.join(GOLD, "avg_cases.json")))
+    sums = np.array([int(c["sum"]) for c in g["cases"]], np.int64)
+    cnts = np.array([int(c["count"]) for c in g["cases"]], np.int64)
+    got = O.avg(sums, cnts)
+    for c, x in zip(g["cases"], got):
+        assert float(x).hex() == float.fromhex(c["avg_hex"]).hex(), c["note"]
+
+
+def test_avg_within_two_roundings():
+    """For random sums over the whole int64 range and counts up to 10^9:
+    the average is within two double roundings (2^-52 relative) of the exact
+    quotient, and equal to the correctly rounded quotient whenever the sum
+    converts to double exactly (|sum| <= 2^53)."""
+    from fractions import Fraction
+    rng = np.random.default_rng(8)
+    mags = rng.integers(0, 63, 4000)
+    sums = np.array([int(rng.integers(-(1 << int(m)), 1 << int(m), endpoint=True)) if m else 0 for m in mags],
+                    np.int64)
+    cnts = rng.integers(1, 10 ** 9, 4000).astype(np.int64)
+    cnts[:500] = 1
+    got = O.avg(sums, cnts)
+    for s, c, x in zip(sums.tolist(), cnts.tolist(), got.tolist()):
+        q = Fraction(s, c)
+        assert abs(Fraction(x) - q) <= abs(q) * Fraction(1, 1 << 52)
+        if abs(s) <= 1 << 53:
+            assert x == float(q)
+
+
+def test_avg_of_pipeline_groups():
+    """The average of SUM(price*qty) over COUNT for the tiny pipeline's
+    groups, and AVG(price) of a join-free pipeline against per-group means
+    taken with exact fractions."""
+    from fractions import Fraction
+    g = json.load(open(os.path.join(GOLD, "tiny_pipeline.json")))
+    e = g["expect"]
+    assert O.avg(e["sum"], e["count"]).tolist() == [950.0, 1000.0, 600.0, 800.0]
+    rng = np.random.default_rng(4)
+    key = rng.integers(0, 7, 500).astype(np.int32)
+    price = rng.integers(100, 10 ** 7, 500).astype(np.int64)
+    q = O.Query(preds=[], fk_col=-1, key_hi_col=-1, key_lo_col=0, aggs=[(O.SUM, 1, -1), (O.COUNT, -1, -1)])
+    r = O.pipeline([key, price], q)
+    got = O.avg(r["aggs"][0], r["aggs"][1])
+    for k, x in zip(r["keys"].tolist(), got.tolist()):
+        rows = price[key == k].tolist()
+        assert x == float(Fraction(sum(rows), len(rows)))
+
+
 # ---------------------------------------------------------------- planted mistakes
 def test_pins_catch_planted_mistakes():
     """The brute-force pins reject plausible oracle mistakes: a dropped

@@ -106,3 +106,47 @@ def test_row_cap_keeps_rounds_short():
     adm = serve.Admission(budget_bytes=10 ** 9, slots=100)
     serve.serve_loop(trace, ex, adm, clock=clock, idle_sleep=0, row_cap=100)
     assert ex.rounds == [[0, 1], [2], [3, 4, 5]]        # oldest first; the big one alone
+
+
+def test_cancel_frees_slot_and_budget():
+    """Cancellation at each stage: before admission (dropped, never run),
+    admitted but not launched (slot and budget returned at once, and a
+    waiting request takes them), and in flight (kept until its round
+    completes, then released, its result not counted)."""
+    clock = FakeClock()
+    # rounds of one request (row_cap): request 0 runs first; 1 and 2 wait
+    trace = [datagen.Arrival(0.0, 0, 0, 10, 100) for _ in range(4)]
+    ex = FakeExecutor(clock, dur=0.05, cost=100)
+    adm = serve.Admission(budget_bytes=200, slots=2)        # two in flight at most
+    released = []
+    orig = adm.release
+
+    def spy(slot, cost):
+        released.append((round(clock.t, 4), slot))
+        orig(slot, cost)
+    adm.release = spy
+    # 0 and 1 are admitted at once; 0 launches, 1 waits in `ready` behind the
+    # running round; cancel 1 then (its slot goes to 2); cancel 3 before it
+    # is admitted; cancel 0 while its round runs
+    st = serve.serve_loop(trace, ex, adm, clock=clock, idle_sleep=0, row_cap=10,
+                          cancel_at={1: 0.01, 3: 0.011, 0: 0.02})
+    assert st.cancelled == 3
+    launched = [r for rd in ex.rounds for r in rd]
+    assert 1 not in launched and 3 not in launched          # never ran
+    assert 0 in launched and 2 in launched
+    assert len(st.latencies_ms) == 1 and st.rows == 10       # only request 2 counts
+    assert adm.used == 0 and adm.busy == 0                  # everything released
+    # request 1's slot came back before round 0 finished, and request 2 took it
+    t_rel1 = [t for t, s in released][0]
+    assert t_rel1 < 0.05
+    assert ex.rounds[0] == [0] and ex.rounds[1] == [2]
+
+
+def test_cancel_unknown_or_finished_is_ignored():
+    clock = FakeClock()
+    trace = [datagen.Arrival(0.0, 0, 0, 10, 100) for _ in range(3)]
+    ex = FakeExecutor(clock, dur=0.001, cost=1)
+    adm = serve.Admission(budget_bytes=10, slots=10)
+    st = serve.serve_loop(trace, ex, adm, clock=clock, idle_sleep=0, cancel_at={2: 5.0})
+    assert st.cancelled == 0 and len(st.latencies_ms) == 3
+    assert adm.used == 0 and adm.busy == 0
