@@ -385,8 +385,8 @@ def run_qe(args):
         except qe.QeError as e:   # a library error in an extra leg is reported, not fatal to the line
             extras["variants"] = {"error": str(e)}
             torch.cuda.empty_cache()
-    if "extras" in args.forms:
-        extras["skew_40m_groups"] = run_skew(args, qe, ctx, dev, stream, peak, max(3, args.steps // 2))
+    if "extras" in args.forms or "skew" in args.forms:
+        extras["skew_40m_groups"] = run_skew(args, qe, ctx, dev, stream, peak, max(9, args.steps // 2))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -475,11 +475,23 @@ def run_extras(args, qe, ctx, fact, dim, key, pay, okeys, opay, dev, stream, pea
     return out
 
 
+SKEW_SWEEP = (0.01, 0.05, 0.10, 0.25, 0.50, 0.75, 0.90)
+
+
 def run_skew(args, qe, ctx, dev, stream, peak, it):
     """Skewed, high-cardinality pipeline: 300M fact rows with Zipf(1.1) foreign
-    keys over a 50M-row dimension, grouped on ~40M distinct int64 keys (HBM
-    hash table), at 1 %, 50 % and 90 % selectivity.  hbm_frac counts the
-    28 bytes each fact row reads (fk, date, price, qty, int64 group key)."""
+    keys over a 50M-row dimension, grouped on ~40M distinct int64 keys, with
+    the selectivity swept over 1 .. 90 % through date < c and through a
+    dictionary-code predicate code < K.  Groups this many take the
+    partitioned group-by (count, scan, scatter of 24-byte rows into parts,
+    aggregation of part after part in L2-resident hash windows).  hbm_frac
+    counts the 28 bytes each fact row reads (fk, date, price, qty, int64
+    group key; code instead of date for the code sweep); part_bytes states
+    the extra traffic of the partition round trip (the count pass reads the
+    8-byte key of every row; each survivor is written and read back as 24
+    bytes).  Also timed: the 50 % point through the direct HBM hash table
+    (the path the partitioning replaces) and the group-by on 10^6
+    dictionary codes."""
     from paper_2506_09226_gb300 import datagen
     n_fact = max(1, args.fact_rows // 2)
     n_dim = max(1, args.dim_rows * 5 // 2)
@@ -488,22 +500,59 @@ def run_skew(args, qe, ctx, dev, stream, peak, it):
     fact = datagen.star_fact(n_fact, n_dim, seed=3, device=dev, zipf_s=1.1, n_codes=1_000_000,
                              n_gkeys=max(1, n_fact * 2 // 15))
     log(f"skew workload generated in {time.time() - t0:.1f}s")
-    cols = [fact[c] for c in ("fk", "date", "price", "qty", "gkey")]
+    cols = [fact[c] for c in ("fk", "date", "price", "qty", "gkey", "code")]
     aggs = [(qe.SUM, 2, 3), (qe.COUNT, -1, -1), (qe.MIN, 2, -1), (qe.MAX, 2, -1)]
     cap = max(1, n_fact * 2 // 15)
     groups, gout = qe.alloc_groups(cap, 4, dev)
-    res = {"fact_rows": n_fact, "dim_rows": n_dim}
-    for sel in (0.01, 0.50, 0.90):
-        c = int(round(sel * datagen.DATE_SPAN))
-        d = qe.pipeline_desc(cols, [(1, qe.LT, c)], fk_col=0, dim_key=dim["key"], dim_payload=dim["attr"],
-                             key_hi_col=-1, key_lo_col=4, aggs=aggs, expected_groups=cap, est_selectivity=sel)
-        fn = lambda: qe.qe_pipeline(ctx, d, cap, check=False, out=(groups, gout))  # noqa: E731
+    res = {"fact_rows": n_fact, "dim_rows": n_dim, "groups_pool": cap}
+    phases = ("part_count", "part_scatter_rows", "part_fold", "pipeline")
+
+    def one(pred, key_col, capacity, sel_est):
+        d = qe.pipeline_desc(cols, [pred], fk_col=0, dim_key=dim["key"], dim_payload=dim["attr"],
+                             key_hi_col=-1, key_lo_col=key_col, aggs=aggs, expected_groups=capacity,
+                             est_selectivity=sel_est)
+        fn = lambda: qe.qe_pipeline(ctx, d, capacity, check=False, out=(groups, gout))  # noqa: E731
         fn()
         ctx.sync_status()
-        ms = timed(fn, max(3, it // 3), stream)
-        res[f"{int(sel * 100)}%"] = {"ms": ms, "rows_per_s": n_fact / (ms * 1e-3),
-                                     "ngroups": int(groups.ngroups.item()),
-                                     "hbm_frac": round(28 * n_fact / (ms * 1e-3) / 1e9 / peak, 4)}
+        ctx.profile(True)
+        ctx.profile_reset()
+        iters = max(3, it // 3)
+        ms = timed(fn, iters, stream)
+        kern = {}
+        for ph in phases:
+            c, tot = ctx.profile_read(ph)
+            if c:
+                kern[ph] = round(tot / c, 4)
+        ctx.profile(False)
+        ctx.sync_status()
+        ng = int(groups.ngroups.item())
+        return ms, kern, ng
+
+    for colname, ci, span in (("date", 1, datagen.DATE_SPAN), ("code", 5, 1_000_000)):
+        sweep = {}
+        for sel in SKEW_SWEEP:
+            c = int(round(sel * span))
+            ms, kern, ng = one((ci, qe.LT, c), 4, cap, sel)
+            nsurv = None
+            if "part_count" in kern:
+                nsurv = int((fact[colname] < c).sum().item())
+            sweep[f"{int(round(sel * 100))}%"] = {
+                "ms": ms, "rows_per_s": n_fact / (ms * 1e-3), "ngroups": ng,
+                "hbm_frac": round(28 * n_fact / (ms * 1e-3) / 1e9 / peak, 4), "kernels_ms": kern,
+                "part_bytes": (8 * n_fact + 48 * nsurv) if nsurv is not None else 0}
+        res[f"sweep_{colname}"] = sweep
+    # the direct HBM hash table at 50 %, for comparison
+    ctx.set_tuning("gb_partition", 1)
+    try:
+        ms, kern, ng = one((1, qe.LT, int(round(0.5 * datagen.DATE_SPAN))), 4, cap, 0.5)
+        res["direct_hbm_table_50%"] = {"ms": ms, "rows_per_s": n_fact / (ms * 1e-3), "ngroups": ng,
+                                       "hbm_frac": round(28 * n_fact / (ms * 1e-3) / 1e9 / peak, 4)}
+    finally:
+        ctx.set_tuning("gb_partition", 0)
+    # group-by on the 10^6 dictionary codes at 50 % (a hash table of ~84 MB)
+    ms, kern, ng = one((1, qe.LT, int(round(0.5 * datagen.DATE_SPAN))), 5, 1_000_000, 0.5)
+    res["codes_1m_groups_50%"] = {"ms": ms, "rows_per_s": n_fact / (ms * 1e-3), "ngroups": ng,
+                                  "hbm_frac": round(24 * n_fact / (ms * 1e-3) / 1e9 / peak, 4), "kernels_ms": kern}
     ctx.sync_status()
     del dim, fact, cols, groups, gout
     torch.cuda.empty_cache()
@@ -521,6 +570,10 @@ def run_variants(args, qe, ctx, dev, stream, peak, it):
       single_table: filter + group-by flag, no join (fk_col = -1): 17 B per row;
       inner_probe: stand-alone probe of the dimension's dense table over the
         filter's selection vector: 4 B selection + 4 B key + 8 B per output;
+      open_20m_* / open_50m_*: the same build and probe with the table in the
+        open-addressing layout, for the 20M-row dimension and for a 50M-row
+        one probed by a foreign key uniform over its keys: build 8 B in per
+        row + 8 B per slot written; probe as inner_probe;
       semi_join / anti_join: stand-alone, over the filter's selection vector:
         4 B selection + 4 B key + 4 B per output position;
       multi_build / multi_probe: many-to-many join against a partsupp-shaped
@@ -596,6 +649,34 @@ def run_variants(args, qe, ctx, dev, stream, peak, it):
     k = int(ocnt.item())
     res["inner_probe"] = entry(ms, nsel, 8 * nsel + 8 * k, outputs=k)
     hd.destroy()
+
+    # open addressing at scale: the dimension's 20M keys, and 50M keys probed
+    # by a foreign key uniform over them, in the open-addressing layout
+    # (linear probing, 8-byte slots, CAS insert) instead of the dense array
+    g50 = torch.Generator(device=dev)
+    g50.manual_seed(50)
+    for nk in (nd, nd * 5 // 2):
+        dk = dim if nk == nd else datagen.star_dim(nk, 1000, seed=6, device=dev)
+        pk = fact["fk"] if nk == nd else torch.randint(0, nk, (n,), generator=g50, device=dev, dtype=torch.int32)
+
+        def obuild():
+            qe.qe_join_build(ctx, dk["key"], dk["attr"], layout=qe.HT_OPEN, key_range=(0, nk - 1),
+                             check=False).destroy()
+        obuild()
+        ctx.sync_status()
+        bms = timed(obuild, it, stream)
+        ho = qe.qe_join_build(ctx, dk["key"], dk["attr"], layout=qe.HT_OPEN, key_range=(0, nk - 1))
+        fn = lambda: qe.qe_join_probe(ctx, ho, pk, sel, n=nsel, capacity=nsel, out_rows=out_rows,  # noqa: E731
+                                      out_payload=out_pay, out_count=ocnt, check=False)
+        fn()
+        ctx.sync_status()
+        ms = timed(fn, it, stream)
+        k = int(ocnt.item())
+        tag = f"open_{nk // 1_000_000}m"
+        res[tag + "_build"] = entry(bms, nk, 8 * nk + 8 * ho.info().slots, slots=int(ho.info().slots))
+        res[tag + "_probe"] = entry(ms, nsel, 8 * nsel + 8 * k, outputs=k)
+        ho.destroy()
+        del dk, pk
 
     # stand-alone semi- and anti-join
     hs = qe.qe_join_build_set(ctx, half)

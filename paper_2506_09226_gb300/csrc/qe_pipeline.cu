@@ -306,6 +306,21 @@ qe_status pipeline_launch(qe_ctx *ctx, PipeSpec &P, const PipePlan &plan, const 
     return launch(ctx, k_pipeline<2>, P, plan.T, plan.table, PT * 2, s);
 }
 
+qe_status pipeline_partitioned(qe_ctx *ctx, PipeSpec &P, const qe_groups_out *out, int64_t groups, cudaStream_t s);
+
+// Whether a pipeline whose groups go to the HBM hash table takes the
+// partitioned path: when tuned so, or (auto) when that table would be far
+// larger than L2 (random read-modify-writes in DRAM) and the input is large
+// enough to amortise the extra passes.
+static bool use_partitioned(qe_ctx *ctx, const PipeSpec &P, int64_t capacity)
+{
+    if (ctx->tune_gb_partition == 1 || P.n == 0) return false;
+    if (ctx->tune_gb_partition == 2) return true;
+    uint64_t want = static_cast<uint64_t>(capacity > 32 ? capacity : 32) * 2, slots = 64;
+    while (slots < want) slots <<= 1;
+    return slots * (1 + P.ops.n) * 8 > (256ull << 20) && P.n >= (int64_t(1) << 22);
+}
+
 extern "C" qe_status qe_pipeline(qe_ctx *ctx, const qe_pipeline_desc *desc, const qe_groups_out *out, void *stream)
 {
     if (!ctx) return QE_ERR_INVALID_ARG;
@@ -344,6 +359,16 @@ extern "C" qe_status qe_pipeline(qe_ctx *ctx, const qe_pipeline_desc *desc, cons
             if (e != cudaSuccess) st = qe_cuda_fail(ctx, e, "pipeline: dense table");
         }
         P.gdense = static_cast<unsigned long long *>(gd);
+    }
+    // Groups that only fit an HBM hash table far larger than L2: partition
+    // the rows on the key's hash and aggregate each part in L2 (qe_pipe_part.cu).
+    if (st == QE_OK && plan.T.mode == TM_GLOBAL_HASH && use_partitioned(ctx, P, out->capacity)) {
+        P.g = GTable{};
+        P.g.st = ctx->dstat;
+        P.g.capacity = out->capacity;
+        st = pipeline_partitioned(ctx, P, out, out->capacity, s);
+        if (built) qe_join_destroy(ctx, built, s);
+        return st;
     }
     GroupTableHost t;
     if (st == QE_OK) st = gt_create(ctx, out->capacity, P.ops.n, t, s);

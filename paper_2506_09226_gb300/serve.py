@@ -341,8 +341,11 @@ def default_shapes(scale: float = 1.0):
 
 
 def bench_serve(ctx, device, stream, peak_gbs: float, duration_s: float = 10.0, rate: float = 2000.0,
-                scale: float = 1.0, serial_s: float = 1.0, log=print, seed: int = 5) -> dict:
-    """Served form on a Poisson trace against serial per-request replays."""
+                scale: float = 1.0, serial_s: float = 1.0, log=print, seed: int = 5,
+                sat_rates=(1000.0, 2000.0, 4000.0, 8000.0), sat_seconds: float = 1.0) -> dict:
+    """Served form on a Poisson trace against serial per-request replays, then
+    a saturation sweep over rising arrival rates (each a trace of
+    sat_seconds) against serial fused replay."""
     torch.cuda.empty_cache()
     tables = ResidentTables(ctx, default_shapes(scale), device, log=log)
     resident = tables.bytes()
@@ -377,6 +380,19 @@ def bench_serve(ctx, device, stream, peak_gbs: float, duration_s: float = 10.0, 
         torch.cuda.current_stream().synchronize()
     fused_serial = serial_replay(prefix, fused).summary()
     ctx.sync_status()
+    # saturation sweep: the arrival rate rising past what serial fused
+    # execution sustains, served (continuous batching) against serial fused
+    # replay of the same trace
+    sweep = {}
+    for lam in sat_rates:
+        tr = datagen.poisson_trace(sat_seconds, lam, tables.rows, seed=seed + int(lam), n_lo=1e4,
+                                   n_hi=min(5e8, min(tables.rows)))
+        sv = serve_loop(tr, ex, Admission(slots * REQ_BYTES, slots), row_cap=ROW_CAP).summary()
+        sf = serial_replay(tr, fused).summary()
+        ctx.sync_status()
+        sweep[str(int(lam))] = {"requests": len(tr), "served": {k: sv[k] for k in ("p50_ms", "p99_ms", "rows_per_s")},
+                                "serial_fused": {k: sf[k] for k in ("p50_ms", "p99_ms", "rows_per_s")}}
+        log(f"saturation {lam:.0f} req/s: served p99 {sv['p99_ms']:.1f} ms, serial fused p99 {sf['p99_ms']:.1f} ms")
     tables.close()
     del scratch, outs
     torch.cuda.empty_cache()
@@ -384,5 +400,6 @@ def bench_serve(ctx, device, stream, peak_gbs: float, duration_s: float = 10.0, 
             "served": served,
             "prefix_s": serial_s, "served_prefix": st_pre, "serial_per_operator_prefix": per_op,
             "serial_fused_prefix": fused_serial,
+            "saturation": {"trace_s": sat_seconds, "rates": sweep},
             "p99_speedup_vs_per_operator": per_op["p99_ms"] / max(st_pre["p99_ms"], 1e-9),
             "throughput_vs_per_operator": st_pre["rows_per_s"] / max(per_op["rows_per_s"], 1e-9)}
