@@ -53,7 +53,8 @@ typedef enum {
     QE_ERR_RESERVED_KEY = 5,  /* key equal to the table's empty-slot marker  */
     QE_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up          */
     QE_ERR_CUDA = 7,          /* a CUDA runtime call failed                  */
-    QE_ERR_NO_DEVICE = 8      /* no usable sm_103a device                     */
+    QE_ERR_NO_DEVICE = 8,     /* no usable sm_103a device                     */
+    QE_ERR_DEVICE_CHECK = 9   /* a bounds check of the checked build failed  */
 } qe_status;
 
 /* Element type of a column; the value is the element size in bytes. */
@@ -154,6 +155,15 @@ void qe_debug_set_spin_limit(qe_ctx *ctx, int64_t iterations);
  *                   write-combining one.
  * Unknown names return QE_ERR_INVALID_ARG. */
 qe_status qe_set_tuning(qe_ctx *ctx, const char *name, int64_t value);
+
+/* Nonzero when this library is the bounds-checked build (libqe_checked.so,
+ * compiled with QE_CHECKED): its kernels test the indices of their scatter
+ * writes, segment ranges and shared-memory table slots against the bounds
+ * they derive them from, and instead of an access out of bounds record
+ * QE_ERR_DEVICE_CHECK (with the offending index as the required size) and
+ * skip it.  It stands in for a memory checker; the plain build omits the
+ * tests. */
+int qe_build_checked(void);
 
 /* Number of kernels this context has launched so far (host-side counter). */
 int64_t qe_launch_count(const qe_ctx *ctx);
@@ -489,6 +499,11 @@ typedef struct {
     int32_t tile_rows;       /* fact rows per work item            */
     int32_t smem_slots;      /* shared-memory group-table slots    */
     int32_t use_graph;       /* capture the launch in a CUDA graph */
+    int64_t build_ahead_bytes;  /* join-table bytes built ahead of their
+                                   probes (0 = 32 MB): the work items of a
+                                   pipeline's in-kernel build are placed that
+                                   far ahead of its probe items, so tables are
+                                   probed while still in L2 */
 } qe_batch_opts;
 
 /* Plan a batch of n pipelines that share one persistent launch: every

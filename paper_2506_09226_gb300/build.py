@@ -1,9 +1,12 @@
 """Build libqe.so (the CUDA operator library) in-tree for sm_103a.
 
 Each translation unit under csrc/ is compiled by its own nvcc process (in
-parallel), then linked into paper_2506_09226_gb300/libqe.so.  Objects go to
-paper_2506_09226_gb300/_build/.  A unit is rebuilt when it or any header it
-may include is newer than its object.
+parallel), then linked into paper_2506_09226_gb300/libqe.so.  The same units
+are also compiled with -DQE_CHECKED into libqe_checked.so, the bounds-checked
+build whose kernels test their write indices and report QE_ERR_DEVICE_CHECK
+instead of writing out of bounds.  Objects go to
+paper_2506_09226_gb300/_build/ (and _build/checked/).  A unit is rebuilt when
+it or any header it may include is newer than its object.
 """
 from __future__ import annotations
 
@@ -18,6 +21,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libqe.so")
+LIB_CHECKED = os.path.join(PKG, "libqe_checked.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -43,20 +47,25 @@ def _stale(obj: str, src: str, hdr_mtime: float) -> bool:
     return m < os.path.getmtime(src) or m < hdr_mtime
 
 
-def build(verbose: bool = False, extra_flags: list | None = None) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, extra_flags: list | None = None, checked: bool = True) -> str:
+    """Compile and link libqe.so, and (checked=True) libqe_checked.so; the
+    units of both are compiled in one pool.  Returns the path of libqe.so."""
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdr_mtime = max([os.path.getmtime(h) for h in _headers()] + [0.0])
     nvcc = _nvcc()
-    flags = NVCC_FLAGS + (extra_flags or [])
+    variants = [(BUILD, LIB, NVCC_FLAGS + (extra_flags or []))]
+    if checked:
+        variants.append((os.path.join(BUILD, "checked"), LIB_CHECKED, NVCC_FLAGS + ["-DQE_CHECKED"] + (extra_flags or [])))
     jobs = []
-    for src in srcs:
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        if _stale(obj, src, hdr_mtime):
-            jobs.append((src, obj))
+    for bdir, _, flags in variants:
+        os.makedirs(bdir, exist_ok=True)
+        for src in srcs:
+            obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
+            if _stale(obj, src, hdr_mtime):
+                jobs.append((src, obj, flags))
 
     def compile_one(job):
-        src, obj = job
+        src, obj, flags = job
         cmd = [nvcc] + flags + ["-c", src, "-o", obj + ".tmp"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -68,13 +77,14 @@ def build(verbose: bool = False, extra_flags: list | None = None) -> str:
         for out in ex.map(compile_one, jobs):
             if verbose and out:
                 sys.stderr.write(out)
-    objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in srcs]
-    if jobs or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        tmp = LIB + f".tmp{os.getpid()}"
-        r = subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs, capture_output=True, text=True)
-        if r.returncode != 0:
-            raise RuntimeError(f"link failed:\n{r.stderr}")
-        os.replace(tmp, LIB)
+    for bdir, lib, _ in variants:
+        objs = [os.path.join(bdir, os.path.basename(s)[:-3] + ".o") for s in srcs]
+        if not os.path.exists(lib) or os.path.getmtime(lib) < max(os.path.getmtime(o) for o in objs):
+            tmp = lib + f".tmp{os.getpid()}"
+            r = subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs, capture_output=True, text=True)
+            if r.returncode != 0:
+                raise RuntimeError(f"link failed:\n{r.stderr}")
+            os.replace(tmp, lib)
     return LIB
 
 

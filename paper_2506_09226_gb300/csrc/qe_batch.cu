@@ -10,8 +10,9 @@
 //     table, flushed into the pipeline's HBM tables at the end of the item;
 //   - the block that finishes a pipeline's last probe item compacts that
 //     pipeline's groups into its output.
-// Blocks claim items in order from one atomic counter, and every build item
-// precedes every probe item in that order, so a probe item waits (bounded,
+// Blocks claim items in order from one atomic counter; a pipeline's build
+// items are placed a little ahead of its probe items (so its table is still
+// in L2 when probed) and always before them, so a probe item waits (bounded,
 // QE_ERR_TIMEOUT on expiry) only for builds that running blocks already hold.
 // Tables built inside the kernel are read with L2-only loads.
 #include <vector>
@@ -391,14 +392,31 @@ extern "C" qe_status qe_batch_create(qe_ctx *ctx, const qe_pipeline_desc *descs,
     }
     const size_t counters_off = z_bytes;
     z_bytes += up(static_cast<size_t>(n) * 2 * sizeof(unsigned)) + 256;
-    // items: every build item, then every probe item
-    for (int i = 0; i < n; i++)
+    // Item order.  Build items run ahead of their pipeline's probe items by
+    // at most `ahead` bytes of join tables built but not yet probed (and at
+    // least one pipeline), so a table is probed while it still sits in L2
+    // instead of being written to and read back from DRAM: with every build
+    // first, 10,000 small tables would all be evicted before any probe.
+    // Every build item of a pipeline precedes its probe items, so a probe
+    // item waits only for items claimed before it.
+    auto push_builds = [&](int i) {
         for (int j = 0; j < pipes[i].nbuild; j++) {
             const int64_t r0 = static_cast<int64_t>(j) * BUILD_ROWS;
             items.push_back({i, 0, r0, std::min<int64_t>(descs[i].n_dim, r0 + BUILD_ROWS)});
         }
-    for (int i = 0; i < n; i++)
+    };
+    const size_t ahead = o.build_ahead_bytes > 0 ? static_cast<size_t>(o.build_ahead_bytes) : (size_t(32) << 20);
+    int next_build = 0;
+    size_t pending = 0;             // table bytes built and not yet probed
+    for (int i = 0; i < n; i++) {
+        while (next_build < n && (next_build <= i || pending + sz[next_build].pay + sz[next_build].bm <= ahead)) {
+            push_builds(next_build);
+            pending += sz[next_build].pay + sz[next_build].bm;
+            next_build++;
+        }
         for (int j = 0; j < pipes[i].nprobe; j++) items.push_back({i, 1, j, descs[i].n_fact});
+        pending -= sz[i].pay + sz[i].bm;
+    }
     const size_t pipes_bytes = up(sizeof(BatchPipe) * n), items_bytes = up(sizeof(BatchItem) * items.size());
 
     qe_batch *b = new qe_batch();

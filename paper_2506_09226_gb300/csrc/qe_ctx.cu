@@ -112,6 +112,8 @@ extern "C" qe_status qe_set_tuning(qe_ctx *ctx, const char *name, int64_t value)
         ctx->tune_force_generic = value != 0;
     } else if (n == "part_general") {
         ctx->tune_part_general = value != 0;
+    } else if (n == "l2_hint") {
+        ctx->tune_l2_hint = value != 0;
     } else if (n == "gb_partition") {
         if (value < 0 || value > 2) return qe_fail(ctx, QE_ERR_INVALID_ARG, "gb_partition must be 0, 1 or 2");
         ctx->tune_gb_partition = static_cast<int>(value);
@@ -126,6 +128,15 @@ extern "C" qe_status qe_set_tuning(qe_ctx *ctx, const char *name, int64_t value)
 }
 
 extern "C" int64_t qe_launch_count(const qe_ctx *ctx) { return ctx ? ctx->launches.load() : 0; }
+
+extern "C" int qe_build_checked(void)
+{
+#ifdef QE_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
+}
 
 extern "C" qe_status qe_profile_enable(qe_ctx *ctx, int on)
 {
@@ -192,6 +203,7 @@ static const char *status_name(int c)
     case QE_ERR_RESERVED_KEY: return "key equals the reserved empty-slot marker";
     case QE_ERR_TIMEOUT: return "bounded device wait expired";
     case QE_ERR_INVALID_ARG: return "build key outside the stated range";
+    case QE_ERR_DEVICE_CHECK: return "bounds check failed (index + 1 as required)";
     default: return "device error";
     }
 }

@@ -45,6 +45,7 @@ struct qe_ctx {
     int tune_part_general = 0;      // partition: skip the write-combining scatter
     int tune_gb_partition = 0;      // large HBM group tables: 0 auto, 1 never partition, 2 always
     int tune_gb_part_log2p = 0;     // parts of the partitioned group-by (log2; 0 = planned)
+    int tune_l2_hint = 0;           // star pipeline: L2 policies on fact loads and payload lookups
     bool profiling = false;
     std::mutex prof_mu;
     std::map<std::string, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>> prof;
@@ -114,6 +115,16 @@ __device__ __forceinline__ void dev_report(qe_dev_status *st, int code, int64_t 
                   static_cast<unsigned long long>(required));
 }
 
+// Bounds check of the checked build (QE_CHECKED): true when `cond` holds;
+// otherwise records QE_ERR_DEVICE_CHECK with `val` and returns false, so the
+// caller skips the access.  Always true in the plain build.
+#ifdef QE_CHECKED
+#define QE_DCHECK(st, cond, val) \
+    ((cond) ? true : (dev_report((st), QE_ERR_DEVICE_CHECK, static_cast<int64_t>(val) + 1), false))
+#else
+#define QE_DCHECK(st, cond, val) true
+#endif
+
 // MurmurHash3 64-bit finalizer (A. Appleby, public domain), the partition
 // function: destination = top log2(F) bits.
 __device__ __forceinline__ uint64_t dev_fmix64(uint64_t k)
@@ -153,6 +164,53 @@ __device__ __forceinline__ uint32_t dev_part_id(int64_t key, int log2f, int mode
         return static_cast<uint32_t>(k >> 32) >> (32 - log2f);
     }
     return static_cast<uint32_t>((k >> shift) & ((uint64_t(1) << log2f) - 1));
+}
+
+// L2 eviction policies (createpolicy) and loads that carry one.  The fused
+// pipeline streams its fact columns once (evict first) while the dimension's
+// payload array is looked up at random for the whole pass (evict last), so
+// the lookups keep hitting L2 instead of being pushed out by the stream.
+__device__ __forceinline__ uint64_t l2_policy_evict_first()
+{
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint64_t l2_policy_evict_last()
+{
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ int32_t ld_hint_i32(const int32_t *a, uint64_t pol)
+{
+    int32_t v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ int32_t ld_hint_s8(const signed char *a, uint64_t pol)
+{
+    int32_t v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s8 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ long long ld_hint_i64(const long long *a, uint64_t pol)
+{
+    long long v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(v) : "l"(a), "l"(pol));
+    return v;
+}
+
+// Random lookup that allocates in L1 and carries an L2 policy.
+__device__ __forceinline__ int32_t ld_lookup_i32(const int32_t *a, uint64_t pol)
+{
+    int32_t v;
+    asm("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+    return v;
 }
 
 // Read element i of a column as int64 (sign-extended).

@@ -257,6 +257,7 @@ __global__ void __launch_bounds__(PT) k_part_scatter(PartArgs A)
             const uint32_t w = wA[t];
             const int src = static_cast<int>(w & 0xfffu);
             const int64_t d = run[w >> 12] + t;
+            if (!QE_DCHECK(A.st, d >= 0 && d < A.n, d)) continue;
             out_store(reinterpret_cast<long long *>(A.out_keys) + d, keys[src], wpol);
             if (FAST) {
                 out_store(static_cast<long long *>(A.out_pay[0]) + d, pays[src], wpol);

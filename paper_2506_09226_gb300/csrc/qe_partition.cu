@@ -445,6 +445,7 @@ __global__ void __launch_bounds__(T, MINB) k_part_scatter_wc(PartArgs A)
                         if (np && e4 > r4) {
                             long long *o = ob[d] + r4;
                             for (int j = 0; j < np; j++) {
+                                if (!QE_DCHECK(A.st, o + j >= outK && o + j < outK + A.n, (o + j) - outK)) continue;
                                 __stcs(o + j, pK[d * 3 + j]);
                                 if (PAY) __stcs(o + dP + j, pP[d * 3 + j]);
                             }
@@ -493,6 +494,7 @@ __global__ void __launch_bounds__(T, MINB) k_part_scatter_wc(PartArgs A)
                             k = sK[t];
                         }
                         if (t < x.y) {
+                            if (!QE_DCHECK(A.st, o + q >= outK && o + q < outK + A.n, (o + q) - outK)) continue;
                             __stcs(o + q, k);
                             if (PAY) __stcs(o + q + dP, v);
                         } else {
@@ -550,6 +552,7 @@ __global__ void __launch_bounds__(T, MINB) k_part_scatter_wc(PartArgs A)
                         // this chunk completes the pending sector: write its earlier rows
                         long long *o = ob[p] + r4;
                         for (int j = 0; j < np; j++) {
+                            if (!QE_DCHECK(A.st, o + j >= outK && o + j < outK + A.n, (o + j) - outK)) continue;
                             __stcs(o + j, pK[p * 3 + j]);
                             if (PAY) __stcs(o + dP + j, pP[p * 3 + j]);
                         }
@@ -576,6 +579,7 @@ __global__ void __launch_bounds__(T, MINB) k_part_scatter_wc(PartArgs A)
                     const int q = x.x + t;
                     if (t < x.y) {
                         long long *o = ob[p] + q;
+                        if (!QE_DCHECK(A.st, o >= outK && o < outK + A.n, o - outK)) continue;
                         __stcs(o, sK[t]);
                         if (PAY) __stcs(o + dP, sP[t]);
                     } else {
@@ -598,6 +602,7 @@ __global__ void __launch_bounds__(T, MINB) k_part_scatter_wc(PartArgs A)
             const int np = r > 0 ? (r & 3) : 0;
             long long *o = ob[p] + (r & ~3);
             for (int j = 0; j < np; j++) {
+                if (!QE_DCHECK(A.st, o + j >= outK && o + j < outK + A.n, (o + j) - outK)) continue;
                 __stcs(o + j, pK[p * 3 + j]);
                 if (PAY) __stcs(o + dP + j, pP[p * 3 + j]);
             }

@@ -382,10 +382,11 @@ enum { STAR_INNER = 0, STAR_SEMI = 1, STAR_ANTI = 2, STAR_NONE = 3 };
 // (or spilled hash) update of the ITEMS rows a thread holds; bit k of cin
 // marks row k as inside the range.  cl holds the key column of the kinds
 // other than STAR_INNER.
-template <bool GLOBAL, int ITEMS, bool NSUM, int JK = STAR_INNER>
+template <bool GLOBAL, int ITEMS, bool NSUM, int JK = STAR_INNER, bool L2H = false>
 __device__ __forceinline__ void star_rows(const PipeSpec &P, unsigned long long *sm, const int (&cd)[ITEMS],
                                           const int (&cf)[ITEMS], const int (&ch)[ITEMS], const int (&cl)[ITEMS],
-                                          const int (&cq)[ITEMS], const long long (&cx)[ITEMS], unsigned cin)
+                                          const int (&cq)[ITEMS], const long long (&cx)[ITEMS], unsigned cin,
+                                          uint64_t pol_keep = 0)
 {
     bool ok[ITEMS];
     int32_t pay[ITEMS];
@@ -395,7 +396,10 @@ __device__ __forceinline__ void star_rows(const PipeSpec &P, unsigned long long 
         if constexpr (JK == STAR_INNER) {
             const uint32_t ks = static_cast<uint32_t>(cf[k]) - static_cast<uint32_t>(P.ht.key_min);
             const bool hit = ((cin >> k) & 1u) && pass && ks < P.ht.range;
-            pay[k] = hit ? ht_ld(P.ht, P.ht.payload + ks) : 0;
+            if constexpr (L2H)
+                pay[k] = hit ? ld_lookup_i32(P.ht.payload + ks, pol_keep) : 0;
+            else
+                pay[k] = hit ? ht_ld(P.ht, P.ht.payload + ks) : 0;
             ok[k] = hit && (P.ht.full || ((ht_ld(P.ht, P.ht.bitmap + (ks >> 5)) >> (ks & 31)) & 1u));
         } else if constexpr (JK == STAR_NONE) {
             pay[k] = cl[k];
@@ -420,6 +424,7 @@ __device__ __forceinline__ void star_rows(const PipeSpec &P, unsigned long long 
         const unsigned long long emax = static_cast<unsigned long long>(cx[k]) ^ GB_SIGN;
         if (hh < P.s_hspan && ll < P.s_lspan) {
             const uint32_t idx = hh * P.s_lspan + ll;
+            if (!QE_DCHECK(P.g.st, idx < P.s_ns, idx)) continue;
             if (GLOBAL) {
                 unsigned long long *cell = P.gdense + static_cast<uint64_t>(idx) * 4;
                 atomicAdd(cell, v);
@@ -464,13 +469,20 @@ __device__ __forceinline__ void star_rows(const PipeSpec &P, unsigned long long 
 // starting at r0, r0 + stride, ... below r1; all columns of the next tile are
 // loaded into registers while the current one is processed, so the register
 // file holds the loads in flight.
-template <bool GLOBAL, int ITEMS, int THREADS, bool NSUM, int JK = STAR_INNER>
+template <bool GLOBAL, int ITEMS, int THREADS, bool NSUM, int JK = STAR_INNER, bool L2H = false>
 __device__ __forceinline__ void star_range(const PipeSpec &P, unsigned long long *sm, int64_t r0, int64_t r1,
                                            int64_t stride)
 {
     int d[ITEMS], f[ITEMS], h[ITEMS], l[ITEMS], q[ITEMS];
     long long x[ITEMS];
     unsigned inmask = 0;
+    // L2H: fact columns evict first, payload lookups evict last
+    const uint64_t pol_stream = L2H ? l2_policy_evict_first() : 0;
+    const uint64_t pol_keep = L2H ? l2_policy_evict_last() : 0;
+    auto ld32 = [&](const int32_t *a) -> int { return L2H ? ld_hint_i32(a, pol_stream) : __ldcs(a); };
+    auto ld8 = [&](const signed char *a) -> int {
+        return L2H ? ld_hint_s8(a, pol_stream) : static_cast<int>(__ldcs(a));
+    };
     auto load = [&](int64_t t0) {
         inmask = 0;
 #pragma unroll
@@ -478,18 +490,18 @@ __device__ __forceinline__ void star_range(const PipeSpec &P, unsigned long long
             const int64_t r = t0 + k * THREADS + threadIdx.x;
             const bool in = r < r1;
             inmask |= in ? (1u << k) : 0u;
-            d[k] = in ? __ldcs(P.s_pred + r) : 0;
-            f[k] = JK != STAR_NONE && in ? __ldcs(P.s_fk + r) : 0;
+            d[k] = in ? ld32(P.s_pred + r) : 0;
+            f[k] = JK != STAR_NONE && in ? ld32(P.s_fk + r) : 0;
             h[k] = (JK == STAR_INNER || P.s_has_hi) && in
-                       ? (P.s_h8 ? static_cast<int>(__ldcs(static_cast<const signed char *>(P.s_hi) + r))
-                                 : __ldcs(static_cast<const int32_t *>(P.s_hi) + r))
+                       ? (P.s_h8 ? ld8(static_cast<const signed char *>(P.s_hi) + r)
+                                 : ld32(static_cast<const int32_t *>(P.s_hi) + r))
                        : 0;
             l[k] = JK != STAR_INNER && in
-                       ? (P.s_l8 ? static_cast<int>(__ldcs(static_cast<const signed char *>(P.s_lo) + r))
-                                 : __ldcs(static_cast<const int32_t *>(P.s_lo) + r))
+                       ? (P.s_l8 ? ld8(static_cast<const signed char *>(P.s_lo) + r)
+                                 : ld32(static_cast<const int32_t *>(P.s_lo) + r))
                        : 0;
-            x[k] = in ? __ldcs(P.s_x + r) : 0;
-            q[k] = in ? __ldcs(P.s_y + r) : 0;
+            x[k] = in ? (L2H ? ld_hint_i64(P.s_x + r, pol_stream) : __ldcs(P.s_x + r)) : 0;
+            q[k] = in ? ld32(P.s_y + r) : 0;
         }
     };
     if (r0 >= r1) return;
@@ -508,7 +520,7 @@ __device__ __forceinline__ void star_range(const PipeSpec &P, unsigned long long
             cx[k] = x[k];
         }
         load(t0 + stride);   // next tile's loads overlap this tile's work
-        star_rows<GLOBAL, ITEMS, NSUM, JK>(P, sm, cd, cf, ch, cl, cq, cx, cin);
+        star_rows<GLOBAL, ITEMS, NSUM, JK, L2H>(P, sm, cd, cf, ch, cl, cq, cx, cin, pol_keep);
     }
 }
 

@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(PT, 1) k_pipeline(PipeSpec P, TableCfg T)
 // NSUM: the shared-memory direct array keeps SUM as 32-bit halves (small
 // arrays, where many rows hit each slot and 64-bit atomics collide most).
 // JK: the star kind (STAR_INNER, STAR_SEMI, STAR_ANTI, STAR_NONE).
-template <bool GLOBAL, int ITEMS, bool NSUM, int JK>
+template <bool GLOBAL, int ITEMS, bool NSUM, int JK, bool L2H = false>
 __global__ void __launch_bounds__(PT, 1) k_pipeline_star(PipeSpec P, TableCfg T)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(PT, 1) k_pipeline_star(PipeSpec P, TableCfg T)
     __syncthreads();
     // grid-stride tiles: at any moment the blocks read neighbouring tiles
     constexpr int64_t TR = static_cast<int64_t>(PT) * ITEMS;
-    star_range<GLOBAL, ITEMS, PT, NSUM, JK>(P, sm, static_cast<int64_t>(blockIdx.x) * TR, P.n, TR * gridDim.x);
+    star_range<GLOBAL, ITEMS, PT, NSUM, JK, L2H>(P, sm, static_cast<int64_t>(blockIdx.x) * TR, P.n, TR * gridDim.x);
     __syncthreads();
     if (!GLOBAL) table_flush(P, T, sm, NSUM ? 2 : 1);
 }
@@ -292,6 +292,14 @@ qe_status pipeline_launch(qe_ctx *ctx, PipeSpec &P, const PipePlan &plan, const 
         star_predicate(P);
         // rows per thread: 3 by default, 2 when tuned so
         const bool two = ctx->tune_star_items == 2;
+        if (ctx->tune_l2_hint && !two) {
+            // L2 policies: fact columns evict first, payload lookups evict last
+            if (plan.T.mode == TM_GLOBAL_DENSE)
+                return launch(ctx, k_pipeline_star<true, 3, false, STAR_INNER, true>, P, plan.T, 0, PT * 3, s);
+            if (P.dk.nslots <= STAR_NSUM_SLOTS)
+                return launch(ctx, k_pipeline_star<false, 3, true, STAR_INNER, true>, P, plan.T, plan.table, PT * 3, s);
+            return launch(ctx, k_pipeline_star<false, 3, false, STAR_INNER, true>, P, plan.T, plan.table, PT * 3, s);
+        }
         if (plan.T.mode == TM_GLOBAL_DENSE)
             return two ? launch(ctx, k_pipeline_star<true, 2, false, STAR_INNER>, P, plan.T, 0, PT * 2, s)
                        : launch(ctx, k_pipeline_star<true, 3, false, STAR_INNER>, P, plan.T, 0, PT * 3, s);

@@ -19,13 +19,15 @@ from dataclasses import dataclass
 
 import torch
 
-_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libqe.so")
+_LIB_DIR = os.path.dirname(os.path.abspath(__file__))
+# QE_LIB=checked selects the bounds-checked build (libqe_checked.so)
+_LIB_PATH = os.path.join(_LIB_DIR, "libqe_checked.so" if os.environ.get("QE_LIB") == "checked" else "libqe.so")
 
 # qe_status
 OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_OOM, ERR_DUPLICATE_KEY, ERR_RESERVED_KEY, ERR_TIMEOUT, ERR_CUDA, \
-    ERR_NO_DEVICE = range(9)
+    ERR_NO_DEVICE, ERR_DEVICE_CHECK = range(10)
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CAPACITY", 3: "OOM", 4: "DUPLICATE_KEY", 5: "RESERVED_KEY",
-                6: "TIMEOUT", 7: "CUDA", 8: "NO_DEVICE"}
+                6: "TIMEOUT", 7: "CUDA", 8: "NO_DEVICE", 9: "DEVICE_CHECK"}
 # qe_type
 I8, I32, I64 = 1, 4, 8
 # qe_cmp
@@ -97,7 +99,8 @@ class qe_pipeline_desc(ctypes.Structure):
 
 class qe_batch_opts(ctypes.Structure):
     _fields_ = [("block_threads", ctypes.c_int32), ("tile_rows", ctypes.c_int32),
-                ("smem_slots", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+                ("smem_slots", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("build_ahead_bytes", ctypes.c_int64)]
 
 
 # exchange planner (include/qe_plan.h)
@@ -126,6 +129,7 @@ _SIGS = {
     "qe_debug_fail_alloc": (None, [ctypes.c_void_p, ctypes.c_int]),
     "qe_debug_set_spin_limit": (None, [ctypes.c_void_p, ctypes.c_int64]),
     "qe_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
+    "qe_build_checked": (ctypes.c_int, []),
     "qe_set_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int64]),
     "qe_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "qe_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int64),

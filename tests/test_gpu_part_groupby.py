@@ -75,17 +75,20 @@ def _oracle(fact, dim, key_col, date_lt, kind=O.INNER, key_hi=-1):
     return O.pipeline([fact[c].numpy() for c in SKEW], q, dk, dim["attr"].numpy() if kind == O.INNER else None)
 
 
-@pytest.mark.parametrize("log2p", [1, 3, 8, 10])
-def test_part_groupby_int64_keys(ctx, log2p):
+@pytest.mark.parametrize("log2p,generic", [(1, False), (3, False), (8, False), (10, False), (8, True)])
+def test_part_groupby_int64_keys(ctx, log2p, generic):
     """~200K distinct int64 keys over 1M rows: keys from a fact column (every
-    row counted from the key column), at 2 .. 1024 parts."""
+    row counted from the key column), at 2 .. 1024 parts, through the
+    star-shape scatter (register-prefetched) and the generic one."""
     ctx.set_tuning("gb_part_log2p", log2p)
+    ctx.set_tuning("force_generic", int(generic))
     try:
         fact, dim = _skew(1_000_003, 50_000, 200_000, seed=61)
         g = _run(ctx, fact, dim, 6, 1278, 262_144)
         _equal(g, _oracle(fact, dim, 6, 1278))
     finally:
         ctx.set_tuning("gb_part_log2p", 0)
+        ctx.set_tuning("force_generic", 0)
 
 
 @pytest.mark.parametrize("date_lt", [0, 26, 2301, 2557])

@@ -40,6 +40,18 @@ def test_library_exports_every_declared_entry_point(lib):
     assert set(qe.EXPORTED) <= set(names)        # the binding declares nothing the header lacks
 
 
+def test_checked_build_is_marked(lib):
+    """libqe.so is the plain build and libqe_checked.so the bounds-checked one."""
+    assert lib.qe_build_checked() == 0
+    chk = os.path.join(ROOT, "paper_2506_09226_gb300", "libqe_checked.so")
+    if not os.path.exists(chk):
+        from paper_2506_09226_gb300 import build
+        build.build()
+    c = ctypes.CDLL(chk)
+    c.qe_build_checked.restype = ctypes.c_int
+    assert c.qe_build_checked() == 1
+
+
 def test_create_without_device_fails_cleanly(lib):
     import torch
     if torch.cuda.is_available():
