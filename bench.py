@@ -484,12 +484,13 @@ def run_skew(args, qe, ctx, dev, stream, peak, it):
     the selectivity swept over 1 .. 90 % through date < c and through a
     dictionary-code predicate code < K.  Groups this many take the
     partitioned group-by (count, scan, scatter of 24-byte rows into parts,
-    aggregation of part after part in L2-resident hash windows).  hbm_frac
-    counts the 28 bytes each fact row reads (fk, date, price, qty, int64
-    group key; code instead of date for the code sweep); part_bytes states
-    the extra traffic of the partition round trip (the count pass reads the
-    8-byte key of every row; each survivor is written and read back as 24
-    bytes).  Also timed: the 50 % point through the direct HBM hash table
+    split of every part into sub-parts, shared-memory aggregation of each
+    sub-part).  hbm_frac counts the 28 bytes each fact row reads (fk, date,
+    price, qty, int64 group key; code instead of date for the code sweep);
+    part_bytes states the extra traffic of the partition round trips (the
+    count pass reads the 8-byte key of every row; each survivor is written
+    by the scatter, read and written by the split and read by the fold, 24
+    bytes each time).  Also timed: the 50 % point through the direct HBM hash table
     (the path the partitioning replaces) and the group-by on 10^6
     dictionary codes."""
     from paper_2506_09226_gb300 import datagen
@@ -505,7 +506,7 @@ def run_skew(args, qe, ctx, dev, stream, peak, it):
     cap = max(1, n_fact * 2 // 15)
     groups, gout = qe.alloc_groups(cap, 4, dev)
     res = {"fact_rows": n_fact, "dim_rows": n_dim, "groups_pool": cap}
-    phases = ("part_count", "part_scatter_rows", "part_fold", "pipeline")
+    phases = ("part_count", "part_scatter_rows", "part_split", "part_fold", "pipeline")
 
     def one(pred, key_col, capacity, sel_est):
         d = qe.pipeline_desc(cols, [pred], fk_col=0, dim_key=dim["key"], dim_payload=dim["attr"],
@@ -539,7 +540,7 @@ def run_skew(args, qe, ctx, dev, stream, peak, it):
             sweep[f"{int(round(sel * 100))}%"] = {
                 "ms": ms, "rows_per_s": n_fact / (ms * 1e-3), "ngroups": ng,
                 "hbm_frac": round(28 * n_fact / (ms * 1e-3) / 1e9 / peak, 4), "kernels_ms": kern,
-                "part_bytes": (8 * n_fact + 48 * nsurv) if nsurv is not None else 0}
+                "part_bytes": (8 * n_fact + 96 * nsurv) if nsurv is not None else 0}
         res[f"sweep_{colname}"] = sweep
     # the direct HBM hash table at 50 %, for comparison
     ctx.set_tuning("gb_partition", 1)

@@ -153,6 +153,16 @@ void qe_debug_set_spin_limit(qe_ctx *ctx, int64_t iterations);
  *                   kernel (chunks ranked over one or two digits, any
  *                   payload types, one pass at every fan-out) instead of the
  *                   write-combining one.
+ *   "l2_hint"       nonzero: the star pipeline loads fact columns with an
+ *                   L2 evict-first policy and looks payloads up with an
+ *                   evict-last one (measured no faster; off by default).
+ *   "gb_partition"  pipelines whose groups need an HBM hash table: 0 = the
+ *                   partitioned group-by when that table would exceed 256 MB
+ *                   and the fact table has 4M rows or more, 1 = never,
+ *                   2 = always.
+ *   "gb_part_log2p" / "gb_part_log2q"
+ *                   log2 of the partitioned group-by's parts (1..10; 0 =
+ *                   planned) and sub-parts per part (0..8; -1 = planned).
  * Unknown names return QE_ERR_INVALID_ARG. */
 qe_status qe_set_tuning(qe_ctx *ctx, const char *name, int64_t value);
 

@@ -117,6 +117,11 @@ extern "C" qe_status qe_set_tuning(qe_ctx *ctx, const char *name, int64_t value)
     } else if (n == "gb_partition") {
         if (value < 0 || value > 2) return qe_fail(ctx, QE_ERR_INVALID_ARG, "gb_partition must be 0, 1 or 2");
         ctx->tune_gb_partition = static_cast<int>(value);
+    } else if (n == "gb_fold2") {
+        ctx->tune_gb_fold2 = value != 0;
+    } else if (n == "gb_part_log2q") {
+        if (value < -1 || value > 8) return qe_fail(ctx, QE_ERR_INVALID_ARG, "gb_part_log2q must be in [-1, 8]");
+        ctx->tune_gb_part_log2q = static_cast<int>(value);
     } else if (n == "gb_part_log2p") {
         if (value < 0 || value > 10) return qe_fail(ctx, QE_ERR_INVALID_ARG, "gb_part_log2p must be in [0, 10]");
         ctx->tune_gb_part_log2p = static_cast<int>(value);

@@ -45,6 +45,8 @@ struct qe_ctx {
     int tune_part_general = 0;      // partition: skip the write-combining scatter
     int tune_gb_partition = 0;      // large HBM group tables: 0 auto, 1 never partition, 2 always
     int tune_gb_part_log2p = 0;     // parts of the partitioned group-by (log2; 0 = planned)
+    int tune_gb_part_log2q = -1;    // sub-parts per part (log2; -1 = planned)
+    int tune_gb_fold2 = 0;          // partitioned fold: two 512-thread blocks per SM
     int tune_l2_hint = 0;           // star pipeline: L2 policies on fact loads and payload lookups
     bool profiling = false;
     std::mutex prof_mu;

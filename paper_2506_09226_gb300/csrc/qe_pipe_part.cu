@@ -5,10 +5,10 @@
 // to handle efficiently (Sec. 7.2) and, for its exchange, applies one
 // partitioning function to every row before the local operator runs on each
 // part (Sec. 2.2).  Here the same idea keeps a group-by with tens of
-// millions of groups out of random DRAM read-modify-writes: the surviving
-// rows are partitioned on the hash of their group key, so that each part's
-// groups fit a hash table that stays in L2, and each part is aggregated in
-// turn.
+// millions of groups out of random DRAM read-modify-writes and L2 atomics:
+// the surviving rows are partitioned twice on the hash of their group key,
+// until each sub-part's groups fit one block's shared-memory hash table, and
+// each sub-part is then aggregated on chip and written out once.
 //
 //   count    one contiguous row range per block; each row's part p (top
 //            log2p bits of fmix64 of the stored key) is counted in a shared
@@ -25,33 +25,27 @@
 //            each part its start) and written as (stored key, X, Y) -- 24
 //            bytes -- to the end of their segments, consecutive threads
 //            storing consecutive 8-byte words of each part's run.  The final
-//            cursors give each segment's fill.
-//   fold     one persistent kernel over an ordered list of work items:
-//            stage s holds the fold items (s, b) of part s -- one per
-//            segment -- and then the compaction chunks of part s - lag.
-//            Part p aggregates into window p mod R of a ring of R hash
-//            tables (linear probing on the low hash bits, atomics), which
-//            together stay resident in L2.  A compaction chunk waits
-//            (bounded) for every fold item of its part, emits its slots'
-//            groups straight into the caller's output and zeroes them; a
-//            fold item of part p waits (bounded) for the compaction of part
-//            p - R, the previous user of its window.  With lag = R - 2 both
-//            waits are on items claimed a stage or more earlier, so they are
-//            rarely felt; items are claimed in order from one counter and
-//            every wait is on an earlier item, so running blocks always hold
-//            what is waited for.
+//            cursors give each segment's fill.  The star shape (one int32
+//            predicate, a dense or no join, fact-column keys, int64 X and
+//            int32 Y) loads the next tile into registers meanwhile.
+//   split    the filled rows of every segment, in chunks of at most 4,096,
+//            each sorted by sub-part (the next log2q hash bits) in shared
+//            memory and written to a second buffer at the same rows, with
+//            the chunk's sub-part offsets.
+//   fold     one block per sub-part at a time: its runs (one per chunk of
+//            its part) go through a shared-memory hash table (linear
+//            probing, shared atomics); the table's groups are written to
+//            the output with one global atomic per 1,024 slots, and zeroed.
+//            A key that finds no slot within 64 probes (only when a
+//            sub-part gets far more groups than planned) goes to an HBM
+//            spill table, emitted after the fold.
 //
-// Aggregates are exact whatever order rows fold in (wrapping sums, counts,
-// min / max), so the parts need no stable order.
 #include "qe_pipe_core.cuh"
 
 namespace {
 
 constexpr int PPT = 1024;          // threads per block (all phases)
 constexpr int PP_ITEMS = 2;        // rows per thread per tile (count / scatter)
-constexpr int PF_ITEMS = 4;        // rows per thread per round (fold)
-constexpr int FPT = 512;           // threads per fold block; two blocks per SM, so one
-                                   // block's item hand-over overlaps the other's rows
 
 struct PartRow {
     unsigned long long kx;         // stored key: key ^ INT64_MIN (0 is reserved)
@@ -181,14 +175,16 @@ __global__ void __launch_bounds__(PPT) k_pp_count(PartArgs A)
 
 // Exclusive scan of m counts into seg (one block): each thread sums a
 // contiguous run, the run sums are scanned across the block, then each
-// thread writes its run's starts.
-__global__ void __launch_bounds__(PPT) k_pp_scan(const uint32_t *cnt, int64_t m, int64_t *seg)
+// thread writes its run's starts.  With div > 0 the value scanned is
+// ceil(count / div) (chunks of div rows); total (nullable) receives the sum.
+__global__ void __launch_bounds__(PPT) k_pp_scan(const uint32_t *cnt, int64_t m, int64_t *seg, int div, int64_t *total)
 {
     __shared__ int64_t warp_tot[PPT / 32];
     const int64_t per = (m + PPT - 1) / PPT;
     const int64_t a = threadIdx.x * per, b = a + per < m ? a + per : m;
+    auto val = [&](int64_t i) -> int64_t { return div > 0 ? (cnt[i] + div - 1) / div : cnt[i]; };
     int64_t s = 0;
-    for (int64_t i = a; i < b; i++) s += cnt[i];
+    for (int64_t i = a; i < b; i++) s += val(i);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t inc = warp_incl_scan<int64_t>(s);
     if (lane == 31) warp_tot[w] = inc;
@@ -197,12 +193,13 @@ __global__ void __launch_bounds__(PPT) k_pp_scan(const uint32_t *cnt, int64_t m,
         const int64_t t = warp_tot[lane];
         const int64_t ti = warp_incl_scan<int64_t>(t);
         warp_tot[lane] = ti - t;
+        if (lane == 31 && total) *total = ti;
     }
     __syncthreads();
     int64_t run = warp_tot[w] + inc - s;
     for (int64_t i = a; i < b; i++) {
         seg[i] = run;
-        run += cnt[i];
+        run += val(i);
     }
 }
 
@@ -442,30 +439,162 @@ __global__ void __launch_bounds__(PPT, 1) k_pp_scatter_star(PartArgs A)
     pp_scatter_end(A, S, parts);
 }
 
+// ------------------------------------------------------------ split
+// The second partition: every part of the scatter is split once more, into
+// 2^log2q sub-parts (the next hash bits), so that a sub-part's groups fit a
+// shared-memory hash table.  The part's rows are cut into chunks of at most
+// SPLIT_ROWS rows (each inside one segment); a block sorts a chunk by
+// sub-part in shared memory and writes it back to the same rows of a second
+// buffer, with the chunk's sub-part offsets (16-bit, SPLIT_ROWS < 2^16).
+constexpr int SPLIT_ROWS = 4096;
+constexpr int SPT = 1024;                       // threads per split block
+constexpr int SP_ITEMS = SPLIT_ROWS / SPT;
+
+struct SplitArgs {
+    int32_t log2p, log2q, nblk, pad;
+    int64_t m;                     // segments (parts x nblk)
+    int64_t nrows;                 // rows of both buffers
+    qe_dev_status *st;
+    const int64_t *seg;
+    const uint32_t *fill;
+    const int64_t *cpre;           // [m + 1] chunks before each segment; cpre[m] = chunks
+    const PartRow *rows;           // the scatter's rows
+    PartRow *rows2;                // the split rows (same row numbers)
+    uint16_t *off2;                // [chunks][2^log2q + 1] sub-part starts inside each chunk
+    int64_t *cstart;               // [chunks] first row of each chunk
+    unsigned long long *counter;   // chunk claims
+};
+
+__device__ __forceinline__ uint32_t pp_subpart(unsigned long long kx, int log2p, int log2q)
+{
+    return log2q ? static_cast<uint32_t>((dev_fmix64(kx) << log2p) >> (64 - log2q)) : 0u;
+}
+
+static inline size_t pp_split_smem(int log2q)
+{
+    return static_cast<size_t>(SPLIT_ROWS) * 24 + static_cast<size_t>(2 << log2q) * 4 + 64;
+}
+
+__global__ void __launch_bounds__(SPT, 1) k_pp_split(SplitArgs A)
+{
+    extern __shared__ __align__(16) unsigned char sp_smem[];
+    const int Q = 1 << A.log2q;
+    unsigned long long *stage = reinterpret_cast<unsigned long long *>(sp_smem);   // [SPLIT_ROWS][3]
+    unsigned *tcnt = reinterpret_cast<unsigned *>(stage + 3 * SPLIT_ROWS);         // [Q]
+    unsigned *tstart = tcnt + Q;                                                   // [Q]
+    __shared__ long long s_j;
+    __shared__ int s_w[SPT / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < Q; i += SPT) tcnt[i] = 0;
+    while (true) {
+        // claim a segment; its chunks are cpre[j] .. cpre[j + 1]
+        if (threadIdx.x == 0) s_j = static_cast<long long>(atomicAdd(A.counter, 1ull));
+        __syncthreads();
+        const int64_t j = s_j;
+        __syncthreads();                   // every thread has read s_j before the next claim
+        if (j >= A.m) break;
+        const int64_t cA = A.cpre[j], cB = A.cpre[j + 1];
+        for (int64_t c = cA; c < cB; c++) {
+            const int64_t k = c - cA;
+            const int64_t r0 = A.seg[j] + k * SPLIT_ROWS;
+            const int64_t rend = A.seg[j] + A.fill[j];
+            int n = static_cast<int>(r0 + SPLIT_ROWS < rend ? SPLIT_ROWS : rend - r0);
+            if (!QE_DCHECK(A.st, r0 >= 0 && n >= 0 && r0 + n <= A.nrows, r0 + n)) n = 0;
+            unsigned long long kx[SP_ITEMS];
+            long long xv[SP_ITEMS], yv[SP_ITEMS];
+            uint32_t sub[SP_ITEMS], rank[SP_ITEMS];
+    #pragma unroll
+            for (int t = 0; t < SP_ITEMS; t++) {
+                const int i = t * SPT + threadIdx.x;
+                kx[t] = 0;
+                xv[t] = yv[t] = 0;
+                if (i < n) {
+                    const PartRow *r = A.rows + r0 + i;
+                    kx[t] = __ldcs(&r->kx);
+                    xv[t] = __ldcs(&r->x);
+                    yv[t] = __ldcs(&r->y);
+                }
+            }
+    #pragma unroll
+            for (int t = 0; t < SP_ITEMS; t++) {
+                sub[t] = kx[t] ? pp_subpart(kx[t], A.log2p, A.log2q) : 0u;
+                rank[t] = kx[t] ? atomicAdd(&tcnt[sub[t]], 1u) : 0u;
+            }
+            __syncthreads();
+            {
+                // exclusive scan of the Q sub-part counts
+                const int per = (Q + SPT - 1) / SPT;
+                unsigned loc = 0;
+                for (int q = 0; q < per; q++) {
+                    const int i = threadIdx.x * per + q;
+                    if (i < Q) loc += tcnt[i];
+                }
+                const unsigned inc = warp_incl_scan(loc);
+                if (lane == 31) s_w[warp] = static_cast<int>(inc);
+                __syncthreads();
+                if (warp == 0) {
+                    constexpr int NW = SPT / 32;
+                    const int w = lane < NW ? s_w[lane] : 0;
+                    const int wi = warp_incl_scan(w);
+                    if (lane < NW) s_w[lane] = wi - w;
+                }
+                __syncthreads();
+                unsigned run = static_cast<unsigned>(s_w[warp]) + inc - loc;
+                for (int q = 0; q < per; q++) {
+                    const int i = threadIdx.x * per + q;
+                    if (i < Q) {
+                        tstart[i] = run;
+                        run += tcnt[i];
+                    }
+                }
+            }
+            __syncthreads();
+    #pragma unroll
+            for (int t = 0; t < SP_ITEMS; t++) {
+                if (!kx[t]) continue;
+                const unsigned pos = tstart[sub[t]] + rank[t];
+                stage[3 * pos] = kx[t];
+                stage[3 * pos + 1] = static_cast<unsigned long long>(xv[t]);
+                stage[3 * pos + 2] = static_cast<unsigned long long>(yv[t]);
+            }
+            __syncthreads();
+            unsigned long long *dst = reinterpret_cast<unsigned long long *>(A.rows2 + r0);
+            for (int w = threadIdx.x; w < 3 * n; w += SPT) __stcg(dst + w, stage[w]);
+            uint16_t *o = A.off2 + c * (Q + 1);
+            for (int i = threadIdx.x; i <= Q; i += SPT) o[i] = static_cast<uint16_t>(i < Q ? tstart[i] : n);
+            if (threadIdx.x == 0) A.cstart[c] = r0;
+            __syncthreads();
+            for (int i = threadIdx.x; i < Q; i += SPT) tcnt[i] = 0;
+            __syncthreads();
+        }
+    }
+}
+
 // ------------------------------------------------------------ fold
+// One block per sub-part at a time: the sub-part's runs (one per chunk of
+// its part) are folded into a shared-memory hash table, whose groups are
+// then written straight to the output; keys that find no slot within the
+// probe limit go to an HBM spill table, emitted at the end.
+constexpr int FT = 1024;                        // threads per fold block
+constexpr int F_ITEMS = 2;                      // rows per lane in flight (64 per warp)
+constexpr int F_RUNS = 1024;                    // runs described in shared memory at a time
+constexpr int F_PROBES = 64;                    // shared-table probe limit before a spill
+constexpr int F_EMIT_GROUPS = 128;              // slot groups of 32 in the largest shared table
+
 struct FoldArgs {
     AggOps ops;
     int32_t src[QE_MAX_AGGS];
-    int32_t log2p, nblk;
-    int32_t log2w;                 // window slots = 1 << log2w
-    int32_t ring;                  // windows in the ring (power of two)
-    int32_t chunks;                // compaction chunks per window
-    int32_t lag;                   // stage s compacts part s - lag (1 <= lag < ring)
-    int32_t stride;                // words per slot: key + aggregates
-    int32_t cnt;                   // COUNT aggregate (averages), or -1
+    int32_t log2p, log2q, nblk, log2s;          // log2s: shared-table slots
+    int32_t cnt;                                // COUNT aggregate (averages), or -1
     int32_t pad;
-    const int64_t *seg;
-    const uint32_t *fill;
-    const PartRow *rows;
-    unsigned long long *win;       // ring * (1 << log2w) * stride words
-    unsigned *done_fold, *done_comp;   // [parts]
-    unsigned *abort;               // set when a wait expired: later waits give up at once
-    unsigned long long *items;     // item counter
-    unsigned long long *emitted;   // groups written to `out`
+    const int64_t *cpre;
+    const uint16_t *off2;
+    const int64_t *cstart;
+    const PartRow *rows2;
+    GTable spill;
+    unsigned long long *counter;                // sub-part claims
+    unsigned long long *emitted;                // groups written to `out`
     qe_groups_out out;
-    int64_t nitems;
-    int64_t nrows;                 // scratch rows (bounds of the segments)
-    int64_t spin_limit;
     qe_dev_status *st;
 };
 
@@ -477,201 +606,232 @@ __device__ __forceinline__ unsigned long long pp_value(const FoldArgs &A, int a,
     return agg_encode(A.ops.op[a], v);
 }
 
-// Slot of kx in a window (inserting it), starting from its home slot; -1
-// when a probe chain of GT_MAX_PROBE slots holds neither the key nor an
-// empty slot (more groups in the part than the window can take).
-static __device__ __noinline__ int64_t pp_find_insert(unsigned long long *win, uint64_t wmask, int stride,
-                                                      unsigned long long kx, uint64_t i)
+static __device__ __noinline__ void pp_spill_ni(const GTable g, const AggOps ops, unsigned long long kx,
+                                                unsigned long long e0, unsigned long long e1, unsigned long long e2,
+                                                unsigned long long e3)
 {
-    const uint64_t limit = wmask < GT_MAX_PROBE ? wmask : GT_MAX_PROBE;
-    for (uint64_t probes = 0; probes <= limit; probes++) {
-        unsigned long long *cell = win + i * stride;
-        const unsigned long long c = __ldcg(cell);
-        if (c == kx) return static_cast<int64_t>(i);
-        if (c == 0) {
-            const unsigned long long old = atomicCAS(cell, 0ull, kx);
-            if (old == 0 || old == kx) return static_cast<int64_t>(i);
-        }
-        i = (i + 1) & wmask;
-    }
-    return -1;
+    const unsigned long long e[QE_MAX_AGGS] = {e0, e1, e2, e3};
+    gt_fold_row(g, ops, kx, e);
 }
 
-// Fold the n rows of one segment into a window.  Each thread holds
-// PF_ITEMS rows; their home slots are read before any of them folds, so the
-// rows' L2 round trips overlap.
-__device__ void pp_fold_segment(const FoldArgs &A, unsigned long long *win, const PartRow *rows, int64_t n)
+// Emit n words-per-slot table rows [s0, s1) of a table with `stride`
+// words per slot laid out as keys[S] then aggs[a][S] (shared) or as
+// AoS slots (HBM spill, aos = true): positions come from one atomic per
+// FT slots.  Emitted shared slots are zeroed.
+template <bool AOS, int T>
+__device__ void pp_emit(const FoldArgs &A, unsigned long long *t, uint64_t S, uint64_t s0, uint64_t s1, int stride)
 {
-    const uint64_t wmask = (uint64_t(1) << A.log2w) - 1;
-    for (int64_t b0 = 0; b0 < n; b0 += FPT * PF_ITEMS) {
-        unsigned long long kx[PF_ITEMS], cur[PF_ITEMS];
-        long long x[PF_ITEMS], y[PF_ITEMS];
-        uint64_t home[PF_ITEMS];
-#pragma unroll
-        for (int k = 0; k < PF_ITEMS; k++) {
-            const int64_t i = b0 + k * FPT + threadIdx.x;
-            kx[k] = 0;
-            x[k] = y[k] = 0;
-            if (i < n) {
-                kx[k] = __ldcs(&rows[i].kx);
-                x[k] = __ldcs(&rows[i].x);
-                y[k] = __ldcs(&rows[i].y);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < PF_ITEMS; k++) {
-            home[k] = dev_fmix64(kx[k]) & wmask;
-            cur[k] = kx[k] ? __ldcg(win + home[k] * A.stride) : 0;
-        }
-#pragma unroll
-        for (int k = 0; k < PF_ITEMS; k++) {
-            if (!kx[k]) continue;
-            const int64_t s = cur[k] == kx[k] ? static_cast<int64_t>(home[k])
-                                              : pp_find_insert(win, wmask, A.stride, kx[k], home[k]);
-            if (s < 0) {
-                dev_report(A.st, QE_ERR_CAPACITY, A.out.capacity + 1);
-                continue;
-            }
-            // fire-and-forget reductions: a group gets only a few rows per
-            // part, so reading MIN/MAX cells first would add two dependent
-            // L2 round trips per row and save few atomics
-            unsigned long long *cell = win + s * A.stride + 1;
-#pragma unroll
-            for (int a = 0; a < QE_MAX_AGGS; a++) {
-                if (a >= A.ops.n) continue;
-                const unsigned long long e = pp_value(A, a, x[k], y[k]);
-                if (A.ops.op[a] == QE_SUM || A.ops.op[a] == QE_COUNT)
-                    atomicAdd(cell + a, e);
-                else
-                    atomicMax(cell + a, e);
-            }
-        }
-    }
-}
-
-// Emit the groups of slots [s0, s1) of a window into the output and zero
-// those slots.  The block takes its output positions with one atomic per
-// FPT slots (warp counts scanned in shared memory), not one per warp.
-__device__ void pp_compact_chunk(const FoldArgs &A, unsigned long long *win, int64_t s0, int64_t s1)
-{
-    __shared__ unsigned s_wc[FPT / 32];
+    __shared__ unsigned s_wc[32];
     __shared__ unsigned long long s_first;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t b = s0; b < s1; b += FPT) {
-        const int64_t i = b + threadIdx.x;
+    for (uint64_t b = s0; b < s1; b += T) {
+        const uint64_t i = b + threadIdx.x;
         const bool in = i < s1;
-        unsigned long long *cell = win + i * A.stride;
-        const unsigned long long kx = in ? __ldcg(cell) : 0ull;
+        const unsigned long long kx = in ? (AOS ? __ldcg(t + i * stride) : t[i]) : 0ull;
         const unsigned m = __ballot_sync(QE_FULL_MASK, kx != 0);
         if (lane == 0) s_wc[warp] = __popc(m);
         __syncthreads();
         if (warp == 0) {
-            constexpr int NW = FPT / 32;
-            const unsigned c = lane < NW ? s_wc[lane] : 0u;
+            const unsigned c = lane < T / 32 ? s_wc[lane] : 0u;
             const unsigned inc = warp_incl_scan(c);
-            if (lane < NW) s_wc[lane] = inc - c;
+            if (lane < T / 32) s_wc[lane] = inc - c;
             if (lane == 31) s_first = inc ? atomicAdd(A.emitted, static_cast<unsigned long long>(inc)) : 0ull;
         }
         __syncthreads();
         if (kx) {
             const int64_t pos = static_cast<int64_t>(s_first) + s_wc[warp] + __popc(m & ((1u << lane) - 1));
+            auto word = [&](int a) -> unsigned long long {
+                return AOS ? __ldcg(t + i * stride + 1 + a) : t[(1 + a) * S + i];
+            };
             if (pos < A.out.capacity) {
                 A.out.keys[pos] = static_cast<int64_t>(kx ^ GB_SIGN);
-                for (int a = 0; a < A.ops.n; a++) A.out.aggs[a][pos] = agg_decode(A.ops.op[a], __ldcg(cell + 1 + a));
+                for (int a = 0; a < A.ops.n; a++) A.out.aggs[a][pos] = agg_decode(A.ops.op[a], word(a));
                 if (A.cnt >= 0)
-                    write_avgs(A.out, pos, A.ops.n, A.cnt,
-                               [&](int a) { return agg_decode(A.ops.op[a], __ldcg(cell + 1 + a)); });
+                    write_avgs(A.out, pos, A.ops.n, A.cnt, [&](int a) { return agg_decode(A.ops.op[a], word(a)); });
             }
-            // an empty slot is all zeros already (its aggregate words are
-            // only touched once its key is set): zero the occupied ones
-            for (int w = 0; w < A.stride; w++) __stcg(cell + w, 0ull);
+            if (!AOS)
+                for (int w = 0; w < stride; w++) t[w * S + i] = 0ull;
         }
         __syncthreads();
     }
 }
 
-// Bounded wait (thread 0) until *ctr reaches want; false on expiry, or at
-// once after any earlier wait of the launch expired.
-__device__ __forceinline__ bool pp_wait(const unsigned *ctr, unsigned want, int64_t limit, unsigned *abort)
+// Emit the groups of a shared-memory table (keys[S], then aggs[a][S]) and
+// zero their slots.  Output positions: every warp-sized group of 32 slots
+// counts its occupied slots, the S / 32 counts are scanned in shared memory
+// and one global atomic reserves the table's run, so the writes stay in slot
+// order, as coalesced as the occupancy allows.
+template <int T>
+__device__ void pp_emit_table(const FoldArgs &A, unsigned long long *t, int log2s, int stride)
 {
-    int64_t spins = 0;
-    while (*reinterpret_cast<const volatile unsigned *>(ctr) < want) {
-        if (++spins > limit || *reinterpret_cast<const volatile unsigned *>(abort)) {
-            atomicExch(abort, 1u);
-            return false;
-        }
-        __nanosleep(64);
+    constexpr int NW = T / 32;
+    __shared__ unsigned s_cnt[F_EMIT_GROUPS];
+    __shared__ unsigned long long s_first;
+    const int S = 1 << log2s, G = S >> 5;              // slot groups of 32
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int g = warp; g < G; g += NW) {
+        const unsigned m = __ballot_sync(QE_FULL_MASK, t[g * 32 + lane] != 0);
+        if (lane == 0) s_cnt[g] = __popc(m);
     }
-    __threadfence();
-    return true;
-}
-
-// Thread 0: claim the next item and wait (bounded) for what it depends on;
-// s_ok = 0 when the wait expired.
-__device__ __forceinline__ void pp_claim(const FoldArgs &A, long long &s_item, int &s_ok)
-{
-    const int parts = 1 << A.log2p;
-    const int64_t per_stage = static_cast<int64_t>(A.nblk) + A.chunks;
-    const int64_t it = static_cast<int64_t>(atomicAdd(A.items, 1ull));
-    s_item = it;
-    s_ok = 1;
-    if (it >= A.nitems) return;
-    const int64_t stage = it / per_stage, r = it % per_stage;
-    if (r < A.nblk) {
-        const int p = static_cast<int>(stage);
-        if (p < parts && p >= A.ring)
-            s_ok = pp_wait(A.done_comp + (p - A.ring), static_cast<unsigned>(A.chunks), A.spin_limit, A.abort);
-    } else if (stage >= A.lag && stage - A.lag < parts) {
-        s_ok = pp_wait(A.done_fold + (stage - A.lag), static_cast<unsigned>(A.nblk), A.spin_limit, A.abort);
-    }
-}
-
-__global__ void __launch_bounds__(FPT, 2) k_pp_fold(FoldArgs A)
-{
-    __shared__ long long s_item;
-    __shared__ int s_ok;
-    const int parts = 1 << A.log2p;
-    const int64_t per_stage = static_cast<int64_t>(A.nblk) + A.chunks;
-    const int64_t wslots = int64_t(1) << A.log2w;
-    if (threadIdx.x == 0) pp_claim(A, s_item, s_ok);
     __syncthreads();
-    while (true) {
-        const int64_t it = s_item;
-        const bool ok = s_ok;
-        if (it >= A.nitems) break;
-        const int64_t stage = it / per_stage, r = it % per_stage;
-        unsigned *done = nullptr;
-        if (r < A.nblk) {
-            // fold segment (stage, r) into window stage mod ring
-            const int p = static_cast<int>(stage);
-            if (p < parts) {
-                const int64_t j = static_cast<int64_t>(p) * A.nblk + r;
-                if (ok && QE_DCHECK(A.st, A.seg[j] >= 0 && A.seg[j] + A.fill[j] <= A.nrows, A.seg[j] + A.fill[j]))
-                    pp_fold_segment(A, A.win + static_cast<int64_t>(p & (A.ring - 1)) * wslots * A.stride,
-                                    A.rows + A.seg[j], A.fill[j]);
-                done = A.done_fold + p;
-            }
-        } else if (stage >= A.lag && stage - A.lag < parts) {
-            // compaction chunk c of part stage - lag, whose fold items were
-            // claimed lag stages earlier
-            const int q = static_cast<int>(stage - A.lag);
-            const int64_t c = r - A.nblk, span = wslots / A.chunks;
-            if (ok)
-                pp_compact_chunk(A, A.win + static_cast<int64_t>(q & (A.ring - 1)) * wslots * A.stride, c * span,
-                                 (c + 1) * span);
-            done = A.done_comp + q;
+    if (warp == 0) {
+        // exclusive scan of the G <= F_EMIT_GROUPS counts, G / 32 per lane
+        const int per = (G + 31) >> 5;
+        unsigned loc = 0;
+        for (int j = 0; j < per; j++) {
+            const int g = lane * per + j;
+            if (g < G) loc += s_cnt[g];
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            if (!ok) dev_report(A.st, QE_ERR_TIMEOUT, 0);
-            if (done) {
-                __threadfence();
-                atomicAdd(done, 1u);
+        const unsigned inc = warp_incl_scan(loc);
+        unsigned run = inc - loc;
+        for (int j = 0; j < per; j++) {
+            const int g = lane * per + j;
+            if (g < G) {
+                const unsigned c = s_cnt[g];
+                s_cnt[g] = run;
+                run += c;
             }
-            pp_claim(A, s_item, s_ok);
         }
-        __syncthreads();
+        if (lane == 31) s_first = inc ? atomicAdd(A.emitted, static_cast<unsigned long long>(inc)) : 0ull;
     }
+    __syncthreads();
+    for (int g = warp; g < G; g += NW) {
+        const int i = g * 32 + lane;
+        const unsigned long long kx = t[i];
+        const unsigned m = __ballot_sync(QE_FULL_MASK, kx != 0);
+        if (!kx) continue;
+        const int64_t pos = static_cast<int64_t>(s_first) + s_cnt[g] + __popc(m & ((1u << lane) - 1));
+        if (pos < A.out.capacity) {
+            A.out.keys[pos] = static_cast<int64_t>(kx ^ GB_SIGN);
+            for (int a = 0; a < A.ops.n; a++) A.out.aggs[a][pos] = agg_decode(A.ops.op[a], t[(1 + a) * S + i]);
+            if (A.cnt >= 0) write_avgs(A.out, pos, A.ops.n, A.cnt, [&](int a) { return agg_decode(A.ops.op[a], t[(1 + a) * S + i]); });
+        }
+        for (int w = 0; w < stride; w++) t[w * S + i] = 0ull;
+    }
+    __syncthreads();
+}
+
+// STAR: the aggregates are [SUM(X*Y), COUNT, MIN(X), MAX(X)] (the shared
+// COUNT word then holds a 32-bit count, read back whole: its high half stays 0).
+template <int T, int MINB, bool STAR>
+__global__ void __launch_bounds__(T, MINB) k_pp_fold(FoldArgs A)
+{
+    static_assert(T <= F_RUNS, "a block describes at most F_RUNS runs at a time");
+    extern __shared__ __align__(16) unsigned char f_smem[];
+    const uint64_t S = uint64_t(1) << A.log2s;
+    const int stride = 1 + A.ops.n;
+    unsigned long long *tab = reinterpret_cast<unsigned long long *>(f_smem);          // keys[S], aggs[a][S]
+    int64_t *rstart = reinterpret_cast<int64_t *>(tab + S * stride);                   // [F_RUNS]
+    unsigned *rlen = reinterpret_cast<unsigned *>(rstart + F_RUNS);                    // [F_RUNS]
+    __shared__ long long s_item;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int Q = 1 << A.log2q;
+    const int64_t nsub = int64_t(1) << (A.log2p + A.log2q);
+    for (uint64_t i = threadIdx.x; i < S * stride; i += T) tab[i] = 0ull;
+    while (true) {
+        if (threadIdx.x == 0) s_item = static_cast<long long>(atomicAdd(A.counter, 1ull));
+        __syncthreads();
+        const int64_t f = s_item;
+        if (f >= nsub) break;
+        const int64_t p = f >> A.log2q, q = f & (Q - 1);
+        const int64_t c0 = A.cpre[p * A.nblk], c1 = A.cpre[(p + 1) * A.nblk];
+        for (int64_t cb = c0; cb < c1; cb += T) {      // T <= F_RUNS runs at a time
+            const int nr = static_cast<int>(c1 - cb < T ? c1 - cb : T);
+            // the runs of sub-part q in chunks cb .. cb + nr
+            if (threadIdx.x < nr) {
+                const int64_t c = cb + threadIdx.x;
+                const uint16_t *o = A.off2 + c * (Q + 1);
+                const unsigned o0 = o[q], o1 = o[q + 1];
+                rlen[threadIdx.x] = o1 - o0;
+                rstart[threadIdx.x] = A.cstart[c] + o0;
+            }
+            __syncthreads();
+            // each warp takes whole runs (about 60 rows each at the planned
+            // sizes): its lanes read consecutive rows of the run
+            for (int r = warp; r < nr; r += T / 32) {
+                const int64_t r0 = rstart[r];
+                const unsigned len = rlen[r];
+                for (unsigned i0 = 0; i0 < len; i0 += 32 * F_ITEMS) {
+                    unsigned long long kx[F_ITEMS];
+                    long long xv[F_ITEMS], yv[F_ITEMS];
+#pragma unroll
+                    for (int t = 0; t < F_ITEMS; t++) {
+                        const unsigned i = i0 + t * 32 + lane;
+                        kx[t] = 0;
+                        xv[t] = yv[t] = 0;
+                        if (i < len) {
+                            const PartRow *row = A.rows2 + r0 + i;
+                            kx[t] = __ldcs(&row->kx);
+                            xv[t] = __ldcs(&row->x);
+                            yv[t] = __ldcs(&row->y);
+                        }
+                    }
+#pragma unroll
+                    for (int t = 0; t < F_ITEMS; t++) {
+                        if (!kx[t]) continue;
+                        const uint32_t mask = static_cast<uint32_t>(S - 1);
+                        uint32_t h = static_cast<uint32_t>(dev_fmix64(kx[t])) & mask;
+                        int slot = -1;
+                        for (int pr = 0; pr < F_PROBES; pr++) {
+                            const unsigned long long cur = reinterpret_cast<volatile unsigned long long *>(tab)[h];
+                            if (cur == kx[t]) {
+                                slot = static_cast<int>(h);
+                                break;
+                            }
+                            if (cur == 0) {
+                                const unsigned long long old = atomicCAS(tab + h, 0ull, kx[t]);
+                                if (old == 0 || old == kx[t]) {
+                                    slot = static_cast<int>(h);
+                                    break;
+                                }
+                            }
+                            h = (h + 1) & mask;
+                        }
+                        if constexpr (STAR) {
+                            // [SUM(X*Y), COUNT, MIN(X), MAX(X)]: the encodings
+                            // inline, COUNT as a 32-bit counter in its word's
+                            // low half (a sub-part has fewer than 2^32 rows)
+                            const unsigned long long v = static_cast<unsigned long long>(xv[t]) *
+                                                         static_cast<unsigned long long>(yv[t]);
+                            const unsigned long long emin = ~(static_cast<unsigned long long>(xv[t]) ^ GB_SIGN);
+                            const unsigned long long emax = static_cast<unsigned long long>(xv[t]) ^ GB_SIGN;
+                            if (slot >= 0) {
+                                smem_add64(tab + S + slot, v);
+                                atomicAdd(reinterpret_cast<unsigned *>(tab + 2 * S + slot), 1u);
+                                unsigned long long *cmin = tab + 3 * S + slot, *cmax = tab + 4 * S + slot;
+                                if (*cmin < emin) atomicMax(cmin, emin);
+                                if (*cmax < emax) atomicMax(cmax, emax);
+                            } else {
+                                pp_spill_ni(A.spill, A.ops, kx[t], v, 1ull, emin, emax);
+                            }
+                        } else {
+                            unsigned long long e[QE_MAX_AGGS];
+#pragma unroll
+                            for (int a = 0; a < QE_MAX_AGGS; a++) e[a] = a < A.ops.n ? pp_value(A, a, xv[t], yv[t]) : 0ull;
+                            if (slot >= 0) {
+#pragma unroll
+                                for (int a = 0; a < QE_MAX_AGGS; a++)
+                                    if (a < A.ops.n) st_update(tab + (1 + a) * S + slot, A.ops.op[a], e[a]);
+                            } else {
+                                pp_spill_ni(A.spill, A.ops, kx[t], e[0], e[1], e[2], e[3]);
+                            }
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        pp_emit_table<T>(A, tab, A.log2s, stride);
+    }
+}
+
+// The spill table's groups, appended to the output.
+__global__ void __launch_bounds__(FT) k_pp_spill_emit(FoldArgs A)
+{
+    const uint64_t slots = A.spill.mask + 1;
+    const uint64_t per = (slots + gridDim.x - 1) / gridDim.x;
+    const uint64_t s0 = blockIdx.x * per, s1 = s0 + per < slots ? s0 + per : slots;
+    pp_emit<true, FT>(A, A.spill.words, 0, s0, s1, A.spill.stride);
 }
 
 __global__ void k_pp_count_out(const unsigned long long *emitted, int64_t capacity, int64_t *ngroups, qe_dev_status *st)
@@ -683,31 +843,30 @@ __global__ void k_pp_count_out(const unsigned long long *emitted, int64_t capaci
 
 }  // namespace
 
-// Parameters of the partitioned group-by for `groups` expected groups with
-// `stride` words per slot: parts (log2p), window slots (log2w) and ring
-// windows, so that every window takes its part's groups at a load of at
-// most about 2/3 and the whole ring stays within `ring_bytes` of L2.
+// Parameters of the partitioned group-by for `groups` (at most) groups:
+// parts of the scatter (log2p; at most 256, so a block writes few pages at
+// a time), sub-parts per part (log2q) and shared-table slots (log2s), so
+// that a sub-part's groups fill its shared table to about 60 % on average.
 struct PartPlan {
-    int log2p = 0, log2w = 0, ring = 0, chunks = 0;
+    int log2p = 0, log2q = 0, log2s = 0;
 };
 
-static PartPlan part_plan(int64_t groups, int stride, int log2p_hint)
+static PartPlan part_plan(int64_t groups, int naggs, size_t smem_budget, int log2p_hint, int log2q_hint)
 {
     PartPlan pl;
-    const uint64_t ring_bytes = 48ull << 20;
-    pl.ring = 4;
-    for (int lp = 1; lp <= 10; lp++) {
-        const uint64_t per = static_cast<uint64_t>(groups + (int64_t(1) << lp) - 1) >> lp;
-        int lw = 12;
-        while ((uint64_t(1) << lw) < per + per / 2) lw++;
-        pl.log2p = lp;
-        pl.log2w = lw;
-        if (log2p_hint > 0 ? lp == log2p_hint
-                           : (uint64_t(1) << lw) * stride * 8 * static_cast<uint64_t>(pl.ring) <= ring_bytes)
-            break;
-    }
-    pl.chunks = static_cast<int>((int64_t(1) << pl.log2w) / 8192);
-    if (pl.chunks < 1) pl.chunks = 1;
+    // shared-table slots: the largest power of two whose table (and the run
+    // descriptors) fits the shared-memory budget, at most 4096
+    int ls = 12;
+    while (ls > 6 && ((size_t(1) << ls) * (1 + naggs) * 8 + F_RUNS * 12 + 64) > smem_budget) ls--;
+    pl.log2s = ls;
+    const uint64_t per_sub = (uint64_t(1) << ls) * 6 / 10;      // groups per sub-part at ~60 % load
+    const uint64_t subs = (static_cast<uint64_t>(groups > 0 ? groups : 1) + per_sub - 1) / per_sub;
+    int lt = 0;
+    while ((uint64_t(1) << lt) < subs) lt++;
+    pl.log2p = log2p_hint > 0 ? log2p_hint : (lt < 8 ? (lt > 1 ? lt : 1) : 8);
+    pl.log2q = lt > pl.log2p ? lt - pl.log2p : 0;
+    if (pl.log2q > 8) pl.log2q = 8;
+    if (log2q_hint >= 0) pl.log2q = log2q_hint;
     return pl;
 }
 
@@ -737,21 +896,34 @@ static const void *pp_star_kernel(int kind)
 qe_status pipeline_partitioned(qe_ctx *ctx, PipeSpec &P, const qe_groups_out *out, int64_t groups, cudaStream_t s)
 {
     const int stride = 1 + P.ops.n;
-    const PartPlan pl = part_plan(groups, stride, ctx->tune_gb_part_log2p);
-    const int parts = 1 << pl.log2p;
+    // fold shape: one 1,024-thread block per SM with the largest shared
+    // table, or two 512-thread blocks with half-size tables each, so that
+    // one block's hand-over between sub-parts overlaps the other's rows
+    const bool fold2 = ctx->tune_gb_fold2 != 0;
+    const size_t smem_per_sm = ctx->smem_optin > 2048 ? ctx->smem_optin - 2048 : 0;
+    const size_t smem_budget = fold2 ? smem_per_sm / 2 - 1024 : smem_per_sm;
+    const PartPlan pl = part_plan(groups, P.ops.n, smem_budget, ctx->tune_gb_part_log2p, ctx->tune_gb_part_log2q);
+    const int parts = 1 << pl.log2p, Q = 1 << pl.log2q;
     const int nblk = ctx->num_sms;
     const int64_t tr = static_cast<int64_t>(PPT) * PP_ITEMS;
     int64_t rpb = qe_ceil_div(qe_ceil_div(P.n > 0 ? P.n : 1, nblk), tr) * tr;
     const int64_t m = static_cast<int64_t>(parts) * nblk;
-    const int64_t wslots = int64_t(1) << pl.log2w;
+    // chunks: at most one per SPLIT_ROWS rows plus one per segment
+    const int64_t max_chunks = P.n / SPLIT_ROWS + m + 1;
+    // spill table for keys that find no shared slot (skewed hashes): an
+    // eighth of the groups, at least 64K
+    const int64_t spill_cap = groups / 8 > 65536 ? groups / 8 : 65536;
+    uint64_t spill_slots = 64;
+    while (spill_slots < static_cast<uint64_t>(2 * spill_cap)) spill_slots <<= 1;
     auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
     const size_t b_rows = up(static_cast<size_t>(P.n) * sizeof(PartRow));
-    const size_t b_cnt = up(m * 4), b_seg = up(m * 8), b_fill = up(m * 4);
-    const size_t b_win = up(static_cast<size_t>(pl.ring) * wslots * stride * 8);
-    const size_t b_done = up(static_cast<size_t>(parts) * 8);
+    const size_t b_cnt = up(m * 4), b_seg = up(m * 8), b_fill = up(m * 4), b_cpre = up((m + 1) * 8);
+    const size_t b_off2 = up(static_cast<size_t>(max_chunks) * (Q + 1) * 2), b_cstart = up(max_chunks * 8);
+    const size_t b_spill = up(spill_slots * stride * 8);
     const size_t b_ctr = 256;
     void *mem = nullptr;
-    qe_status st = qe_alloc(ctx, &mem, b_rows + b_cnt + b_seg + b_fill + b_win + b_done + b_ctr, s);
+    qe_status st = qe_alloc(ctx, &mem,
+                            2 * b_rows + b_cnt + b_seg + b_fill + b_cpre + b_off2 + b_cstart + b_spill + b_ctr, s);
     if (st != QE_OK) return st;
     char *c = static_cast<char *>(mem);
     PartArgs A{};
@@ -761,57 +933,89 @@ qe_status pipeline_partitioned(qe_ctx *ctx, PipeSpec &P, const qe_groups_out *ou
     A.rows_per_blk = rpb;
     A.count_all = P.lo_slot != QE_JOIN_PAYLOAD;
     A.rows = reinterpret_cast<PartRow *>(c);
-    A.cnt = reinterpret_cast<uint32_t *>(c + b_rows);
-    A.seg = reinterpret_cast<int64_t *>(c + b_rows + b_cnt);
-    A.fill = reinterpret_cast<uint32_t *>(c + b_rows + b_cnt + b_seg);
-    char *zero = c + b_rows + b_cnt + b_seg + b_fill;   // window ring, done counters, item and group counters
-    cudaError_t e = cudaMemsetAsync(zero, 0, b_win + b_done + b_ctr, s);
+    PartRow *rows2 = reinterpret_cast<PartRow *>(c + b_rows);
+    char *q = c + 2 * b_rows;
+    A.cnt = reinterpret_cast<uint32_t *>(q);
+    A.seg = reinterpret_cast<int64_t *>(q + b_cnt);
+    A.fill = reinterpret_cast<uint32_t *>(q + b_cnt + b_seg);
+    int64_t *cpre = reinterpret_cast<int64_t *>(q + b_cnt + b_seg + b_fill);
+    uint16_t *off2 = reinterpret_cast<uint16_t *>(q + b_cnt + b_seg + b_fill + b_cpre);
+    int64_t *cstart = reinterpret_cast<int64_t *>(q + b_cnt + b_seg + b_fill + b_cpre + b_off2);
+    char *zero = q + b_cnt + b_seg + b_fill + b_cpre + b_off2 + b_cstart;   // spill table, counters
+    cudaError_t e = cudaMemsetAsync(zero, 0, b_spill + b_ctr, s);
+    unsigned long long *ctr = reinterpret_cast<unsigned long long *>(zero + b_spill);
+
+    SplitArgs SA{};
+    SA.log2p = pl.log2p;
+    SA.log2q = pl.log2q;
+    SA.nblk = nblk;
+    SA.m = m;
+    SA.nrows = P.n;
+    SA.st = ctx->dstat;
+    SA.seg = A.seg;
+    SA.fill = A.fill;
+    SA.cpre = cpre;
+    SA.rows = A.rows;
+    SA.rows2 = rows2;
+    SA.off2 = off2;
+    SA.cstart = cstart;
+    SA.counter = ctr;
+
     FoldArgs F{};
     F.ops = P.ops;
     for (int a = 0; a < QE_MAX_AGGS; a++) F.src[a] = P.src[a];
     F.log2p = pl.log2p;
+    F.log2q = pl.log2q;
     F.nblk = nblk;
-    F.log2w = pl.log2w;
-    F.ring = pl.ring;
-    F.chunks = pl.chunks;
-    F.stride = stride;
+    F.log2s = pl.log2s;
     F.cnt = -1;
     for (int a = 0; a < QE_MAX_AGGS; a++)
         if (out->avg[a]) F.cnt = agg_count_index(P.ops);
-    F.seg = A.seg;
-    F.fill = A.fill;
-    F.rows = A.rows;
-    F.win = reinterpret_cast<unsigned long long *>(zero);
-    F.done_fold = reinterpret_cast<unsigned *>(zero + b_win);
-    F.done_comp = F.done_fold + parts;
-    F.items = reinterpret_cast<unsigned long long *>(zero + b_win + b_done);
-    F.emitted = F.items + 1;
-    F.abort = reinterpret_cast<unsigned *>(F.items + 2);
+    F.cpre = cpre;
+    F.off2 = off2;
+    F.cstart = cstart;
+    F.rows2 = rows2;
+    F.spill.words = reinterpret_cast<unsigned long long *>(zero);
+    F.spill.mask = spill_slots - 1;
+    F.spill.stride = stride;
+    F.spill.capacity = out->capacity;
+    F.spill.st = ctx->dstat;
+    F.counter = ctr + 1;
+    F.emitted = ctr + 2;
     F.out = *out;
-    F.lag = pl.ring > 2 ? pl.ring - 2 : 1;
-    F.nitems = static_cast<int64_t>(parts + F.lag) * (nblk + pl.chunks);
-    F.nrows = P.n;
-    F.spin_limit = ctx->spin_limit;
     F.st = ctx->dstat;
+
     const size_t sm_count = static_cast<size_t>(parts) * 4;
     const size_t sm_scatter = pp_scatter_smem(parts);
+    const size_t sm_split = pp_split_smem(pl.log2q);
+    const size_t sm_fold = (size_t(1) << pl.log2s) * stride * 8 + F_RUNS * 12 + 64;
     // the scatter kernel: the star shape's register-prefetched loop, or the generic one
     const int skind = ctx->tune_force_generic ? -1 : pp_star_kind(P);
     const void *kscatter = reinterpret_cast<const void *>(k_pp_scatter);
     if (skind >= 0) {
-        PipeSpec &Q = A.P;
-        star_predicate(Q);
-        kscatter = Q.type[Q.lo_slot] == QE_I64 ? pp_star_kernel<true>(skind) : pp_star_kernel<false>(skind);
+        PipeSpec &Qs = A.P;
+        star_predicate(Qs);
+        kscatter = Qs.type[Qs.lo_slot] == QE_I64 ? pp_star_kernel<true>(skind) : pp_star_kernel<false>(skind);
     }
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(kscatter, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm_scatter));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pp_split, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm_split));
+    const bool star_aggs = P.ops.n == 4 && P.ops.op[0] == QE_SUM && P.src[0] == SRC_XY && P.ops.op[1] == QE_COUNT &&
+                           P.ops.op[2] == QE_MIN && P.src[2] == SRC_X && P.ops.op[3] == QE_MAX && P.src[3] == SRC_X;
+    const void *kfold = fold2 ? (star_aggs ? reinterpret_cast<const void *>(k_pp_fold<FT / 2, 2, true>)
+                                           : reinterpret_cast<const void *>(k_pp_fold<FT / 2, 2, false>))
+                              : (star_aggs ? reinterpret_cast<const void *>(k_pp_fold<FT, 1, true>)
+                                           : reinterpret_cast<const void *>(k_pp_fold<FT, 1, false>));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kfold, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm_fold));
     if (e == cudaSuccess && P.n > 0) {
         {
             ProfScope prof(ctx, "part_count", s);
             k_pp_count<<<nblk, PPT, sm_count, s>>>(A);
             QE_LAUNCHED(ctx);
         }
-        k_pp_scan<<<1, PPT, 0, s>>>(A.cnt, m, A.seg);
+        k_pp_scan<<<1, PPT, 0, s>>>(A.cnt, m, A.seg, 0, nullptr);
         QE_LAUNCHED(ctx);
         e = cudaGetLastError();
         if (e == cudaSuccess) {
@@ -821,8 +1025,21 @@ qe_status pipeline_partitioned(qe_ctx *ctx, PipeSpec &P, const qe_groups_out *ou
             QE_LAUNCHED(ctx);
         }
         if (e == cudaSuccess) {
+            k_pp_scan<<<1, PPT, 0, s>>>(A.fill, m, cpre, SPLIT_ROWS, cpre + m);
+            QE_LAUNCHED(ctx);
+            ProfScope prof(ctx, "part_split", s);
+            k_pp_split<<<nblk, SPT, sm_split, s>>>(SA);
+            QE_LAUNCHED(ctx);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) {
             ProfScope prof(ctx, "part_fold", s);
-            k_pp_fold<<<2 * nblk, FPT, 0, s>>>(F);
+            void *fargs[] = {&F};
+            e = cudaLaunchKernel(kfold, dim3(fold2 ? 2 * nblk : nblk), dim3(fold2 ? FT / 2 : FT), fargs, sm_fold, s);
+            QE_LAUNCHED(ctx);
+        }
+        if (e == cudaSuccess) {
+            k_pp_spill_emit<<<nblk, FT, 0, s>>>(F);
             QE_LAUNCHED(ctx);
             e = cudaGetLastError();
         }

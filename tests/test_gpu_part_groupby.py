@@ -2,14 +2,16 @@
 the CPU oracle, bit-exact.
 
 A pipeline whose groups only fit an HBM hash table far larger than L2 runs
-in four steps: count each row's part (top bits of the key's hash), scan,
-scatter the survivors into per-part segments, then aggregate part after part
-in a ring of L2-resident hash windows, emitting each window's groups straight
-into the output (Sec. 7.2 on large hash tables; Sec. 2.2 on one partitioning
-function applied before the local operator).  The knob "gb_partition" = 2
-forces that path at test sizes, and "gb_part_log2p" sets the number of parts,
-so every part count from 2 to 1024 is covered, as are group keys from fact
-columns (every row counted from its key columns) and from the join payload
+as: count each row's part (top bits of the key's hash), scan, scatter the
+survivors into per-part segments, split every part into sub-parts (the next
+hash bits), then aggregate each sub-part in one block's shared-memory hash
+table and write its groups straight into the output (Sec. 7.2 on large hash
+tables; Sec. 2.2 on one partitioning function applied before the local
+operator).  The knob "gb_partition" = 2 forces that path at test sizes,
+"gb_part_log2p" sets the number of parts (2 .. 1024 are covered) and
+"gb_part_log2q" the sub-parts, so the spill to the HBM table of keys that
+find no shared slot is covered too, as are group keys from fact columns
+(every row counted from its key columns) and from the join payload
 (survivors counted), semi- and anti-joins, empty and ragged inputs, many
 groups per part, averages, reserved keys and too-small outputs.
 """
@@ -91,12 +93,34 @@ def test_part_groupby_int64_keys(ctx, log2p, generic):
         ctx.set_tuning("force_generic", 0)
 
 
-@pytest.mark.parametrize("date_lt", [0, 26, 2301, 2557])
-def test_part_groupby_selectivity(ctx, date_lt):
-    """0 %, 1 %, 90 % and 100 % of the rows, dictionary-code keys."""
-    fact, dim = _skew(700_001, 30_000, 100_000, seed=62)
-    g = _run(ctx, fact, dim, 5, date_lt, 131_072)
-    _equal(g, _oracle(fact, dim, 5, date_lt))
+@pytest.mark.parametrize("log2q", [4, 5])
+def test_part_groupby_spill(ctx, log2q):
+    """Too few sub-parts for the groups (200K groups in 2 x 16 or 2 x 32
+    sub-parts of a 4,096-slot shared table): a third of the keys, or a few,
+    find no shared slot and spill to the HBM table; the result is still
+    exact."""
+    ctx.set_tuning("gb_part_log2p", 1)
+    ctx.set_tuning("gb_part_log2q", log2q)
+    try:
+        fact, dim = _skew(800_000, 20_000, 200_000, seed=69)
+        g = _run(ctx, fact, dim, 6, 2557, 1 << 20)
+        _equal(g, _oracle(fact, dim, 6, 2557))
+    finally:
+        ctx.set_tuning("gb_part_log2p", 0)
+        ctx.set_tuning("gb_part_log2q", -1)
+
+
+@pytest.mark.parametrize("date_lt,fold2", [(0, 0), (26, 0), (2301, 0), (2557, 0), (26, 1), (2301, 1)])
+def test_part_groupby_selectivity(ctx, date_lt, fold2):
+    """0 %, 1 %, 90 % and 100 % of the rows, dictionary-code keys; the fold
+    as one 1,024-thread block per SM and as two 512-thread blocks."""
+    ctx.set_tuning("gb_fold2", fold2)
+    try:
+        fact, dim = _skew(700_001, 30_000, 100_000, seed=62)
+        g = _run(ctx, fact, dim, 5, date_lt, 131_072)
+        _equal(g, _oracle(fact, dim, 5, date_lt))
+    finally:
+        ctx.set_tuning("gb_fold2", 0)
 
 
 def test_part_groupby_payload_and_hi_keys(ctx):
