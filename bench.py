@@ -531,7 +531,7 @@ def run_skew(args, qe, ctx, dev, stream, peak, it):
 
     for colname, ci, span in (("date", 1, datagen.DATE_SPAN), ("code", 5, 1_000_000)):
         sweep = {}
-        for sel in SKEW_SWEEP:
+        for sel in args.skew_sweep:
             c = int(round(sel * span))
             ms, kern, ng = one((ci, qe.LT, c), 4, cap, sel)
             nsurv = None
@@ -831,6 +831,8 @@ def main():
                     help="fact rows (and pairs) per reference-arm step")
     ap.add_argument("--cpu-sample", type=int, default=32_000_000,
                     help="fact rows (and pairs) of the cpu_baseline sample")
+    ap.add_argument("--skew-sweep", type=lambda v: tuple(float(x) for x in v.split(",")), default=SKEW_SWEEP,
+                    help="selectivities of the skewed pipeline's sweeps (comma-separated)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()

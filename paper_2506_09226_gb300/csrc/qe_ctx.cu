@@ -112,6 +112,9 @@ extern "C" qe_status qe_set_tuning(qe_ctx *ctx, const char *name, int64_t value)
         ctx->tune_force_generic = value != 0;
     } else if (n == "part_general") {
         ctx->tune_part_general = value != 0;
+    } else if (n == "part_span") {
+        if (value < 0 || value > 1024) return qe_fail(ctx, QE_ERR_INVALID_ARG, "part_span must be in [0, 1024]");
+        ctx->tune_part_span = static_cast<int>(value);
     } else if (n == "l2_hint") {
         ctx->tune_l2_hint = value != 0;
     } else if (n == "gb_partition") {

@@ -43,6 +43,7 @@ struct qe_ctx {
     int tune_star_items = 0;        // 0: default
     int tune_force_generic = 0;
     int tune_part_general = 0;      // partition: skip the write-combining scatter
+    int tune_part_span = 0;         // two-pass partition: first-pass ranges per second-pass item (0 = 8)
     int tune_gb_partition = 0;      // large HBM group tables: 0 auto, 1 never partition, 2 always
     int tune_gb_part_log2p = 0;     // parts of the partitioned group-by (log2; 0 = planned)
     int tune_gb_part_log2q = -1;    // sub-parts per part (log2; -1 = planned)

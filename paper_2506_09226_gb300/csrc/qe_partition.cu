@@ -56,6 +56,7 @@ struct PartArgs {
     int sub_bits;             // two passes: bits of the second-pass digit
     int64_t nitems;           // work items (WC_SINGLE / WC_PASS1: one per block range)
     int g1;                   // two passes: first-pass block ranges
+    int span;                 // two passes: first-pass ranges per second-pass item
     const int64_t *t1;        // two passes: [g1][F1] first-pass start of (range, digit)
     const uint32_t *h1;       // two passes: [g1][F1] rows of (range, digit)
 };
@@ -309,11 +310,16 @@ __global__ void __launch_bounds__(T, MINB) k_part_scatter_wc(PartArgs A)
         int64_t lo, hi;
         int b = static_cast<int>(item), qhi = 0;
         if (A.omode == WC_PASS2) {
-            qhi = static_cast<int>(item / A.g1);
-            b = static_cast<int>(item % A.g1);
-            const int64_t j = static_cast<int64_t>(b) * (Ffull >> A.sub_bits) + qhi;
-            lo = A.t1[j];
-            hi = lo + A.h1[j];
+            // ranges [b, b1) of high digit q: their scratch rows are one run
+            // (t1[b + 1][q] = t1[b][q] + h1[b][q]), and so are their output
+            // rows of each destination (q, r), in range order
+            const int nspan = (A.g1 + A.span - 1) / A.span;
+            qhi = static_cast<int>(item / nspan);
+            b = static_cast<int>(item % nspan) * A.span;
+            const int b1 = b + A.span < A.g1 ? b + A.span : A.g1;
+            const int64_t F1 = Ffull >> A.sub_bits;
+            lo = A.t1[static_cast<int64_t>(b) * F1 + qhi];
+            hi = A.t1[static_cast<int64_t>(b1 - 1) * F1 + qhi] + A.h1[static_cast<int64_t>(b1 - 1) * F1 + qhi];
         } else {
             lo = static_cast<int64_t>(b) * A.rows_per_block;
             hi = min(A.n, lo + A.rows_per_block);
@@ -827,9 +833,10 @@ extern "C" qe_status qe_partition(qe_ctx *ctx, const int64_t *keys, const qe_col
             A2.omode = WC_PASS2;
             A2.sub_bits = sub_bits;
             A2.g1 = static_cast<int>(G);
+            A2.span = ctx->tune_part_span > 0 ? ctx->tune_part_span : 8;
             A2.t1 = t1;
             A2.h1 = h1;
-            A2.nitems = G * F1;
+            A2.nitems = qe_ceil_div(G, A2.span) * F1;
             void *args2[] = {&A2};
             e = cudaLaunchKernel(ws2.kernel, dim3(static_cast<unsigned>(G2)), dim3(ws2.threads), args2, smem2, s);
             QE_LAUNCHED(ctx);

@@ -594,6 +594,7 @@ struct FoldArgs {
     GTable spill;
     unsigned long long *counter;                // sub-part claims
     unsigned long long *emitted;                // groups written to `out`
+    unsigned *spilled;                          // set once any key went to the spill table
     qe_groups_out out;
     qe_dev_status *st;
 };
@@ -608,10 +609,11 @@ __device__ __forceinline__ unsigned long long pp_value(const FoldArgs &A, int a,
 
 static __device__ __noinline__ void pp_spill_ni(const GTable g, const AggOps ops, unsigned long long kx,
                                                 unsigned long long e0, unsigned long long e1, unsigned long long e2,
-                                                unsigned long long e3)
+                                                unsigned long long e3, unsigned *spilled)
 {
     const unsigned long long e[QE_MAX_AGGS] = {e0, e1, e2, e3};
     gt_fold_row(g, ops, kx, e);
+    if (*reinterpret_cast<volatile unsigned *>(spilled) == 0) atomicExch(spilled, 1u);
 }
 
 // Emit n words-per-slot table rows [s0, s1) of a table with `stride`
@@ -802,7 +804,7 @@ __global__ void __launch_bounds__(T, MINB) k_pp_fold(FoldArgs A)
                                 if (*cmin < emin) atomicMax(cmin, emin);
                                 if (*cmax < emax) atomicMax(cmax, emax);
                             } else {
-                                pp_spill_ni(A.spill, A.ops, kx[t], v, 1ull, emin, emax);
+                                pp_spill_ni(A.spill, A.ops, kx[t], v, 1ull, emin, emax, A.spilled);
                             }
                         } else {
                             unsigned long long e[QE_MAX_AGGS];
@@ -813,7 +815,7 @@ __global__ void __launch_bounds__(T, MINB) k_pp_fold(FoldArgs A)
                                 for (int a = 0; a < QE_MAX_AGGS; a++)
                                     if (a < A.ops.n) st_update(tab + (1 + a) * S + slot, A.ops.op[a], e[a]);
                             } else {
-                                pp_spill_ni(A.spill, A.ops, kx[t], e[0], e[1], e[2], e[3]);
+                                pp_spill_ni(A.spill, A.ops, kx[t], e[0], e[1], e[2], e[3], A.spilled);
                             }
                         }
                     }
@@ -828,6 +830,7 @@ __global__ void __launch_bounds__(T, MINB) k_pp_fold(FoldArgs A)
 // The spill table's groups, appended to the output.
 __global__ void __launch_bounds__(FT) k_pp_spill_emit(FoldArgs A)
 {
+    if (*A.spilled == 0) return;           // nothing spilled: the table is empty
     const uint64_t slots = A.spill.mask + 1;
     const uint64_t per = (slots + gridDim.x - 1) / gridDim.x;
     const uint64_t s0 = blockIdx.x * per, s1 = s0 + per < slots ? s0 + per : slots;
@@ -910,9 +913,9 @@ qe_status pipeline_partitioned(qe_ctx *ctx, PipeSpec &P, const qe_groups_out *ou
     const int64_t m = static_cast<int64_t>(parts) * nblk;
     // chunks: at most one per SPLIT_ROWS rows plus one per segment
     const int64_t max_chunks = P.n / SPLIT_ROWS + m + 1;
-    // spill table for keys that find no shared slot (skewed hashes): an
-    // eighth of the groups, at least 64K
-    const int64_t spill_cap = groups / 8 > 65536 ? groups / 8 : 65536;
+    // spill table for keys that find no shared slot (skewed hashes): 1/32 of
+    // the groups, at least 128K (it is cleared on every call)
+    const int64_t spill_cap = groups / 32 > 131072 ? groups / 32 : 131072;
     uint64_t spill_slots = 64;
     while (spill_slots < static_cast<uint64_t>(2 * spill_cap)) spill_slots <<= 1;
     auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
@@ -982,6 +985,7 @@ qe_status pipeline_partitioned(qe_ctx *ctx, PipeSpec &P, const qe_groups_out *ou
     F.spill.st = ctx->dstat;
     F.counter = ctr + 1;
     F.emitted = ctr + 2;
+    F.spilled = reinterpret_cast<unsigned *>(ctr + 3);
     F.out = *out;
     F.st = ctx->dstat;
 
