@@ -542,6 +542,25 @@ def run_skew(args, qe, ctx, dev, stream, peak, it):
                 "hbm_frac": round(28 * n_fact / (ms * 1e-3) / 1e9 / peak, 4), "kernels_ms": kern,
                 "part_bytes": (8 * n_fact + 96 * nsurv) if nsurv is not None else 0}
         res[f"sweep_{colname}"] = sweep
+    # the autotuner's choice at 50 %: direct table or partitioned group-by
+    # (fan-out 64 / 128 / 256 parts), dense or open-addressing join table
+    from paper_2506_09226_gb300 import tune
+    c50 = int(round(0.5 * datagen.DATE_SPAN))
+    dt = qe.pipeline_desc(cols, [(1, qe.LT, c50)], fk_col=0, dim_key=dim["key"], dim_payload=dim["attr"],
+                          key_hi_col=-1, key_lo_col=4, aggs=aggs, expected_groups=cap, est_selectivity=0.5)
+    try:
+        part, log2p, layout = tune.tune_group_placement(
+            ctx, dt, lambda: qe.qe_pipeline(ctx, dt, cap, check=False, out=(groups, gout)), stream)
+        qe.qe_pipeline(ctx, dt, cap, check=False, out=(groups, gout))
+        ctx.sync_status()
+        ms = timed(lambda: qe.qe_pipeline(ctx, dt, cap, check=False, out=(groups, gout)), max(3, it // 3), stream)
+        res["autotuned_50%"] = {"ms": ms, "rows_per_s": n_fact / (ms * 1e-3), "ngroups": int(groups.ngroups.item()),
+                                "hbm_frac": round(28 * n_fact / (ms * 1e-3) / 1e9 / peak, 4),
+                                "choice": {"partitioned": part == 2, "parts_log2": log2p,
+                                           "join_layout": "dense" if layout == qe.HT_DENSE else "open"}}
+    finally:
+        ctx.set_tuning("gb_partition", 0)
+        ctx.set_tuning("gb_part_log2p", 0)
     # the direct HBM hash table at 50 %, for comparison
     ctx.set_tuning("gb_partition", 1)
     try:

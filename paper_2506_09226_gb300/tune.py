@@ -1,11 +1,15 @@
-"""Autotuner for launch shapes and group-table placement.
+"""Autotuner for launch shapes, group-table placement, partition fan-out
+and join-table layout.
 
 Candidates are timed on the device with CUDA events and the fastest is
 cached in a JSON file, keyed by a bucket of the workload's shape, so the
 search runs once per bucket:
   - batched form: rows per work item (16K .. 256K) and where per-block group
     tables live (shared memory, or HBM only);
-  - fused pipeline: rows per thread of the star-shape kernel (2 or 3).
+  - fused pipeline: rows per thread of the star-shape kernel (2 or 3);
+  - pipelines with many groups: the direct HBM hash table against the
+    partitioned group-by at several fan-outs (parts of its first pass), and
+    the join table's layout (dense array or open addressing).
 """
 from __future__ import annotations
 
@@ -21,6 +25,10 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), ".tune_cache.js
 BATCH_ITEM_ROWS = (1 << 14, 1 << 15, 1 << 16, 1 << 17, 1 << 18)
 BATCH_PLACEMENT = (0, -1)        # smem_slots: 0 = shared memory when it fits, -1 = HBM only
 STAR_ITEMS = (2, 3)
+# (gb_partition, gb_part_log2p): the direct HBM table, then the partitioned
+# group-by with 64, 128 or 256 parts (0 = planned)
+GROUP_PLACEMENT = ((1, 0), (2, 6), (2, 7), (2, 8))
+JOIN_LAYOUTS = (qe.HT_DENSE, qe.HT_OPEN)
 
 
 def batch_bucket(sizes) -> str:
@@ -99,4 +107,48 @@ def tune_pipeline(ctx, n_fact: int, groups: int, run, stream, steps: int = 3, pa
         return a.elapsed_time(e) / steps
     best = search(pipeline_bucket(n_fact, groups), list(STAR_ITEMS), time_one, path)
     ctx.set_tuning("star_items", best)
+    return best
+
+
+def placement_bucket(n_fact: int, groups: int, n_dim: int) -> str:
+    return (f"group:n{int(math.log2(max(1, n_fact)))}:g{int(math.log2(max(1, groups)))}"
+            f":d{int(math.log2(max(1, n_dim)))}")
+
+
+def tune_group_placement(ctx, desc, run, stream, steps: int = 2, path: str = CACHE):
+    """Pick, by timing run() (one pipeline call over `desc`), where a
+    many-group pipeline aggregates -- the direct HBM hash table or the
+    partitioned group-by, and at which fan-out -- and the layout of the join
+    table its call builds (dense array or open addressing).  Applies the
+    best (knobs on the context, layout in desc.build) and returns
+    (gb_partition, gb_part_log2p, layout)."""
+    import torch
+
+    old_layout = desc.build.layout
+
+    def time_one(c):
+        part, log2p, layout = c
+        ctx.set_tuning("gb_partition", part)
+        ctx.set_tuning("gb_part_log2p", log2p)
+        desc.build.layout = layout
+        run()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            run()
+        e.record(stream)
+        e.synchronize()
+        return a.elapsed_time(e) / steps
+    cands = [(p, lp, lay) for p, lp in GROUP_PLACEMENT for lay in JOIN_LAYOUTS]
+    try:
+        best = search(placement_bucket(desc.n_fact, desc.expected_groups, desc.n_dim), cands, time_one, path)
+    except Exception:
+        desc.build.layout = old_layout
+        ctx.set_tuning("gb_partition", 0)
+        ctx.set_tuning("gb_part_log2p", 0)
+        raise
+    part, log2p, layout = best
+    ctx.set_tuning("gb_partition", part)
+    ctx.set_tuning("gb_part_log2p", log2p)
+    desc.build.layout = layout
     return best

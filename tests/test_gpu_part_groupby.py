@@ -192,3 +192,25 @@ def test_part_groupby_matches_unpartitioned(ctx):
     assert np.array_equal(g1[0], g2[0])
     for x, y in zip(g1[1], g2[1]):
         assert np.array_equal(x, y)
+
+
+def test_autotuned_placement_matches_oracle(ctx, tmp_path):
+    """The autotuner times the direct HBM table against the partitioned
+    group-by at three fan-outs, with a dense and an open-addressing join
+    table, applies the fastest, and the result of that choice is exact."""
+    from paper_2506_09226_gb300 import tune
+    fact, dim = _skew(1_500_000, 60_000, 300_000, seed=70)
+    f = [fact[c].cuda() for c in SKEW]
+    d = qe.pipeline_desc(f, [(1, qe.LT, 1500)], fk_col=0, dim_key=dim["key"].cuda(), dim_payload=dim["attr"].cuda(),
+                         key_hi_col=-1, key_lo_col=6, aggs=AGGS, expected_groups=524_288)
+    g, o = qe.alloc_groups(524_288, 4, torch.device("cuda"))
+    stream = torch.cuda.current_stream()
+    try:
+        best = tune.tune_group_placement(ctx, d, lambda: qe.qe_pipeline(ctx, d, 524_288, check=False, out=(g, o)),
+                                         stream, path=str(tmp_path / "tune.json"))
+        assert best in [(p, lp, lay) for p, lp in tune.GROUP_PLACEMENT for lay in tune.JOIN_LAYOUTS]
+        qe.qe_pipeline(ctx, d, 524_288, out=(g, o))
+        _equal(g, _oracle(fact, dim, 6, 1500))
+    finally:
+        ctx.set_tuning("gb_partition", 2)
+        ctx.set_tuning("gb_part_log2p", 0)
