@@ -128,7 +128,12 @@ extern "C" qe_status qe_set_tuning(qe_ctx *ctx, const char *name, int64_t value)
     } else if (n == "gb_part_log2p") {
         if (value < 0 || value > 10) return qe_fail(ctx, QE_ERR_INVALID_ARG, "gb_part_log2p must be in [0, 10]");
         ctx->tune_gb_part_log2p = static_cast<int>(value);
-
+    } else if (n == "join_partition") {
+        if (value < 0 || value > 2) return qe_fail(ctx, QE_ERR_INVALID_ARG, "join_partition must be 0, 1 or 2");
+        ctx->tune_join_partition = static_cast<int>(value);
+    } else if (n == "join_part_log2") {
+        if (value < 0 || value > 8) return qe_fail(ctx, QE_ERR_INVALID_ARG, "join_part_log2 must be in [0, 8]");
+        ctx->tune_join_part_log2 = static_cast<int>(value);
     } else {
         return qe_fail(ctx, QE_ERR_INVALID_ARG, "unknown tuning knob " + n);
     }

@@ -49,6 +49,8 @@ struct qe_ctx {
     int tune_gb_part_log2q = -1;    // sub-parts per part (log2; -1 = planned)
     int tune_gb_fold2 = 0;          // partitioned fold: two 512-thread blocks per SM
     int tune_l2_hint = 0;           // star pipeline: L2 policies on fact loads and payload lookups
+    int tune_join_partition = 0;    // join builds into large tables: 0 auto, 1 never region-order, 2 always
+    int tune_join_part_log2 = 0;    // regions of a region-ordered build (log2; 0 = planned)
     bool profiling = false;
     std::mutex prof_mu;
     std::map<std::string, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>> prof;
@@ -87,6 +89,42 @@ qe_status qe_fail(qe_ctx *ctx, qe_status st, const std::string &msg);
 qe_status qe_cuda_fail(qe_ctx *ctx, cudaError_t e, const char *where);
 qe_status qe_alloc(qe_ctx *ctx, void **p, size_t bytes, cudaStream_t s);
 void qe_free(qe_ctx *ctx, void *p, cudaStream_t s);
+
+// Region-ordered build input (qe_join_part.cu).  The region of a row is the
+// top log2p bits of its slot: fmix32(key) & mask (RP_HASH32, the open
+// table), (uint32)fmix64(hi << 32 | lo) & mask (RP_PAIR64, the pair-key
+// table), or key - kmin (RP_DENSE, a dense table, clamped to the last
+// region); region = slot >> shift.
+enum : int { RP_HASH32 = 0, RP_PAIR64 = 1, RP_DENSE = 2 };
+struct RegionPlan {
+    int kind;
+    int log2p;        // 1 .. 8
+    int shift;
+    uint32_t mask;
+    int32_t kmin;
+};
+// log2 of the regions for a build of nrows into a table of table_bytes, or 0
+// for a build in input order (the knobs "join_partition", "join_part_log2").
+// With the knob at 0 (automatic) only builds with by_default set are
+// reordered: the multimap build gains (80M rows: 6.2 -> 3.0 ms), the
+// open-addressing and pair-key builds measured slower reordered.
+int region_plan_log2(const qe_ctx *ctx, uint64_t table_bytes, int64_t nrows, bool by_default);
+// Rows of ncols int32 columns (column 0 the key; columns 0 and 1 the key pair
+// of RP_PAIR64) reordered region by region into *scratch, allocated here
+// from the context (the caller frees it with qe_free once the build kernels
+// are enqueued); on return cols[c] points at the reordered column c.  The
+// order inside a region is unspecified.  plan.log2p == 0: nothing is done,
+// *scratch = NULL.
+qe_status region_order(qe_ctx *ctx, const RegionPlan &plan, const int32_t **cols, int ncols, int64_t n,
+                       void **scratch, cudaStream_t s, const uint32_t **counts = nullptr);
+// Fills and builds an open-addressing table of nslots slots (8-byte {key,
+// payload} words, or pair = 16-byte {packed key pair, payload} slots) from
+// rows that region_order reordered with `plan` (counts: its rows per
+// region); plan.shift >= 4.  Replaces the fill and the insert kernel of a
+// build in input order; reports the same errors.
+qe_status region_fill_insert(qe_ctx *ctx, bool pair, const int32_t *const *cols, bool has_pay, int64_t n,
+                             unsigned long long *slots, uint64_t nslots, const RegionPlan &plan, const uint32_t *counts,
+                             cudaStream_t s);
 
 #define QE_CUDA(ctx, call)                                        \
     do {                                                          \

@@ -478,17 +478,38 @@ qe_status join_build_impl(qe_ctx *ctx, const int32_t *keys, const int32_t *paylo
             return st;
         }
         ht->open = static_cast<unsigned long long *>(ht->mem);
-        k_fill_u64<<<grid_for(ctx, static_cast<int64_t>(slots)), 256, 0, s>>>(ht->open, static_cast<int64_t>(slots),
-                                                                               HT_EMPTY_SLOT);
-        QE_LAUNCHED(ctx);
-        cudaError_t e = cudaGetLastError();
-        if (e == cudaSuccess && nrows > 0) {
+        // rows in region order when the table is far larger than L2
+        const int log2s = qe_log2_ceil(slots);
+        int lp = region_plan_log2(ctx, ht->bytes, nrows, false);
+        lp = lp < log2s - 4 ? lp : (log2s > 5 ? log2s - 4 : 0);   // regions of >= 16 slots
+        const RegionPlan plan{RP_HASH32, lp, log2s - lp, static_cast<uint32_t>(slots - 1), 0};
+        const int32_t *cols[2] = {keys, payload};
+        void *scratch = nullptr;
+        const uint32_t *counts = nullptr;
+        st = region_order(ctx, plan, cols, payload ? 2 : 1, nrows, &scratch, s, &counts);
+        if (st == QE_OK && scratch)
+            st = region_fill_insert(ctx, false, cols, payload != nullptr, nrows, ht->open, slots, plan, counts, s);
+        if (st != QE_OK) {
+            if (scratch) qe_free(ctx, scratch, s);
+            qe_free(ctx, ht->mem, s);
+            delete ht;
+            return st;
+        }
+        cudaError_t e = cudaSuccess;
+        if (!scratch) {
+            k_fill_u64<<<grid_for(ctx, static_cast<int64_t>(slots)), 256, 0, s>>>(
+                ht->open, static_cast<int64_t>(slots), HT_EMPTY_SLOT);
+            QE_LAUNCHED(ctx);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess && nrows > 0 && !scratch) {
             ProfScope prof(ctx, "build", s);
-            k_build_open<<<grid_for(ctx, nrows), 256, 0, s>>>(keys, payload, nrows, ht->open,
+            k_build_open<<<grid_for(ctx, nrows), 256, 0, s>>>(cols[0], payload ? cols[1] : nullptr, nrows, ht->open,
                                                               static_cast<uint32_t>(slots - 1), ctx->dstat);
             QE_LAUNCHED(ctx);
             e = cudaGetLastError();
         }
+        if (scratch) qe_free(ctx, scratch, s);
         if (e != cudaSuccess) {
             qe_free(ctx, ht->mem, s);
             delete ht;
@@ -533,19 +554,39 @@ extern "C" qe_status qe_join_build_pair(qe_ctx *ctx, const int32_t *key_hi, cons
         return st;
     }
     ht->open = static_cast<unsigned long long *>(ht->mem);
-    // every word to the empty marker: the key words mark empty slots, the
-    // payload words are written before any probe reads them
-    const int64_t words = static_cast<int64_t>(2 * slots);
-    k_fill_u64<<<grid_for(ctx, words), 256, 0, s>>>(ht->open, words, HT_EMPTY_SLOT);
-    QE_LAUNCHED(ctx);
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess && nrows > 0) {
+    // rows in region order when the table is far larger than L2
+    const int log2s = qe_log2_ceil(slots);
+    int lp = region_plan_log2(ctx, ht->bytes, nrows, false);
+    lp = lp < log2s - 4 ? lp : (log2s > 5 ? log2s - 4 : 0);   // regions of >= 16 slots
+    const RegionPlan plan{RP_PAIR64, lp, log2s - lp, static_cast<uint32_t>(slots - 1), 0};
+    const int32_t *cols[3] = {key_hi, key_lo, payload};
+    void *scratch = nullptr;
+    const uint32_t *counts = nullptr;
+    st = region_order(ctx, plan, cols, 3, nrows, &scratch, s, &counts);
+    if (st == QE_OK && scratch) st = region_fill_insert(ctx, true, cols, true, nrows, ht->open, slots, plan, counts, s);
+    if (st != QE_OK) {
+        if (scratch) qe_free(ctx, scratch, s);
+        qe_free(ctx, ht->mem, s);
+        delete ht;
+        return st;
+    }
+    cudaError_t e = cudaSuccess;
+    if (!scratch) {
+        // every word to the empty marker: the key words mark empty slots, the
+        // payload words are written before any probe reads them
+        const int64_t words = static_cast<int64_t>(2 * slots);
+        k_fill_u64<<<grid_for(ctx, words), 256, 0, s>>>(ht->open, words, HT_EMPTY_SLOT);
+        QE_LAUNCHED(ctx);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && nrows > 0 && !scratch) {
         ProfScope prof(ctx, "build", s);
-        k_build_pair<<<grid_for(ctx, nrows), 256, 0, s>>>(key_hi, key_lo, payload, nrows, ht->open,
+        k_build_pair<<<grid_for(ctx, nrows), 256, 0, s>>>(cols[0], cols[1], cols[2], nrows, ht->open,
                                                           static_cast<uint32_t>(slots - 1), ctx->dstat);
         QE_LAUNCHED(ctx);
         e = cudaGetLastError();
     }
+    if (scratch) qe_free(ctx, scratch, s);
     if (e != cudaSuccess) {
         qe_free(ctx, ht->mem, s);
         delete ht;

@@ -390,6 +390,22 @@ extern "C" qe_status qe_join_build_multi(qe_ctx *ctx, const int32_t *keys, const
     int64_t *total = reinterpret_cast<int64_t *>(p + b_start + b_cnt + b_vals + b_open);
     const unsigned grid = grid_of(ctx, nrows);
     const uint32_t r32 = static_cast<uint32_t>(range), mask = static_cast<uint32_t>(nslots - 1);
+    // rows in region order (dense: by key range; open: by slot) when the
+    // table is far larger than L2
+    const int log2s = qe_log2_ceil(nslots);
+    int lp = region_plan_log2(ctx, ht->bytes, nrows, true);
+    lp = lp < log2s ? lp : log2s;
+    const int32_t *cols[2] = {keys, payload};
+    void *scratch = nullptr;
+    st = region_order(ctx, RegionPlan{layout == QE_HT_DENSE ? RP_DENSE : RP_HASH32, lp, log2s - lp, mask, kmin}, cols,
+                      2, nrows, &scratch, s);
+    if (st != QE_OK) {
+        qe_free(ctx, ht->mem, s);
+        delete ht;
+        return st;
+    }
+    keys = cols[0];
+    payload = cols[1];
     // 1. rows per key (dense slot, or open slot's low half copied out)
     cudaError_t e = cudaMemsetAsync(ht->mcnt, 0, nslots * 4, s);
     if (e == cudaSuccess) {
@@ -434,6 +450,7 @@ extern "C" qe_status qe_join_build_multi(qe_ctx *ctx, const int32_t *keys, const
         QE_LAUNCHED(ctx);
         e = cudaGetLastError();
     }
+    if (scratch) qe_free(ctx, scratch, s);
     if (e != cudaSuccess || st != QE_OK) {
         qe_free(ctx, ht->mem, s);
         delete ht;
