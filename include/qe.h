@@ -165,9 +165,10 @@ void qe_debug_set_spin_limit(qe_ctx *ctx, int64_t iterations);
  *                   planned) and sub-parts per part (0..8; -1 = planned).
  *   "join_partition" join builds into tables of 256 MB or more: 0 = rows
  *                   reordered region by region (the top bits of the slot
- *                   they hash to) before the inserts for the multimap build
- *                   of 4M rows or more, input order otherwise; 1 = always
- *                   input order; 2 = always reordered (every build kind).
+ *                   they hash to) before the inserts for the multimap and
+ *                   pair-key builds of 4M rows or more, input order
+ *                   otherwise; 1 = always input order; 2 = always reordered
+ *                   (every build kind).
  *   "join_part_log2" log2 of the regions of a reordered build (1..8; 0 =
  *                   planned: regions of about 32 MB).
  * Unknown names return QE_ERR_INVALID_ARG. */

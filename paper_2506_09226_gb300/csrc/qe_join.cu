@@ -478,7 +478,9 @@ qe_status join_build_impl(qe_ctx *ctx, const int32_t *keys, const int32_t *paylo
             return st;
         }
         ht->open = static_cast<unsigned long long *>(ht->mem);
-        // rows in region order when the table is far larger than L2
+        // rows in region order when the table is far larger than L2, only
+        // when tuned so: on GB300 it measured slower for this table (20M /
+        // 50M keys: 0.78 -> 0.86 ms and 2.08 -> 2.50 ms)
         const int log2s = qe_log2_ceil(slots);
         int lp = region_plan_log2(ctx, ht->bytes, nrows, false);
         lp = lp < log2s - 4 ? lp : (log2s > 5 ? log2s - 4 : 0);   // regions of >= 16 slots
@@ -554,9 +556,10 @@ extern "C" qe_status qe_join_build_pair(qe_ctx *ctx, const int32_t *key_hi, cons
         return st;
     }
     ht->open = static_cast<unsigned long long *>(ht->mem);
-    // rows in region order when the table is far larger than L2
+    // rows in region order when the table is far larger than L2 (on by
+    // default: 80M pairs into a 4 GB table, 6.5 -> 5.1 ms on GB300)
     const int log2s = qe_log2_ceil(slots);
-    int lp = region_plan_log2(ctx, ht->bytes, nrows, false);
+    int lp = region_plan_log2(ctx, ht->bytes, nrows, true);
     lp = lp < log2s - 4 ? lp : (log2s > 5 ? log2s - 4 : 0);   // regions of >= 16 slots
     const RegionPlan plan{RP_PAIR64, lp, log2s - lp, static_cast<uint32_t>(slots - 1), 0};
     const int32_t *cols[3] = {key_hi, key_lo, payload};

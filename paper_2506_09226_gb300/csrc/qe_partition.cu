@@ -14,11 +14,13 @@
 //                      chunk stably by destination in shared memory and writes
 //                      the rows in destination order, keeping a running output
 //                      offset per destination so rows keep their input order.
-//                      Two kernels:
-//                      k_part_scatter_wc (one int64 payload or none, F <= 512):
-//                        register-prefetched chunks, one-pass ranking with
-//                        per-warp counters, and write-combining of 32-byte
-//                        sectors (see below);
+//                      Three kernels:
+//                      k_part_scatter_sf (one int64 payload or none, at most
+//                        64 digits: F <= 64 in one pass, F = 1024 .. 4096 in
+//                        two passes) and k_part_scatter_wc (the same inputs,
+//                        F = 128 .. 512 in one pass): register-prefetched
+//                        chunks, one-pass ranking with per-warp counters, and
+//                        write-combining of 32-byte sectors (see below);
 //                      k_part_scatter (qe_part_general.cuh; any payloads, any
 //                        fan-out): bulk-copy (TMA) double-buffered chunks and
 //                        a one- or two-digit LSD ranking.
@@ -152,7 +154,8 @@ __global__ void __launch_bounds__(1024) k_part_basescan(const int64_t *tot, int6
 
 // ---------------------------------------------------------------------------
 // Write-combining scatter: int64 keys with no payload or one int64 payload,
-// fan-out F <= 512.  A block walks its rows in chunks of T * IT;
+// 128 .. 512 digits (k_part_scatter_sf below takes up to 64 digits, with the
+// same chunk walk and sector rule).  A block walks its rows in chunks of T * IT;
 // the next chunk is loaded into registers while the current one is ranked.
 //
 // Ranking is one pass: each warp counts destinations in its own row of the
@@ -351,167 +354,8 @@ __global__ void __launch_bounds__(T, MINB) k_part_scatter_wc(PartArgs A)
             wc_load<PAY, IT>(A, r0 + CH, hi, nkv);       // rows past hi are not read
 
             uint32_t dg[IT], rk[IT];
-            if constexpr (BITS <= 6) {
-                // ---- up to 64 digits: register counters, every warp scans
-                // the counter matrix itself and owns digits p == warp
-                // (mod NWARP): their running offsets, pending rows and
-                // output runs.
-                constexpr int NCL = BITS > 5 ? 2 : 1;     // digits per lane: lane, lane + 32
-                uint32_t cl[NCL];
-#pragma unroll
-                for (int k = 0; k < NCL; k++) cl[k] = 0;
-                // digit and rank among the warp's earlier rows of that digit:
-                // lane e computes which lanes hold digit e (AND over bits of
-                // the bit ballots or their complements); a row reads its
-                // peers and its base count from lane (digit & 31)
-                // first every item's masks (independent of each other), then
-                // the counters' prefix over items, then the shuffles: no
-                // dependency chain through the counters
-                unsigned me0[IT], me1[IT];
-#pragma unroll
-                for (int i = 0; i < IT; i++) {
-                    const bool valid = m == CH || warp * 32 * IT + i * 32 + lane < m;
-                    const uint32_t d =
-                        valid ? (dev_part_id(kv[i].x, A.log2f, A.mode, A.shift) >> A.dshift) & A.dmask : 0u;
-                    unsigned me = m == CH ? QE_FULL_MASK : __ballot_sync(QE_FULL_MASK, valid);
-#pragma unroll
-                    for (int bit = 0; bit < (BITS < 5 ? BITS : 5); bit++) {
-                        const unsigned set = __ballot_sync(QE_FULL_MASK, (d >> bit) & 1u);
-                        me &= ((lane >> bit) & 1) ? set : ~set;
-                    }
-                    unsigned me1v = 0;
-                    if (BITS > 5) {
-                        const unsigned set5 = __ballot_sync(QE_FULL_MASK, (d >> 5) & 1u);
-                        me1v = me & set5;
-                        me &= ~set5;
-                    }
-                    me0[i] = me;
-                    me1[i] = me1v;
-                    dg[i] = valid ? d : 0xffffffffu;
-                }
-#pragma unroll
-                for (int i = 0; i < IT; i++) {
-                    const uint32_t d = dg[i] == 0xffffffffu ? 0u : dg[i];
-                    const int src = static_cast<int>(d & 31u);
-                    unsigned peers = __shfl_sync(QE_FULL_MASK, me0[i], src);
-                    uint32_t basec = __shfl_sync(QE_FULL_MASK, cl[0], src);
-                    if (BITS > 5) {
-                        const unsigned peers1 = __shfl_sync(QE_FULL_MASK, me1[i], src);
-                        const uint32_t base1 = __shfl_sync(QE_FULL_MASK, cl[NCL - 1], src);
-                        if (d >= 32u) {
-                            peers = peers1;
-                            basec = base1;
-                        }
-                    }
-                    rk[i] = basec + __popc(peers & lt);
-                    cl[0] += __popc(me0[i]);
-                    if (BITS > 5) cl[NCL - 1] += __popc(me1[i]);
-                }
-#pragma unroll
-                for (int k = 0; k < NCL; k++)
-                    if (lane + 32 * k < F) cnt[warp * FC + lane + 32 * k] = static_cast<uint16_t>(cl[k]);
-                __syncthreads();
-                // per digit: rows of earlier warps (pre), the chunk's total
-                // (tot) and the digit's first sorted position (st)
-                uint32_t pre[NCL], tot[NCL], st[NCL];
-#pragma unroll
-                for (int k = 0; k < NCL; k++) {
-                    pre[k] = 0;
-                    tot[k] = 0;
-                    const int d = lane + 32 * k;
-                    if (d < F) {
-#pragma unroll
-                        for (int w = 0; w < NWARP; w++) {
-                            const uint32_t x = cnt[w * FC + d];
-                            pre[k] += w < warp ? x : 0u;
-                            tot[k] += x;
-                        }
-                    }
-                }
-                {
-                    const uint32_t inc0 = warp_incl_scan(tot[0]);
-                    st[0] = inc0 - tot[0];
-                    if (BITS > 5) {
-                        const uint32_t all0 = __shfl_sync(QE_FULL_MASK, inc0, 31);
-                        const uint32_t inc1 = warp_incl_scan(tot[NCL - 1]);
-                        st[NCL - 1] = all0 + inc1 - tot[NCL - 1];
-                    }
-                }
-                // the owned digits' running offsets; a chunk that completes a
-                // pending sector writes the sector's earlier rows
-#pragma unroll
-                for (int k = 0; k < NCL; k++) {
-                    const int d = lane + 32 * k;
-                    if (d < F && d % NWARP == warp) {
-                        const int r = rq[d];
-                        const int h = static_cast<int>(tot[k]);
-                        const int e = r + h;
-                        const int r4 = r & ~3, e4 = e & ~3;
-                        const int np = r > 0 ? (r & 3) : 0;
-                        if (np && e4 > r4) {
-                            long long *o = ob[d] + r4;
-                            for (int j = 0; j < np; j++) {
-                                if (!QE_DCHECK(A.st, o + j >= outK && o + j < outK + A.n, (o + j) - outK)) continue;
-                                __stcs(o + j, pK[d * 3 + j]);
-                                if (PAY) __stcs(o + dP + j, pP[d * 3 + j]);
-                            }
-                        }
-                        const int lim = e4 > 0 ? e4 : 0;
-                        const int kk = lim - r;
-                        const int s0 = static_cast<int>(st[k]);
-                        qt[d] = make_int2(r - s0, s0 + (kk < 0 ? 0 : (kk > h ? h : kk)));
-                        start[d] = st[k];
-                        hist[d] = tot[k];
-                        rq[d] = e;
-                    }
-                }
-                // rows to their sorted positions, (key, payload) as one element
-                uint32_t o0 = st[0] + pre[0], o1 = BITS > 5 ? st[NCL - 1] + pre[NCL - 1] : 0u;
-#pragma unroll
-                for (int i = 0; i < IT; i++) {
-                    const int src = static_cast<int>(dg[i] & 31u);
-                    uint32_t pos = __shfl_sync(QE_FULL_MASK, o0, src);
-                    if (BITS > 5) {
-                        const uint32_t pos1 = __shfl_sync(QE_FULL_MASK, o1, src);
-                        if (dg[i] >= 32u && dg[i] != 0xffffffffu) pos = pos1;
-                    }
-                    if (dg[i] != 0xffffffffu) {
-                        pos += rk[i];
-                        if (PAY)
-                            reinterpret_cast<longlong2 *>(sK)[pos] = kv[i];
-                        else
-                            sK[pos] = kv[i].x;
-                    }
-                }
-                __syncthreads();
-                // each warp writes its digits' runs
-                for (int p = warp; p < F; p += NWARP) {
-                    const int s0 = static_cast<int>(start[p]), h = static_cast<int>(hist[p]);
-                    const int2 x = qt[p];
-                    long long *o = ob[p];
-                    for (int t = s0 + lane; t < s0 + h; t += 32) {
-                        const int q = x.x + t;
-                        long long k, v = 0;
-                        if (PAY) {
-                            const longlong2 kv2 = reinterpret_cast<const longlong2 *>(sK)[t];
-                            k = kv2.x;
-                            v = kv2.y;
-                        } else {
-                            k = sK[t];
-                        }
-                        if (t < x.y) {
-                            if (!QE_DCHECK(A.st, o + q >= outK && o + q < outK + A.n, (o + q) - outK)) continue;
-                            __stcs(o + q, k);
-                            if (PAY) __stcs(o + q + dP, v);
-                        } else {
-                            pK[p * 3 + (q & 3)] = k;
-                            if (PAY) pP[p * 3 + (q & 3)] = v;
-                        }
-                    }
-                }
-                __syncthreads();
-            } else {
-                // ---- many digits: shared-memory counters per warp
+            {
+                // shared-memory counters per warp
 #pragma unroll
                 for (int i = 0; i < IT; i++) {
                     const bool valid = warp * 32 * IT + i * 32 + lane < m;
@@ -616,6 +460,343 @@ __global__ void __launch_bounds__(T, MINB) k_part_scatter_wc(PartArgs A)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Small fan-out scatter: at most 64 digits per launch (fan-out <= 64 in one
+// pass, and both passes of fan-out 1024 .. 4096).  Same work items, output
+// offsets and write-combining rule as k_part_scatter_wc, with the work per
+// row cut down:
+//   * a chunk whose rows all lie inside the item is loaded and ranked
+//     without per-row bounds tests (FULL);
+//   * digit state lives in registers: lane d of every warp keeps the q of
+//     digit d's next row (r, the same in every warp), so the digits' sorted
+//     starts and the write-out need no shared-memory tables;
+//   * every digit's run in the sorted chunk starts on the parity of its r
+//     (one row of padding per digit at most), so the rows of whole sectors
+//     move from shared memory to DRAM as 16-byte pairs of rows;
+//   * the sorted chunk is double-buffered: two barriers per chunk.
+// Each digit is written by one warp (digits p == warp mod NWARP): the rows
+// that complete its pending sector, its whole sectors, two rows per lane,
+// and the rows of its last incomplete sector, kept in shared memory until a
+// later chunk (or the end of the item) completes them.
+template <bool PAY, int BITS, int T, int IT>
+struct SfLayout {
+    static constexpr int NWARP = T / 32, CH = T * IT, NCL = BITS > 5 ? 2 : 1, FMAX = 32 * NCL;
+    static constexpr int SROW = CH + FMAX;                      // rows of one sorted buffer (with padding)
+    static constexpr size_t sK = 0;                             // [2][SROW] keys
+    static constexpr size_t sP = sK + 2 * SROW * 8;             // [2][SROW] payloads
+    static constexpr size_t pK = sP + (PAY ? 2 * SROW * 8 : 0); // [FMAX][4] pending keys
+    static constexpr size_t pP = pK + FMAX * 4 * 8;             // [FMAX][4] pending payloads
+    static constexpr size_t ob = pP + (PAY ? FMAX * 4 * 8 : 0); // [FMAX] key address of q = 0
+    static constexpr size_t cnt = ob + FMAX * 8;                // [NWARP][FMAX] rows per warp and digit
+    static constexpr size_t total = cnt + NWARP * FMAX * 4;
+};
+
+// Rows r0 + (warp-striped positions) of a chunk inside the item: no tests.
+template <bool PAY, int IT>
+__device__ __forceinline__ void sf_load_full(const PartArgs &A, int64_t r0, longlong2 (&kv)[IT])
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long *k = reinterpret_cast<const long long *>(A.keys) + r0 + warp * 32 * IT + lane;
+    const long long *v = static_cast<const long long *>(A.pay[0]) + r0 + warp * 32 * IT + lane;
+#pragma unroll
+    for (int i = 0; i < IT; i++) {
+        kv[i].x = __ldcs(k + i * 32);
+        kv[i].y = PAY ? __ldcs(v + i * 32) : 0;
+    }
+}
+
+// Digit and stable rank (among the warp's earlier rows of the chunk with
+// that digit) of every row; cl[k] counts the warp's rows of digit
+// lane + 32 k.  Lane e forms the mask of lanes whose row has digit e (AND of
+// the digit bits' ballots or their complements); a row reads its peers and
+// its base count from lane (digit & 31).  Invalid rows get digit ~0u.
+template <int BITS, int IT, bool FULL, int NCL>
+__device__ __forceinline__ void sf_rank(const PartArgs &A, const longlong2 (&kv)[IT], int vlo, int vhi,
+                                        uint32_t (&dg)[IT], uint32_t (&rk)[IT], uint32_t (&cl)[NCL])
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1;
+    unsigned me0[IT], me1[IT];
+#pragma unroll
+    for (int i = 0; i < IT; i++) {
+        const int row = warp * 32 * IT + i * 32 + lane;
+        const bool valid = FULL || (row >= vlo && row < vhi);
+        const uint32_t d = valid ? (dev_part_id(kv[i].x, A.log2f, A.mode, A.shift) >> A.dshift) & A.dmask : 0u;
+        unsigned me = FULL ? QE_FULL_MASK : __ballot_sync(QE_FULL_MASK, valid);
+#pragma unroll
+        for (int bit = 0; bit < (BITS < 5 ? BITS : 5); bit++) {
+            const unsigned set = __ballot_sync(QE_FULL_MASK, (d >> bit) & 1u);
+            me &= ((lane >> bit) & 1) ? set : ~set;
+        }
+        unsigned me1v = 0;
+        if (BITS > 5) {
+            const unsigned set5 = __ballot_sync(QE_FULL_MASK, (d >> 5) & 1u);
+            me1v = me & set5;
+            me &= ~set5;
+        }
+        me0[i] = me;
+        me1[i] = me1v;
+        dg[i] = valid ? d : 0xffffffffu;
+    }
+#pragma unroll
+    for (int i = 0; i < IT; i++) {
+        const int src = static_cast<int>(dg[i] & 31u);
+        unsigned peers = __shfl_sync(QE_FULL_MASK, me0[i], src);
+        uint32_t basec = __shfl_sync(QE_FULL_MASK, cl[0], src);
+        if (BITS > 5) {
+            const unsigned peers1 = __shfl_sync(QE_FULL_MASK, me1[i], src);
+            const uint32_t base1 = __shfl_sync(QE_FULL_MASK, cl[NCL - 1], src);
+            if (dg[i] >= 32u) {
+                peers = peers1;
+                basec = base1;
+            }
+        }
+        rk[i] = basec + __popc(peers & lt);
+        cl[0] += __popc(me0[i]);
+        if (BITS > 5) cl[NCL - 1] += __popc(me1[i]);
+    }
+}
+
+// One chunk: rank, place in sorted buffer `buf`, write out.  Returns nothing;
+// rr (q of every lane digit's next row) advances by the chunk's rows.
+template <bool PAY, int BITS, int T, int IT, bool FULL>
+__device__ __forceinline__ void sf_chunk(const PartArgs &A, unsigned char *smem, int buf, const longlong2 (&kv)[IT],
+                                         int vlo, int vhi, int F, int (&rr)[SfLayout<PAY, BITS, T, IT>::NCL],
+                                         long long *outK, int64_t dP, bool vecP)
+{
+    using L = SfLayout<PAY, BITS, T, IT>;
+    constexpr int NWARP = L::NWARP, NCL = L::NCL, FMAX = L::FMAX, SROW = L::SROW;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    long long *bK = reinterpret_cast<long long *>(smem + L::sK) + buf * SROW;
+    long long *bP = reinterpret_cast<long long *>(smem + L::sP) + buf * SROW;
+    long long *pK = reinterpret_cast<long long *>(smem + L::pK);
+    long long *pP = reinterpret_cast<long long *>(smem + L::pP);
+    long long *const *ob = reinterpret_cast<long long *const *>(smem + L::ob);
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(smem + L::cnt);
+
+    uint32_t dg[IT], rk[IT], cl[NCL];
+#pragma unroll
+    for (int k = 0; k < NCL; k++) cl[k] = 0;
+    sf_rank<BITS, IT, FULL, NCL>(A, kv, vlo, vhi, dg, rk, cl);
+#pragma unroll
+    for (int k = 0; k < NCL; k++)
+        if (lane + 32 * k < F) cnt[warp * FMAX + lane + 32 * k] = cl[k];
+    __syncthreads();
+    // per lane digit: rows of earlier warps (pre) and of the chunk (tot); the
+    // digit's run starts at the exclusive scan of (tot + 1) over digits,
+    // moved by one row when needed so that its start has the parity of r
+    uint32_t pre[NCL], tot[NCL], s0[NCL];
+#pragma unroll
+    for (int k = 0; k < NCL; k++) {
+        pre[k] = 0;
+        tot[k] = 0;
+        const int d = lane + 32 * k;
+        if (d < F) {
+#pragma unroll
+            for (int w = 0; w < NWARP; w++) {
+                const uint32_t x = cnt[w * FMAX + d];
+                pre[k] += w < warp ? x : 0u;
+                tot[k] += x;
+            }
+        }
+    }
+    {
+        const uint32_t v0 = lane < F ? tot[0] + 1u : 0u;
+        const uint32_t i0 = warp_incl_scan(v0);
+        const uint32_t b0 = i0 - v0;
+        s0[0] = b0 + ((static_cast<uint32_t>(rr[0]) - b0) & 1u);
+        if (NCL > 1) {
+            const uint32_t all0 = __shfl_sync(QE_FULL_MASK, i0, 31);
+            const uint32_t v1 = lane + 32 < F ? tot[NCL - 1] + 1u : 0u;
+            const uint32_t i1 = warp_incl_scan(v1);
+            const uint32_t b1 = all0 + i1 - v1;
+            s0[NCL - 1] = b1 + ((static_cast<uint32_t>(rr[NCL - 1]) - b1) & 1u);
+        }
+    }
+    // rows to their sorted positions
+    {
+        const uint32_t o0 = s0[0] + pre[0], o1 = NCL > 1 ? s0[NCL - 1] + pre[NCL - 1] : 0u;
+#pragma unroll
+        for (int i = 0; i < IT; i++) {
+            const int src = static_cast<int>(dg[i] & 31u);
+            uint32_t pos = __shfl_sync(QE_FULL_MASK, o0, src);
+            if (NCL > 1) {
+                const uint32_t pos1 = __shfl_sync(QE_FULL_MASK, o1, src);
+                if (dg[i] >= 32u) pos = pos1;
+            }
+            if (FULL || dg[i] != 0xffffffffu) {
+                pos += rk[i];
+                bK[pos] = kv[i].x;
+                if (PAY) bP[pos] = kv[i].y;
+            }
+        }
+    }
+    __syncthreads();
+    // this warp's digits
+#pragma unroll
+    for (int j = 0; j < FMAX / NWARP; j++) {
+        const int p = warp + NWARP * j;
+        if (p >= F) break;
+        const int kk = p >> 5, src = p & 31;
+        const int r = __shfl_sync(QE_FULL_MASK, kk ? rr[NCL - 1] : rr[0], src);
+        const int h = static_cast<int>(__shfl_sync(QE_FULL_MASK, kk ? tot[NCL - 1] : tot[0], src));
+        const int s = static_cast<int>(__shfl_sync(QE_FULL_MASK, kk ? s0[NCL - 1] : s0[0], src));
+        long long *o = ob[p];
+        const int e = r + h;
+        const int x = r - s;                       // row q sits at bK[q - x]; x is even
+        const int lim = e > 0 ? (e & ~3) : 0;      // rows q < lim are written now
+        const int a = r > 0 ? ((r + 3) & ~3) : 0;  // first whole sector of this chunk's rows
+        if (r < 0) {
+            // rows before the item's first sector boundary: their sector is
+            // shared with the previous item and written in two parts
+            const int q = r + lane;
+            if (lane < 3 && q < 0 && q < e && QE_DCHECK(A.st, o + q >= outK && o + q < outK + A.n, (o + q) - outK)) {
+                __stcs(o + q, bK[q - x]);
+                if (PAY) __stcs(o + q + dP, bP[q - x]);
+            }
+        } else if ((r & 3) && e >= a) {
+            // the pending sector completes: its earlier rows, then this chunk's
+            const int q = (r & ~3) + lane;
+            if (lane < 4 && QE_DCHECK(A.st, o + q >= outK && o + q < outK + A.n, (o + q) - outK)) {
+                const bool old = q < r;
+                __stcs(o + q, old ? pK[p * 4 + lane] : bK[q - x]);
+                if (PAY) __stcs(o + q + dP, old ? pP[p * 4 + lane] : bP[q - x]);
+            }
+        }
+        for (int q = a + 2 * lane; q < lim; q += 64) {
+            if (!QE_DCHECK(A.st, o + q >= outK && o + q + 1 < outK + A.n, (o + q) - outK)) continue;
+            const int t = q - x;
+            __stcs(reinterpret_cast<longlong2 *>(o + q), *reinterpret_cast<const longlong2 *>(bK + t));
+            if (PAY) {
+                const longlong2 v = *reinterpret_cast<const longlong2 *>(bP + t);
+                if (vecP) {
+                    __stcs(reinterpret_cast<longlong2 *>(o + q + dP), v);
+                } else {
+                    __stcs(o + q + dP, v.x);
+                    __stcs(o + q + 1 + dP, v.y);
+                }
+            }
+        }
+        __syncwarp();
+        {
+            // rows of the last incomplete sector wait in shared memory
+            const int q = (lim > r ? lim : r) + lane;
+            if (lane < 3 && q < e) {
+                pK[p * 4 + (q & 3)] = bK[q - x];
+                if (PAY) pP[p * 4 + (q & 3)] = bP[q - x];
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NCL; k++) rr[k] += static_cast<int>(tot[k]);
+}
+
+template <bool PAY, int BITS, int T, int IT, int MINB>
+__global__ void __launch_bounds__(T, MINB) k_part_scatter_sf(PartArgs A)
+{
+    using L = SfLayout<PAY, BITS, T, IT>;
+    constexpr int NWARP = L::NWARP, CH = L::CH, NCL = L::NCL;
+    static_assert(L::FMAX % NWARP == 0, "digits per warp");
+    extern __shared__ __align__(128) unsigned char smem[];
+    long long *pK = reinterpret_cast<long long *>(smem + L::pK);
+    long long *pP = reinterpret_cast<long long *>(smem + L::pP);
+    long long **ob = reinterpret_cast<long long **>(smem + L::ob);
+    const int F = static_cast<int>(A.dmask) + 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int Ffull = 1 << A.log2f;
+    long long *outK = reinterpret_cast<long long *>(A.out_keys);
+    const int64_t dP = PAY ? static_cast<long long *>(A.out_pay[0]) - outK : 0;
+    const bool vecP = (dP & 1) == 0;
+    const int aoff = static_cast<int>((reinterpret_cast<uintptr_t>(outK) >> 3) & 3);
+
+    for (int64_t item = blockIdx.x; item < A.nitems; item += gridDim.x) {
+        int64_t lo, hi;
+        int b = static_cast<int>(item), qhi = 0;
+        if (A.omode == WC_PASS2) {
+            const int nspan = (A.g1 + A.span - 1) / A.span;
+            qhi = static_cast<int>(item / nspan);
+            b = static_cast<int>(item % nspan) * A.span;
+            const int b1 = b + A.span < A.g1 ? b + A.span : A.g1;
+            const int64_t F1 = Ffull >> A.sub_bits;
+            lo = A.t1[static_cast<int64_t>(b) * F1 + qhi];
+            hi = A.t1[static_cast<int64_t>(b1 - 1) * F1 + qhi] + A.h1[static_cast<int64_t>(b1 - 1) * F1 + qhi];
+        } else {
+            lo = static_cast<int64_t>(b) * A.rows_per_block;
+            hi = min(A.n, lo + A.rows_per_block);
+        }
+        if (hi <= lo) continue;
+        // every warp: q of the next row of its lanes' digits (-hl, where hl
+        // rows fill the key sector the digit's output run starts in); the
+        // owner warp keeps the key address of q = 0
+        int rr[NCL];
+        __syncthreads();                              // the previous item's pending rows are written
+#pragma unroll
+        for (int k = 0; k < NCL; k++) {
+            const int p = lane + 32 * k;
+            rr[k] = 0;
+            if (p < F) {
+                int64_t g;
+                if (A.omode == WC_SINGLE) {
+                    g = A.base[p] + A.off[static_cast<int64_t>(b) * Ffull + p];
+                } else if (A.omode == WC_PASS1) {
+                    g = A.t1[static_cast<int64_t>(b) * F + p];
+                } else {
+                    const int dst = (qhi << A.sub_bits) | p;
+                    g = A.base[dst] + A.off[static_cast<int64_t>(b) * Ffull + dst];
+                }
+                const int hl = static_cast<int>((4 - ((g + aoff) & 3)) & 3);
+                rr[k] = -hl;
+                if (p % NWARP == warp) ob[p] = outK + g + hl;
+            }
+        }
+        const int64_t nch = (hi - lo + CH - 1) / CH;
+        longlong2 kv[IT], nkv[IT];
+        if (hi - lo >= CH) sf_load_full<PAY, IT>(A, lo, kv);
+        else wc_load<PAY, IT>(A, lo, hi, kv);
+        // chunks in pairs, so that the prefetched rows alternate between kv
+        // and nkv without register copies
+        for (int64_t c = 0; c < nch; c += 2) {
+            {
+                const int64_t r0 = lo + c * CH;
+                const int64_t nx = r0 + CH;
+                if (nx + CH <= hi) sf_load_full<PAY, IT>(A, nx, nkv);
+                else if (nx < hi) wc_load<PAY, IT>(A, nx, hi, nkv);
+                if (r0 + CH <= hi)
+                    sf_chunk<PAY, BITS, T, IT, true>(A, smem, 0, kv, 0, CH, F, rr, outK, dP, vecP);
+                else
+                    sf_chunk<PAY, BITS, T, IT, false>(A, smem, 0, kv, 0, static_cast<int>(hi - r0), F, rr, outK, dP,
+                                                      vecP);
+            }
+            if (c + 1 < nch) {
+                const int64_t r0 = lo + (c + 1) * CH;
+                const int64_t nx = r0 + CH;
+                if (nx + CH <= hi) sf_load_full<PAY, IT>(A, nx, kv);
+                else if (nx < hi) wc_load<PAY, IT>(A, nx, hi, kv);
+                if (r0 + CH <= hi)
+                    sf_chunk<PAY, BITS, T, IT, true>(A, smem, 1, nkv, 0, CH, F, rr, outK, dP, vecP);
+                else
+                    sf_chunk<PAY, BITS, T, IT, false>(A, smem, 1, nkv, 0, static_cast<int>(hi - r0), F, rr, outK, dP,
+                                                      vecP);
+            }
+        }
+        __syncwarp();
+        // rows still pending at the end of the item (owner lanes)
+#pragma unroll
+        for (int k = 0; k < NCL; k++) {
+            const int p = lane + 32 * k;
+            if (p < F && p % NWARP == warp && rr[k] > 0) {
+                const int r = rr[k];
+                long long *o = ob[p] + (r & ~3);
+                for (int j = 0; j < (r & 3); j++) {
+                    if (!QE_DCHECK(A.st, o + j >= outK && o + j < outK + A.n, (o + j) - outK)) continue;
+                    __stcs(o + j, pK[p * 4 + j]);
+                    if (PAY) __stcs(o + dP + j, pP[p * 4 + j]);
+                }
+            }
+        }
+    }
+}
+
 // Two passes: per first-pass range b and high digit q, the rows and the
 // scratch start: h1[b][q] = sum over the low digits r of hist[b][q, r] and
 // t1[b][q] = base[q, 0] + sum over r of off[b][q, r] (range b's rows with
@@ -638,25 +819,36 @@ __global__ void k_part_two_pass_tables(const uint32_t *hist, const int64_t *off,
     t1[i] = base[q << sub_bits] + o;
 }
 
-// Block shapes of the write-combining scatter, by fan-out (measured on
-// GB300).  Two blocks of 256 per SM let one block's per-destination phases
-// overlap the other's row phases (up to 32 digits).  From 64 digits a chunk
-// of 256 x 8 rows gives each digit runs too short for the per-digit work, so
-// one block of 512 runs per SM; and every block writes one output page per
-// destination and column at a time, so beyond a few hundred pages per SM
-// (two blocks at 256 digits) the address translation caches miss.
+// Block shapes of the write-combining scatters, by digits per launch
+// (measured on GB300).  Up to 32 digits, two blocks of 256 threads x 8 rows
+// per SM: at 600M pairs and fan-out 1024 it beat one block of 512 x 8 (9.3 ms
+// against 9.9 ms for the two passes), 512 x 4 and 1024 x 4 at 32 warps per
+// SM (10.0 / 10.9 ms; 64 registers with spills) and 256 x 6 (10.1 ms).  From
+// 64 digits a chunk of 256 x 8 rows gives each digit runs too short for the
+// per-digit work, so one block of 512 runs per SM; and every block writes
+// one output page per destination and column at a time, so beyond a few
+// hundred pages per SM (two blocks at 256 digits) the address translation
+// caches miss.
 struct WcShape {
     int threads, items;
     const void *kernel;
+    size_t smem;
 };
 
 template <bool PAY>
 static WcShape wc_shape(int log2f)
 {
-    if (log2f <= 5) return {256, 8, reinterpret_cast<const void *>(k_part_scatter_wc<PAY, 5, 256, 8, 2>)};
-    if (log2f <= 6) return {512, 8, reinterpret_cast<const void *>(k_part_scatter_wc<PAY, 6, 512, 8, 1>)};
-    if (log2f <= 8) return {512, 8, reinterpret_cast<const void *>(k_part_scatter_wc<PAY, 8, 512, 8, 1>)};
-    return {512, 8, reinterpret_cast<const void *>(k_part_scatter_wc<PAY, 10, 512, 8, 1>)};
+    const int F = 1 << log2f;
+    if (log2f <= 5)
+        return {256, 8, reinterpret_cast<const void *>(k_part_scatter_sf<PAY, 5, 256, 8, 2>),
+                SfLayout<PAY, 5, 256, 8>::total};
+    if (log2f <= 6)
+        return {512, 8, reinterpret_cast<const void *>(k_part_scatter_sf<PAY, 6, 512, 8, 1>),
+                SfLayout<PAY, 6, 512, 8>::total};
+    if (log2f <= 8)
+        return {512, 8, reinterpret_cast<const void *>(k_part_scatter_wc<PAY, 8, 512, 8, 1>),
+                WcLayout(F, PAY, 512, 8).total};
+    return {512, 8, reinterpret_cast<const void *>(k_part_scatter_wc<PAY, 10, 512, 8, 1>), WcLayout(F, PAY, 512, 8).total};
 }
 
 // General scatter (any payload columns, any fan-out up to 4096), at 1024
@@ -722,9 +914,9 @@ extern "C" qe_status qe_partition(qe_ctx *ctx, const int64_t *keys, const qe_col
     const WcShape ws = fast ? wc_shape<true>(log2_fanout - sub_bits) : wc_shape<false>(log2_fanout - sub_bits);
     const WcShape ws2 = fast ? wc_shape<true>(sub_bits) : wc_shape<false>(sub_bits);
     const bool big = gen1024::scatter_smem(log2_fanout, fast) <= ctx->smem_optin;
-    const size_t smem = wc ? WcLayout(F1, fast, ws.threads, ws.items).total
+    const size_t smem = wc ? ws.smem
                            : (big ? gen1024::scatter_smem(log2_fanout, fast) : gen512::scatter_smem(log2_fanout, fast));
-    const size_t smem2 = two ? WcLayout(1 << sub_bits, fast, ws2.threads, ws2.items).total : 0;
+    const size_t smem2 = two ? ws2.smem : 0;
     if (smem > ctx->smem_optin || smem2 > ctx->smem_optin)
         return qe_fail(ctx, QE_ERR_INVALID_ARG, "partition: fan-out too large");
     const void *kscatter;
