@@ -62,21 +62,38 @@ struct BatchArgs {
 __device__ void batch_build(const BatchPipe &B, const BatchItem &I, qe_dev_status *st)
 {
     const HtView &h = B.P.ht;
-    for (int64_t r = I.row0 + threadIdx.x; r < I.row1; r += BT) {
-        const int32_t k = __ldcs(B.dim_key + r);
-        const uint32_t s = static_cast<uint32_t>(k) - static_cast<uint32_t>(h.key_min);
-        if (s >= h.range) {
-            dev_report(st, QE_ERR_INVALID_ARG, 0);
-            continue;
+    // BB_ROWS rows per thread and step: their bitmap atomics (whose old value
+    // decides whether the payload is written) are in flight together
+    constexpr int BB_ROWS = 4;
+    for (int64_t r0 = I.row0 + threadIdx.x; r0 < I.row1; r0 += BT * BB_ROWS) {
+        uint32_t sl[BB_ROWS], old[BB_ROWS];
+        int32_t v[BB_ROWS];
+#pragma unroll
+        for (int j = 0; j < BB_ROWS; j++) {
+            const int64_t r = r0 + j * BT;
+            sl[j] = r < I.row1 ? static_cast<uint32_t>(__ldcs(B.dim_key + r)) - static_cast<uint32_t>(h.key_min)
+                               : 0xffffffffu;
+            v[j] = r < I.row1 && B.ht_pay ? __ldcs(B.dim_pay + r) : 0;
         }
-        const uint32_t bit = 1u << (s & 31);
-        const uint32_t old = atomicOr(B.ht_bm + (s >> 5), bit);
-        if (!B.ht_pay) continue;          // a key set (semi- or anti-join): repeats are fine
-        if (old & bit) {
-            dev_report(st, QE_ERR_DUPLICATE_KEY, 0);
-            continue;
+#pragma unroll
+        for (int j = 0; j < BB_ROWS; j++) {
+            old[j] = 0;
+            if (sl[j] < h.range) old[j] = atomicOr(B.ht_bm + (sl[j] >> 5), 1u << (sl[j] & 31));
         }
-        B.ht_pay[s] = __ldcs(B.dim_pay + r);
+#pragma unroll
+        for (int j = 0; j < BB_ROWS; j++) {
+            if (r0 + j * BT >= I.row1) continue;
+            if (sl[j] >= h.range) {
+                dev_report(st, QE_ERR_INVALID_ARG, 0);
+                continue;
+            }
+            if (!B.ht_pay) continue;          // a key set (semi- or anti-join): repeats are fine
+            if ((old[j] >> (sl[j] & 31)) & 1u) {
+                dev_report(st, QE_ERR_DUPLICATE_KEY, 0);
+                continue;
+            }
+            B.ht_pay[sl[j]] = v[j];
+        }
     }
 }
 

@@ -68,25 +68,43 @@ __global__ void k_minmax_init(int32_t *mm)
 }
 
 // payload == NULL: a key set (repeated keys are not an error).
+// BD_ROWS rows per thread and step, so that their bitmap atomics (whose old
+// value decides whether the payload is written) are in flight together.
+constexpr int BD_ROWS = 4;
+
 __global__ void __launch_bounds__(256) k_build_dense(const int32_t *keys, const int32_t *pay, int64_t n,
                                                      int32_t key_min, uint32_t range, int32_t *payload,
                                                      uint32_t *bitmap, qe_dev_status *st)
 {
-    for (int64_t i = blockIdx.x * 256ll + threadIdx.x; i < n; i += static_cast<int64_t>(gridDim.x) * 256) {
-        const int32_t k = __ldcs(keys + i);
-        const uint32_t s = static_cast<uint32_t>(k) - static_cast<uint32_t>(key_min);
-        if (s >= range) {
-            dev_report(st, QE_ERR_INVALID_ARG, 0);
-            continue;
+    const int64_t step = static_cast<int64_t>(gridDim.x) * 256 * BD_ROWS;
+    for (int64_t i0 = blockIdx.x * 256ll * BD_ROWS + threadIdx.x; i0 < n; i0 += step) {
+        uint32_t sl[BD_ROWS], old[BD_ROWS];
+        int32_t v[BD_ROWS];
+#pragma unroll
+        for (int j = 0; j < BD_ROWS; j++) {
+            const int64_t i = i0 + j * 256;
+            sl[j] = i < n ? static_cast<uint32_t>(__ldcs(keys + i)) - static_cast<uint32_t>(key_min) : 0xffffffffu;
+            v[j] = i < n && payload ? __ldcs(pay + i) : 0;
         }
-        const uint32_t bit = 1u << (s & 31);
-        const uint32_t old = atomicOr(bitmap + (s >> 5), bit);
-        if (!payload) continue;
-        if (old & bit) {
-            dev_report(st, QE_ERR_DUPLICATE_KEY, 0);
-            continue;
+#pragma unroll
+        for (int j = 0; j < BD_ROWS; j++) {
+            old[j] = 0;
+            if (sl[j] < range) old[j] = atomicOr(bitmap + (sl[j] >> 5), 1u << (sl[j] & 31));
         }
-        payload[s] = __ldcs(pay + i);
+#pragma unroll
+        for (int j = 0; j < BD_ROWS; j++) {
+            if (i0 + j * 256 >= n) continue;
+            if (sl[j] >= range) {
+                dev_report(st, QE_ERR_INVALID_ARG, 0);
+                continue;
+            }
+            if (!payload) continue;
+            if ((old[j] >> (sl[j] & 31)) & 1u) {
+                dev_report(st, QE_ERR_DUPLICATE_KEY, 0);
+                continue;
+            }
+            payload[sl[j]] = v[j];
+        }
     }
 }
 

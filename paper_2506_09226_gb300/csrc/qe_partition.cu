@@ -473,20 +473,23 @@ __global__ void __launch_bounds__(T, MINB) k_part_scatter_wc(PartArgs A)
 //   * every digit's run in the sorted chunk starts on the parity of its r
 //     (one row of padding per digit at most), so the rows of whole sectors
 //     move from shared memory to DRAM as 16-byte pairs of rows;
-//   * the sorted chunk is double-buffered: two barriers per chunk.
-// Each digit is written by one warp (digits p == warp mod NWARP): the rows
-// that complete its pending sector, its whole sectors, two rows per lane,
-// and the rows of its last incomplete sector, kept in shared memory until a
-// later chunk (or the end of the item) completes them.
+//   * the sorted chunk holds its keys, then its payloads, and is
+//     double-buffered: two barriers per chunk.
+// Each digit is written by one warp (digits p == warp mod NWARP): first the
+// rows of every owned digit's partial sectors in one round, a lane per row
+// (rows completing the digit's pending sector, rows before the item's first
+// sector boundary, and rows of the last incomplete sector, which stay in
+// shared memory until a later chunk or the end of the item completes them),
+// then the whole sectors digit by digit, two rows per lane.
 template <bool PAY, int BITS, int T, int IT>
 struct SfLayout {
     static constexpr int NWARP = T / 32, CH = T * IT, NCL = BITS > 5 ? 2 : 1, FMAX = 32 * NCL;
     static constexpr int SROW = CH + FMAX;                      // rows of one sorted buffer (with padding)
-    static constexpr size_t sK = 0;                             // [2][SROW] keys
-    static constexpr size_t sP = sK + 2 * SROW * 8;             // [2][SROW] payloads
-    static constexpr size_t pK = sP + (PAY ? 2 * SROW * 8 : 0); // [FMAX][4] pending keys
-    static constexpr size_t pP = pK + FMAX * 4 * 8;             // [FMAX][4] pending payloads
-    static constexpr size_t ob = pP + (PAY ? FMAX * 4 * 8 : 0); // [FMAX] key address of q = 0
+    static constexpr int ES = PAY ? 16 : 8;                     // bytes per row: key, payload
+    static_assert(SROW % 2 == 0, "16-byte pairs of rows");
+    static constexpr size_t sb = 0;                             // [2] x (SROW keys, SROW payloads)
+    static constexpr size_t pend = sb + 2 * SROW * ES;          // FMAX * 4 keys, FMAX * 4 payloads
+    static constexpr size_t ob = pend + FMAX * 4 * ES;          // [FMAX] key address of q = 0
     static constexpr size_t cnt = ob + FMAX * 8;                // [NWARP][FMAX] rows per warp and digit
     static constexpr size_t total = cnt + NWARP * FMAX * 4;
 };
@@ -557,8 +560,37 @@ __device__ __forceinline__ void sf_rank(const PartArgs &A, const longlong2 (&kv)
     }
 }
 
-// One chunk: rank, place in sorted buffer `buf`, write out.  Returns nothing;
-// rr (q of every lane digit's next row) advances by the chunk's rows.
+// Row t of a sorted buffer (N rows) or of the pending slots (N = FMAX * 4)
+// as (key, payload): N keys, then N payloads.
+template <bool PAY, int N>
+__device__ __forceinline__ longlong2 sf_row(const unsigned char *base, int t)
+{
+    const long long *k = reinterpret_cast<const long long *>(base);
+    return make_longlong2(k[t], PAY ? k[N + t] : 0);
+}
+template <bool PAY, int N>
+__device__ __forceinline__ void sf_put(unsigned char *base, int t, longlong2 v)
+{
+    long long *k = reinterpret_cast<long long *>(base);
+    k[t] = v.x;
+    if (PAY) k[N + t] = v.y;
+}
+
+// Value of a digit's register state (held by lane p & 31 of every warp,
+// in slot p >> 5) for the digit p of the calling lane.
+template <int NCL, typename V>
+__device__ __forceinline__ V sf_get(const V (&v)[NCL], int p)
+{
+    V x = __shfl_sync(QE_FULL_MASK, v[0], p & 31);
+    if (NCL > 1) {
+        const V y = __shfl_sync(QE_FULL_MASK, v[NCL - 1], p & 31);
+        if (p >= 32) x = y;
+    }
+    return x;
+}
+
+// One chunk: rank, place in sorted buffer `buf`, write out.  rr (q of every
+// lane digit's next row) advances by the chunk's rows.
 template <bool PAY, int BITS, int T, int IT, bool FULL>
 __device__ __forceinline__ void sf_chunk(const PartArgs &A, unsigned char *smem, int buf, const longlong2 (&kv)[IT],
                                          int vlo, int vhi, int F, int (&rr)[SfLayout<PAY, BITS, T, IT>::NCL],
@@ -566,11 +598,11 @@ __device__ __forceinline__ void sf_chunk(const PartArgs &A, unsigned char *smem,
 {
     using L = SfLayout<PAY, BITS, T, IT>;
     constexpr int NWARP = L::NWARP, NCL = L::NCL, FMAX = L::FMAX, SROW = L::SROW;
+    constexpr int NJ = FMAX / NWARP, LPD = 32 / NJ;      // digits per warp, lanes per digit
+    static_assert(LPD >= 8, "a digit's partial sectors take up to seven lanes");
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    long long *bK = reinterpret_cast<long long *>(smem + L::sK) + buf * SROW;
-    long long *bP = reinterpret_cast<long long *>(smem + L::sP) + buf * SROW;
-    long long *pK = reinterpret_cast<long long *>(smem + L::pK);
-    long long *pP = reinterpret_cast<long long *>(smem + L::pP);
+    unsigned char *sb = smem + L::sb + static_cast<size_t>(buf) * SROW * L::ES;
+    unsigned char *pend = smem + L::pend;
     long long *const *ob = reinterpret_cast<long long *const *>(smem + L::ob);
     uint32_t *cnt = reinterpret_cast<uint32_t *>(smem + L::cnt);
 
@@ -624,17 +656,61 @@ __device__ __forceinline__ void sf_chunk(const PartArgs &A, unsigned char *smem,
                 const uint32_t pos1 = __shfl_sync(QE_FULL_MASK, o1, src);
                 if (dg[i] >= 32u) pos = pos1;
             }
-            if (FULL || dg[i] != 0xffffffffu) {
-                pos += rk[i];
-                bK[pos] = kv[i].x;
-                if (PAY) bP[pos] = kv[i].y;
-            }
+            if (FULL || dg[i] != 0xffffffffu) sf_put<PAY, SROW>(sb, static_cast<int>(pos + rk[i]), kv[i]);
         }
     }
     __syncthreads();
-    // this warp's digits
+    // the rows of every owned digit's partial sectors: lanes LPD j .. LPD j + 6
+    // of digit p = warp + NWARP j; roles 0..3 write rows now, roles 4..6 keep
+    // rows pending.  All reads come before any write of a pending slot.
+    {
+        const int j = lane / LPD, role = lane % LPD;
+        const int p = warp + NWARP * j;
+        const int r = sf_get<NCL>(rr, p);
+        const int h = static_cast<int>(sf_get<NCL>(tot, p));
+        const int s = static_cast<int>(sf_get<NCL>(s0, p));
+        longlong2 v = make_longlong2(0, 0);
+        long long *dst = nullptr;
+        int slot = -1;
+        if (p < F) {
+            const int e = r + h;
+            const int x = r - s;                       // row q sits at sorted position q - x; x is even
+            const int lim = e > 0 ? (e & ~3) : 0;      // rows q < lim are written now
+            const int a = r > 0 ? ((r + 3) & ~3) : 0;  // first whole sector of this chunk's rows
+            long long *o = ob[p];
+            if (role < 4) {
+                if (r < 0) {
+                    // rows before the item's first sector boundary: their
+                    // sector is shared with the previous item
+                    const int q = r + role;
+                    if (role < 3 && q < 0 && q < e) {
+                        v = sf_row<PAY, SROW>(sb, q - x);
+                        dst = o + q;
+                    }
+                } else if ((r & 3) && e >= a) {
+                    // the pending sector completes: its earlier rows, then this chunk's
+                    const int q = (r & ~3) + role;
+                    v = q < r ? sf_row<PAY, FMAX * 4>(pend, p * 4 + role) : sf_row<PAY, SROW>(sb, q - x);
+                    dst = o + q;
+                }
+            } else if (role < 7) {
+                const int q = (lim > r ? lim : r) + role - 4;
+                if (q < e) {
+                    v = sf_row<PAY, SROW>(sb, q - x);
+                    slot = p * 4 + (q & 3);
+                }
+            }
+        }
+        __syncwarp();
+        if (dst && QE_DCHECK(A.st, dst >= outK && dst < outK + A.n, dst - outK)) {
+            __stcs(dst, v.x);
+            if (PAY) __stcs(dst + dP, v.y);
+        }
+        if (slot >= 0) sf_put<PAY, FMAX * 4>(pend, slot, v);
+    }
+    // whole sectors, two rows per lane
 #pragma unroll
-    for (int j = 0; j < FMAX / NWARP; j++) {
+    for (int j = 0; j < NJ; j++) {
         const int p = warp + NWARP * j;
         if (p >= F) break;
         const int kk = p >> 5, src = p & 31;
@@ -643,47 +719,23 @@ __device__ __forceinline__ void sf_chunk(const PartArgs &A, unsigned char *smem,
         const int s = static_cast<int>(__shfl_sync(QE_FULL_MASK, kk ? s0[NCL - 1] : s0[0], src));
         long long *o = ob[p];
         const int e = r + h;
-        const int x = r - s;                       // row q sits at bK[q - x]; x is even
-        const int lim = e > 0 ? (e & ~3) : 0;      // rows q < lim are written now
-        const int a = r > 0 ? ((r + 3) & ~3) : 0;  // first whole sector of this chunk's rows
-        if (r < 0) {
-            // rows before the item's first sector boundary: their sector is
-            // shared with the previous item and written in two parts
-            const int q = r + lane;
-            if (lane < 3 && q < 0 && q < e && QE_DCHECK(A.st, o + q >= outK && o + q < outK + A.n, (o + q) - outK)) {
-                __stcs(o + q, bK[q - x]);
-                if (PAY) __stcs(o + q + dP, bP[q - x]);
-            }
-        } else if ((r & 3) && e >= a) {
-            // the pending sector completes: its earlier rows, then this chunk's
-            const int q = (r & ~3) + lane;
-            if (lane < 4 && QE_DCHECK(A.st, o + q >= outK && o + q < outK + A.n, (o + q) - outK)) {
-                const bool old = q < r;
-                __stcs(o + q, old ? pK[p * 4 + lane] : bK[q - x]);
-                if (PAY) __stcs(o + q + dP, old ? pP[p * 4 + lane] : bP[q - x]);
-            }
-        }
+        const int x = r - s;
+        const int lim = e > 0 ? (e & ~3) : 0;
+        const int a = r > 0 ? ((r + 3) & ~3) : 0;
         for (int q = a + 2 * lane; q < lim; q += 64) {
             if (!QE_DCHECK(A.st, o + q >= outK && o + q + 1 < outK + A.n, (o + q) - outK)) continue;
-            const int t = q - x;
-            __stcs(reinterpret_cast<longlong2 *>(o + q), *reinterpret_cast<const longlong2 *>(bK + t));
+            // rows q - x and q - x + 1 (q - x even): one 16-byte load of
+            // their keys and one of their payloads
+            const longlong2 k2 = reinterpret_cast<const longlong2 *>(sb)[(q - x) >> 1];
+            __stcs(reinterpret_cast<longlong2 *>(o + q), k2);
             if (PAY) {
-                const longlong2 v = *reinterpret_cast<const longlong2 *>(bP + t);
+                const longlong2 v2 = reinterpret_cast<const longlong2 *>(sb)[(SROW + q - x) >> 1];
                 if (vecP) {
-                    __stcs(reinterpret_cast<longlong2 *>(o + q + dP), v);
+                    __stcs(reinterpret_cast<longlong2 *>(o + q + dP), v2);
                 } else {
-                    __stcs(o + q + dP, v.x);
-                    __stcs(o + q + 1 + dP, v.y);
+                    __stcs(o + q + dP, v2.x);
+                    __stcs(o + q + 1 + dP, v2.y);
                 }
-            }
-        }
-        __syncwarp();
-        {
-            // rows of the last incomplete sector wait in shared memory
-            const int q = (lim > r ? lim : r) + lane;
-            if (lane < 3 && q < e) {
-                pK[p * 4 + (q & 3)] = bK[q - x];
-                if (PAY) pP[p * 4 + (q & 3)] = bP[q - x];
             }
         }
     }
@@ -698,8 +750,7 @@ __global__ void __launch_bounds__(T, MINB) k_part_scatter_sf(PartArgs A)
     constexpr int NWARP = L::NWARP, CH = L::CH, NCL = L::NCL;
     static_assert(L::FMAX % NWARP == 0, "digits per warp");
     extern __shared__ __align__(128) unsigned char smem[];
-    long long *pK = reinterpret_cast<long long *>(smem + L::pK);
-    long long *pP = reinterpret_cast<long long *>(smem + L::pP);
+    unsigned char *pend = smem + L::pend;
     long long **ob = reinterpret_cast<long long **>(smem + L::ob);
     const int F = static_cast<int>(A.dmask) + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -789,8 +840,9 @@ __global__ void __launch_bounds__(T, MINB) k_part_scatter_sf(PartArgs A)
                 long long *o = ob[p] + (r & ~3);
                 for (int j = 0; j < (r & 3); j++) {
                     if (!QE_DCHECK(A.st, o + j >= outK && o + j < outK + A.n, (o + j) - outK)) continue;
-                    __stcs(o + j, pK[p * 4 + j]);
-                    if (PAY) __stcs(o + dP + j, pP[p * 4 + j]);
+                    const longlong2 v = sf_row<PAY, L::FMAX * 4>(pend, p * 4 + j);
+                    __stcs(o + j, v.x);
+                    if (PAY) __stcs(o + dP + j, v.y);
                 }
             }
         }
