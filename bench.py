@@ -490,7 +490,7 @@ def run_skew(args, qe, ctx, dev, stream, peak, it):
     part_bytes states the extra traffic of the partition round trips (the
     count pass reads the 8-byte key of every row; each survivor is written
     by the scatter, read and written by the split and read by the fold, 24
-    bytes each time).  Also timed: the 50 % point through the direct HBM hash table
+    bytes each time) and hbm_frac_with_partition counts them as well.  Also timed: the 50 % point through the direct HBM hash table
     (the path the partitioning replaces) and the group-by on 10^6
     dictionary codes."""
     from paper_2506_09226_gb300 import datagen
@@ -537,10 +537,12 @@ def run_skew(args, qe, ctx, dev, stream, peak, it):
             nsurv = None
             if "part_count" in kern:
                 nsurv = int((fact[colname] < c).sum().item())
+            pb = (8 * n_fact + 96 * nsurv) if nsurv is not None else 0
             sweep[f"{int(round(sel * 100))}%"] = {
                 "ms": ms, "rows_per_s": n_fact / (ms * 1e-3), "ngroups": ng,
                 "hbm_frac": round(28 * n_fact / (ms * 1e-3) / 1e9 / peak, 4), "kernels_ms": kern,
-                "part_bytes": (8 * n_fact + 96 * nsurv) if nsurv is not None else 0}
+                "part_bytes": pb,
+                "hbm_frac_with_partition": round((28 * n_fact + pb) / (ms * 1e-3) / 1e9 / peak, 4)}
         res[f"sweep_{colname}"] = sweep
     # the autotuner's choice at 50 %: direct table or partitioned group-by
     # (fan-out 64 / 128 / 256 parts), dense or open-addressing join table
