@@ -44,7 +44,7 @@ struct BatchPipe {
     unsigned long long *emitted;       // groups written to `out`
     unsigned *build_done, *probe_done;
     uint64_t hslots;                   // HBM hash table slots
-    int32_t star;                      // star shape: the specialised row loop
+    int32_t star;                      // star kind + 1 (0: the generic row loop)
     int32_t cnt;                       // COUNT aggregate of derived averages, or -1
 };
 
@@ -164,17 +164,28 @@ __device__ void batch_finalize(const BatchPipe &B, qe_dev_status *st)
 // pass that prefetches the next tile across the stride (4.67 / 5.32 ms).
 constexpr int64_t STAR_TR = static_cast<int64_t>(BT) * 3;
 
+template <int JK>
 __device__ __noinline__ void item_star_smem(const PipeSpec &P, unsigned long long *sm, int64_t j, int64_t m, int64_t n)
 {
     for (int64_t t = j * STAR_TR; t < n; t += m * STAR_TR)
-        star_range<false, 3, BT, true>(P, sm, t, t + STAR_TR < n ? t + STAR_TR : n, STAR_TR);
+        star_range<false, 3, BT, true, JK>(P, sm, t, t + STAR_TR < n ? t + STAR_TR : n, STAR_TR);
 }
 
+template <int JK>
 __device__ __noinline__ void item_star_global(const PipeSpec &P, unsigned long long *sm, int64_t j, int64_t m,
                                               int64_t n)
 {
     for (int64_t t = j * STAR_TR; t < n; t += m * STAR_TR)
-        star_range<true, 3, BT, false>(P, sm, t, t + STAR_TR < n ? t + STAR_TR : n, STAR_TR);
+        star_range<true, 3, BT, false, JK>(P, sm, t, t + STAR_TR < n ? t + STAR_TR : n, STAR_TR);
+}
+
+// A star item of kind JK: the direct array in shared memory or in HBM.
+template <int JK>
+__device__ __forceinline__ void item_star(const PipeSpec &P, const TableCfg &T, unsigned long long *sm, int64_t j,
+                                          int64_t m, int64_t n)
+{
+    if (T.mode == TM_SMEM_DENSE) item_star_smem<JK>(P, sm, j, m, n);
+    else item_star_global<JK>(P, sm, j, m, n);
 }
 
 __device__ __noinline__ void item_generic(const PipeSpec &P, const TableCfg T, unsigned long long *sm, int64_t j,
@@ -250,9 +261,13 @@ __global__ void __launch_bounds__(BT, 1) k_batch(BatchArgs A)
         if (!s_flag) {
             table_zero(P, T, sm);
             __syncthreads();
-            if (B.star && T.mode == TM_SMEM_DENSE) item_star_smem(P, sm, I.row0, B.nprobe, I.row1);
-            else if (B.star) item_star_global(P, sm, I.row0, B.nprobe, I.row1);
-            else item_generic(P, T, sm, I.row0, B.nprobe, I.row1);
+            switch (B.star) {
+            case 1 + STAR_INNER: item_star<STAR_INNER>(P, T, sm, I.row0, B.nprobe, I.row1); break;
+            case 1 + STAR_SEMI: item_star<STAR_SEMI>(P, T, sm, I.row0, B.nprobe, I.row1); break;
+            case 1 + STAR_ANTI: item_star<STAR_ANTI>(P, T, sm, I.row0, B.nprobe, I.row1); break;
+            case 1 + STAR_NONE: item_star<STAR_NONE>(P, T, sm, I.row0, B.nprobe, I.row1); break;
+            default: item_generic(P, T, sm, I.row0, B.nprobe, I.row1);
+            }
             __syncthreads();
             table_flush(P, T, sm, B.star ? 2 : 0);   // star items: 32-bit COUNT and SUM halves
         }
@@ -396,7 +411,7 @@ extern "C" qe_status qe_batch_create(qe_ctx *ctx, const qe_pipeline_desc *descs,
                 B.T.mode = TM_GLOBAL_HASH;
             }
         }
-        B.star = !ctx->tune_force_generic && star_shape(B.P, B.T) ? 1 : 0;
+        B.star = ctx->tune_force_generic ? 0 : 1 + star_kind(B.P, B.T);
         if (B.star) star_predicate(B.P);
         uint64_t hs = 64;
         while (hs < static_cast<uint64_t>(2 * (outs[i].capacity > 32 ? outs[i].capacity : 32))) hs <<= 1;

@@ -591,9 +591,4 @@ static inline int star_kind(const PipeSpec &P, const TableCfg &T)
     return P.join_kind == QE_JOIN_SEMI ? STAR_SEMI : STAR_ANTI;
 }
 
-// The inner-join star (the one kind the batch kernel runs as a star item).
-static inline bool star_shape(const PipeSpec &P, const TableCfg &T)
-{
-    return star_kind(P, T) == STAR_INNER;
-}
 

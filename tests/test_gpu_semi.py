@@ -267,3 +267,58 @@ def test_batch_semi_anti_mixed(ctx):
     for k in keep:
         if k[3] is not None:
             k[3].destroy()
+
+
+@pytest.mark.parametrize("smem_slots", [0, -1])
+def test_batch_star_kinds(ctx, smem_slots):
+    """Semi- and anti-join pipelines and pipelines with no join run the star
+    row loop inside a batch as well, beside inner-join star pipelines: group
+    keys of three shapes, the direct arrays in shared memory (smem_slots 0) or
+    in HBM (-1), key sets built inside the kernel, pipelines of several
+    32,768-row items with ragged tails.  Every result equals the oracle's and
+    the pipeline's solo run."""
+    descs, groups, outs, refs, keep = [], [], [], [], []
+
+    def add(d, ref, cap):
+        g, o = qe.alloc_groups(cap, 4, torch.device("cuda"))
+        descs.append(d)
+        groups.append(g)
+        outs.append(o)
+        refs.append((ref, cap))
+
+    i = 0
+    for shape in ("flag", "flag_qty", "fk_5000"):
+        hi, lo, rng_, span = STAR_KEYS[shape]
+        for kind in (qe.SEMI, qe.ANTI, "none"):
+            seed = 300 + i
+            n = 200_003 + 4_099 * i
+            i += 1
+            fact = datagen.star_fact(n, span, seed=seed)
+            dk = np.random.default_rng(seed).integers(span // 10, span - span // 10, span // 2).astype(np.int32)
+            f = [fact[c].cuda() for c in COLS]
+            join = kind != "none"
+            dkt = cuda(dk) if join else None
+            keep.append((f, dkt))
+            d = qe.pipeline_desc(f, [(1, qe.LT, 1278)], fk_col=0 if join else -1, dim_key=dkt, key_hi_col=hi,
+                                 key_lo_col=lo, aggs=AGGS, key_range=rng_,
+                                 dim_key_range=(0, span - 1) if join else None,
+                                 join_kind=kind if join else qe.INNER)
+            q = O.Query(preds=[O.Pred(1, O.LT, 1278)], fk_col=0 if join else -1, key_hi_col=hi, key_lo_col=lo,
+                        aggs=O_AGGS, join_kind=kind if join else O.INNER)
+            add(d, O.pipeline([fact[c].numpy() for c in COLS], q, dk if join else None, None), 8192)
+    for j in range(2):
+        n, nd = 150_001 + 33 * j, 20_000
+        dim = datagen.star_dim(nd, 25, seed=400 + j)
+        fact = datagen.star_fact(n, nd, seed=400 + j)
+        f = [fact[c].cuda() for c in COLS]
+        dkt, dpt = cuda(dim["key"].numpy()), cuda(dim["attr"].numpy())
+        keep.append((f, dkt, dpt))
+        d = qe.pipeline_desc(f, [(1, qe.LT, 1278)], fk_col=0, dim_key=dkt, dim_payload=dpt, key_hi_col=4,
+                             key_lo_col=qe.JOIN_PAYLOAD, aggs=AGGS, key_range=((0, 2), (0, 24)),
+                             dim_key_range=(0, nd - 1))
+        q = O.Query(preds=[O.Pred(1, O.LT, 1278)], fk_col=0, key_hi_col=4, key_lo_col=O.JOIN_PAYLOAD, aggs=O_AGGS)
+        add(d, O.pipeline([fact[c].numpy() for c in COLS], q, dim["key"].numpy(), dim["attr"].numpy()), 128)
+    qe.qe_batch_run(ctx, descs, outs, opts=qe.qe_batch_opts(0, 1 << 15, smem_slots, 0))
+    for d, g, (ref, cap) in zip(descs, groups, refs):
+        _assert_groups(g, ref)
+        _assert_groups(qe.qe_pipeline(ctx, d, cap), ref)
