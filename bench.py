@@ -15,9 +15,10 @@ Also reported on the same JSON line: the per-kernel roofline of the dominant
 kernel, the per-kernel breakdown, partition at fan-out 256 / 4096, the
 per-operator path (filter -> probe -> group-by as separate launches), the
 25K-group variant, an end-to-end number through the public API with the
-inputs copied from pinned host memory every step, the batched and served
-forms, clocks sampled during the timed region, and the CPU oracle on a
-bounded sample (cpu_baseline).
+inputs copied from pinned host memory every step, the batched form (10,000
+inner-join pipelines, and 600 pipelines whose join kinds cycle semi, anti,
+none, inner) and the served form, clocks sampled during the timed region,
+and the CPU oracle on a bounded sample (cpu_baseline).
 
 --impl reference times the CPU oracle (oracle/) on a bounded sample of the
 same workload, per step, and prints the same line with "impl": "reference".
@@ -827,6 +828,8 @@ def run_forms(args, qe, ctx, dev, stream, fact, dim, peak):
     out = {}
     if "batch" in args.forms:
         out["batch"] = B.bench_batch(ctx, args.batch_count, dev, stream, peak, log=log)
+        # join kinds other than the inner join, in one batch
+        out["batch"]["mixed_kinds"] = B.bench_batch_kinds(ctx, 600, dev, stream, peak)
     if "serve" in args.forms:
         from paper_2506_09226_gb300 import serve as S
         out["serve"] = S.bench_serve(ctx, dev, stream, peak, duration_s=args.serve_seconds, log=log,

@@ -171,3 +171,71 @@ def bench_batch(ctx, count: int, device, stream, peak_gbs: float, log=print, ste
             "per_pipeline_fused": {"ms": t_solo, "rows_per_s": rows / (t_solo * 1e-3)},
             "per_operator": {"ms": t_perop, "rows_per_s": rows / (t_perop * 1e-3)},
             "speedup_vs_per_operator": t_perop / t_batch, "speedup_vs_per_pipeline": t_solo / t_batch}
+
+
+def kind_descs(w: dict, kinds) -> list:
+    """Pipeline descriptors over a batch_star workload whose join kinds cycle
+    through `kinds` (qe.INNER, qe.SEMI, qe.ANTI, or "none" for no join):
+    inner joins group by (flag, attribute) as star_descs does; the others
+    group by flag, and a semi- or anti-join tests membership in the first
+    half of the pipeline's dimension keys."""
+    f, d = w["fact"], w["dim"]
+    descs = []
+    for i in range(len(w["sizes"])):
+        a, n = int(w["fact_off"][i]), int(w["sizes"][i])
+        b, nd = int(w["dim_off"][i]), int(w["dim_sizes"][i])
+        cols = [f[c][a:a + n] for c in STAR_COLS]
+        k = kinds[i % len(kinds)]
+        if k == qe.INNER:
+            descs.append(qe.pipeline_desc(cols, [(1, qe.LT, DATE_LT)], fk_col=0, dim_key=d["key"][b:b + nd],
+                                          dim_payload=d["attr"][b:b + nd], key_hi_col=4, key_lo_col=qe.JOIN_PAYLOAD,
+                                          aggs=STAR_AGGS, dim_key_range=(0, nd - 1),
+                                          key_range=((0, 2), (0, N_ATTR - 1)), expected_groups=75))
+        elif k == "none":
+            descs.append(qe.pipeline_desc(cols, [(1, qe.LT, DATE_LT)], fk_col=-1, key_hi_col=-1, key_lo_col=4,
+                                          aggs=STAR_AGGS, key_range=(None, (0, 2)), expected_groups=3))
+        else:
+            descs.append(qe.pipeline_desc(cols, [(1, qe.LT, DATE_LT)], fk_col=0, dim_key=d["key"][b:b + max(1, nd // 2)],
+                                          key_hi_col=-1, key_lo_col=4, aggs=STAR_AGGS, dim_key_range=(0, nd - 1),
+                                          key_range=(None, (0, 2)), expected_groups=3, join_kind=k))
+    return descs
+
+
+def bench_batch_kinds(ctx, count: int, device, stream, peak_gbs: float, steps: int = 3, seed: int = 9) -> dict:
+    """`count` log-uniform pipelines whose join kinds cycle semi, anti, none,
+    inner, in one persistent launch, against per-pipeline fused calls.
+    Algorithmic bytes: 21 per fact row (17 without a join) plus 4 per key
+    built into a semi- / anti-join key set and 8 per dimension row of an
+    inner join."""
+    kinds = (qe.SEMI, qe.ANTI, "none", qe.INNER)
+    sizes = datagen.log_uniform_sizes(count, 1e3, 1e7, seed=seed)
+    w = datagen.batch_star(sizes, N_ATTR, seed=seed, device=device)
+    descs = kind_descs(w, kinds)
+    outs = BatchOutputs(count, CAPACITY, device)
+    b = qe.Batch(ctx, descs, outs.structs, qe.qe_batch_opts(0, 1 << 18, 0, 1), stream)
+    b.launch(stream)
+    ctx.sync_status(stream)
+    t_batch = min(_event_ms(lambda: b.launch(stream), stream) for _ in range(steps))
+    ctx.sync_status(stream)
+    b.destroy(stream)
+    out1, cout1 = qe.alloc_groups(CAPACITY, 4, device)
+
+    def solo():
+        for d in descs:
+            qe.qe_pipeline(ctx, d, CAPACITY, stream=stream, check=False, out=(out1, cout1))
+    solo()
+    ctx.sync_status(stream)
+    t_solo = _event_ms(solo, stream)
+    alg = 0
+    for i, n in enumerate(sizes):
+        k, nd = kinds[i % len(kinds)], max(1, int(n) // 10)
+        alg += (17 if k == "none" else 21) * int(n) + (8 * nd if k == qe.INNER else 0) + \
+            (4 * max(1, nd // 2) if k in (qe.SEMI, qe.ANTI) else 0)
+    rows = int(sizes.sum())
+    del w, outs, descs
+    torch.cuda.empty_cache()
+    return {"pipelines": count, "fact_rows": rows, "kinds": "semi, anti, none, inner (cycling)",
+            "batched": {"ms": t_batch, "rows_per_s": rows / (t_batch * 1e-3),
+                        "hbm_frac": round(alg / (t_batch * 1e-3) / 1e9 / peak_gbs, 4)},
+            "per_pipeline_fused": {"ms": t_solo, "rows_per_s": rows / (t_solo * 1e-3)},
+            "speedup_vs_per_pipeline": t_solo / t_batch}
