@@ -378,18 +378,16 @@ constexpr uint64_t STAR_NSUM_SLOTS = 1024;
 // (membership in a dense key set), or there is no join.
 enum { STAR_INNER = 0, STAR_SEMI = 1, STAR_ANTI = 2, STAR_NONE = 3 };
 
-// The row work of one star tile: predicate, dense lookup, direct-array
-// (or spilled hash) update of the ITEMS rows a thread holds; bit k of cin
-// marks row k as inside the range.  cl holds the key column of the kinds
-// other than STAR_INNER.
-template <bool GLOBAL, int ITEMS, bool NSUM, int JK = STAR_INNER, bool L2H = false>
-__device__ __forceinline__ void star_rows(const PipeSpec &P, unsigned long long *sm, const int (&cd)[ITEMS],
-                                          const int (&cf)[ITEMS], const int (&ch)[ITEMS], const int (&cl)[ITEMS],
-                                          const int (&cq)[ITEMS], const long long (&cx)[ITEMS], unsigned cin,
-                                          uint64_t pol_keep = 0)
+// The row work of one star tile, in two steps: star_lookup (predicate and
+// dense lookup or membership test of the ITEMS rows a thread holds; bit k
+// of cin marks row k as inside the range; cl holds the key column of the
+// kinds other than STAR_INNER) and star_fold (direct-array, or spilled
+// hash, update of the rows that pass).
+template <int ITEMS, int JK = STAR_INNER, bool L2H = false>
+__device__ __forceinline__ void star_lookup(const PipeSpec &P, const int (&cd)[ITEMS], const int (&cf)[ITEMS],
+                                            const int (&cl)[ITEMS], unsigned cin, uint64_t pol_keep, bool (&ok)[ITEMS],
+                                            int32_t (&pay)[ITEMS])
 {
-    bool ok[ITEMS];
-    int32_t pay[ITEMS];
 #pragma unroll
     for (int k = 0; k < ITEMS; k++) {
         const bool pass = (cd[k] >= P.p0_lo && cd[k] <= P.p0_hi) != static_cast<bool>(P.p0_neg);
@@ -414,6 +412,13 @@ __device__ __forceinline__ void star_rows(const PipeSpec &P, unsigned long long 
             ok[k] = live && (JK == STAR_SEMI ? in : !in);
         }
     }
+}
+
+template <bool GLOBAL, int ITEMS, bool NSUM, int JK = STAR_INNER>
+__device__ __forceinline__ void star_fold(const PipeSpec &P, unsigned long long *sm, const int (&ch)[ITEMS],
+                                          const int (&cq)[ITEMS], const long long (&cx)[ITEMS], const bool (&ok)[ITEMS],
+                                          const int32_t (&pay)[ITEMS])
+{
 #pragma unroll
     for (int k = 0; k < ITEMS; k++) {
         if (!ok[k]) continue;
@@ -519,8 +524,20 @@ __device__ __forceinline__ void star_range(const PipeSpec &P, unsigned long long
             cq[k] = q[k];
             cx[k] = x[k];
         }
-        load(t0 + stride);   // next tile's loads overlap this tile's work
-        star_rows<GLOBAL, ITEMS, NSUM, JK, L2H>(P, sm, cd, cf, ch, cl, cq, cx, cin, pol_keep);
+        // the next tile's loads overlap this tile's work; a tile's dimension
+        // reads (payload or membership word) are issued before them, so they
+        // do not queue behind them (600M rows: semi-join 3.51 -> 2.73 ms,
+        // inner join unchanged; the join-free kind has no such reads)
+        bool ok[ITEMS];
+        int32_t pay[ITEMS];
+        if constexpr (JK == STAR_NONE) {
+            load(t0 + stride);
+            star_lookup<ITEMS, JK, L2H>(P, cd, cf, cl, cin, pol_keep, ok, pay);
+        } else {
+            star_lookup<ITEMS, JK, L2H>(P, cd, cf, cl, cin, pol_keep, ok, pay);
+            load(t0 + stride);
+        }
+        star_fold<GLOBAL, ITEMS, NSUM, JK>(P, sm, ch, cq, cx, ok, pay);
     }
 }
 
