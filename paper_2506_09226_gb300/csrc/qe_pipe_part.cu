@@ -575,8 +575,12 @@ __global__ void __launch_bounds__(SPT, 1) k_pp_split(SplitArgs A)
 // its part) are folded into a shared-memory hash table, whose groups are
 // then written straight to the output; keys that find no slot within the
 // probe limit go to an HBM spill table, emitted at the end.
-constexpr int FT = 1024;                        // threads per fold block
-constexpr int F_ITEMS = 2;                      // rows per lane in flight (64 per warp)
+constexpr int FT = 1024;                        // threads per fold (and spill-emit) block
+// Rows per lane and step of the fold, the next step's rows prefetched in
+// registers (300M skewed rows, fold at 50 / 90 % selectivity: one row per
+// lane 2.52 / 4.14 ms; two rows 2.73 / 4.64 ms; two rows with 768 threads
+// 3.21 / 5.48 ms; two rows without the prefetch 2.58 / 4.27 ms).
+constexpr int FOLD_FI = 1;
 constexpr int F_RUNS = 1024;                    // runs described in shared memory at a time
 constexpr int F_PROBES = 64;                    // shared-table probe limit before a spill
 constexpr int F_EMIT_GROUPS = 128;              // slot groups of 32 in the largest shared table
@@ -715,7 +719,7 @@ __device__ void pp_emit_table(const FoldArgs &A, unsigned long long *t, int log2
 
 // STAR: the aggregates are [SUM(X*Y), COUNT, MIN(X), MAX(X)] (the shared
 // COUNT word then holds a 32-bit count, read back whole: its high half stays 0).
-template <int T, int MINB, bool STAR>
+template <int T, int MINB, bool STAR, int FI>
 __global__ void __launch_bounds__(T, MINB) k_pp_fold(FoldArgs A)
 {
     static_assert(T <= F_RUNS, "a block describes at most F_RUNS runs at a time");
@@ -749,77 +753,102 @@ __global__ void __launch_bounds__(T, MINB) k_pp_fold(FoldArgs A)
             }
             __syncthreads();
             // each warp takes whole runs (about 60 rows each at the planned
-            // sizes): its lanes read consecutive rows of the run
-            for (int r = warp; r < nr; r += T / 32) {
-                const int64_t r0 = rstart[r];
-                const unsigned len = rlen[r];
-                for (unsigned i0 = 0; i0 < len; i0 += 32 * F_ITEMS) {
-                    unsigned long long kx[F_ITEMS];
-                    long long xv[F_ITEMS], yv[F_ITEMS];
+            // sizes), r = warp, warp + NW, ...: its lanes read consecutive
+            // rows of a run, FI rows per lane a step, and the rows of the
+            // warp's next step (the run's next rows, or its next run's
+            // first) are loaded while the current step's are folded
+            constexpr int NW = T / 32;
+            int r = warp;
+            unsigned i0 = 0;
+            while (r < nr && rlen[r] == 0) r += NW;
+            unsigned long long kx[FI], nkx[FI];
+            long long xv[FI], yv[FI], nxv[FI], nyv[FI];
+            auto load_step = [&](int rr, unsigned ii, unsigned long long (&k)[FI], long long (&x)[FI],
+                                 long long (&y)[FI]) {
+                const int64_t b0 = rstart[rr];
+                const unsigned len = rlen[rr];
 #pragma unroll
-                    for (int t = 0; t < F_ITEMS; t++) {
-                        const unsigned i = i0 + t * 32 + lane;
-                        kx[t] = 0;
-                        xv[t] = yv[t] = 0;
-                        if (i < len) {
-                            const PartRow *row = A.rows2 + r0 + i;
-                            kx[t] = __ldcs(&row->kx);
-                            xv[t] = __ldcs(&row->x);
-                            yv[t] = __ldcs(&row->y);
-                        }
+                for (int t = 0; t < FI; t++) {
+                    const unsigned i = ii + t * 32 + lane;
+                    k[t] = 0;
+                    x[t] = y[t] = 0;
+                    if (i < len) {
+                        const PartRow *row = A.rows2 + b0 + i;
+                        k[t] = __ldcs(&row->kx);
+                        x[t] = __ldcs(&row->x);
+                        y[t] = __ldcs(&row->y);
                     }
+                }
+            };
+            if (r < nr) load_step(r, 0, kx, xv, yv);
+            while (r < nr) {
+                int r2 = r;
+                unsigned i2 = i0 + 32 * FI;
+                if (i2 >= rlen[r]) {
+                    i2 = 0;
+                    r2 = r + NW;
+                    while (r2 < nr && rlen[r2] == 0) r2 += NW;
+                }
+                if (r2 < nr) load_step(r2, i2, nkx, nxv, nyv);
 #pragma unroll
-                    for (int t = 0; t < F_ITEMS; t++) {
-                        if (!kx[t]) continue;
-                        const uint32_t mask = static_cast<uint32_t>(S - 1);
-                        uint32_t h = static_cast<uint32_t>(dev_fmix64(kx[t])) & mask;
-                        int slot = -1;
-                        for (int pr = 0; pr < F_PROBES; pr++) {
-                            const unsigned long long cur = reinterpret_cast<volatile unsigned long long *>(tab)[h];
-                            if (cur == kx[t]) {
+                for (int t = 0; t < FI; t++) {
+                    if (!kx[t]) continue;
+                    const uint32_t mask = static_cast<uint32_t>(S - 1);
+                    uint32_t h = static_cast<uint32_t>(dev_fmix64(kx[t])) & mask;
+                    int slot = -1;
+                    for (int pr = 0; pr < F_PROBES; pr++) {
+                        const unsigned long long cur = reinterpret_cast<volatile unsigned long long *>(tab)[h];
+                        if (cur == kx[t]) {
+                            slot = static_cast<int>(h);
+                            break;
+                        }
+                        if (cur == 0) {
+                            const unsigned long long old = atomicCAS(tab + h, 0ull, kx[t]);
+                            if (old == 0 || old == kx[t]) {
                                 slot = static_cast<int>(h);
                                 break;
                             }
-                            if (cur == 0) {
-                                const unsigned long long old = atomicCAS(tab + h, 0ull, kx[t]);
-                                if (old == 0 || old == kx[t]) {
-                                    slot = static_cast<int>(h);
-                                    break;
-                                }
-                            }
-                            h = (h + 1) & mask;
                         }
-                        if constexpr (STAR) {
-                            // [SUM(X*Y), COUNT, MIN(X), MAX(X)]: the encodings
-                            // inline, COUNT as a 32-bit counter in its word's
-                            // low half (a sub-part has fewer than 2^32 rows)
-                            const unsigned long long v = static_cast<unsigned long long>(xv[t]) *
-                                                         static_cast<unsigned long long>(yv[t]);
-                            const unsigned long long emin = ~(static_cast<unsigned long long>(xv[t]) ^ GB_SIGN);
-                            const unsigned long long emax = static_cast<unsigned long long>(xv[t]) ^ GB_SIGN;
-                            if (slot >= 0) {
-                                smem_add64(tab + S + slot, v);
-                                atomicAdd(reinterpret_cast<unsigned *>(tab + 2 * S + slot), 1u);
-                                unsigned long long *cmin = tab + 3 * S + slot, *cmax = tab + 4 * S + slot;
-                                if (*cmin < emin) atomicMax(cmin, emin);
-                                if (*cmax < emax) atomicMax(cmax, emax);
-                            } else {
-                                pp_spill_ni(A.spill, A.ops, kx[t], v, 1ull, emin, emax, A.spilled);
-                            }
+                        h = (h + 1) & mask;
+                    }
+                    if constexpr (STAR) {
+                        // [SUM(X*Y), COUNT, MIN(X), MAX(X)]: the encodings
+                        // inline, COUNT as a 32-bit counter in its word's
+                        // low half (a sub-part has fewer than 2^32 rows)
+                        const unsigned long long v = static_cast<unsigned long long>(xv[t]) *
+                                                     static_cast<unsigned long long>(yv[t]);
+                        const unsigned long long emin = ~(static_cast<unsigned long long>(xv[t]) ^ GB_SIGN);
+                        const unsigned long long emax = static_cast<unsigned long long>(xv[t]) ^ GB_SIGN;
+                        if (slot >= 0) {
+                            smem_add64(tab + S + slot, v);
+                            atomicAdd(reinterpret_cast<unsigned *>(tab + 2 * S + slot), 1u);
+                            unsigned long long *cmin = tab + 3 * S + slot, *cmax = tab + 4 * S + slot;
+                            if (*cmin < emin) atomicMax(cmin, emin);
+                            if (*cmax < emax) atomicMax(cmax, emax);
                         } else {
-                            unsigned long long e[QE_MAX_AGGS];
+                            pp_spill_ni(A.spill, A.ops, kx[t], v, 1ull, emin, emax, A.spilled);
+                        }
+                    } else {
+                        unsigned long long e[QE_MAX_AGGS];
 #pragma unroll
-                            for (int a = 0; a < QE_MAX_AGGS; a++) e[a] = a < A.ops.n ? pp_value(A, a, xv[t], yv[t]) : 0ull;
-                            if (slot >= 0) {
+                        for (int a = 0; a < QE_MAX_AGGS; a++) e[a] = a < A.ops.n ? pp_value(A, a, xv[t], yv[t]) : 0ull;
+                        if (slot >= 0) {
 #pragma unroll
-                                for (int a = 0; a < QE_MAX_AGGS; a++)
-                                    if (a < A.ops.n) st_update(tab + (1 + a) * S + slot, A.ops.op[a], e[a]);
-                            } else {
-                                pp_spill_ni(A.spill, A.ops, kx[t], e[0], e[1], e[2], e[3], A.spilled);
-                            }
+                            for (int a = 0; a < QE_MAX_AGGS; a++)
+                                if (a < A.ops.n) st_update(tab + (1 + a) * S + slot, A.ops.op[a], e[a]);
+                        } else {
+                            pp_spill_ni(A.spill, A.ops, kx[t], e[0], e[1], e[2], e[3], A.spilled);
                         }
                     }
                 }
+#pragma unroll
+                for (int t = 0; t < FI; t++) {
+                    kx[t] = nkx[t];
+                    xv[t] = nxv[t];
+                    yv[t] = nyv[t];
+                }
+                r = r2;
+                i0 = i2;
             }
             __syncthreads();
         }
@@ -1007,10 +1036,10 @@ qe_status pipeline_partitioned(qe_ctx *ctx, PipeSpec &P, const qe_groups_out *ou
         e = cudaFuncSetAttribute(k_pp_split, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm_split));
     const bool star_aggs = P.ops.n == 4 && P.ops.op[0] == QE_SUM && P.src[0] == SRC_XY && P.ops.op[1] == QE_COUNT &&
                            P.ops.op[2] == QE_MIN && P.src[2] == SRC_X && P.ops.op[3] == QE_MAX && P.src[3] == SRC_X;
-    const void *kfold = fold2 ? (star_aggs ? reinterpret_cast<const void *>(k_pp_fold<FT / 2, 2, true>)
-                                           : reinterpret_cast<const void *>(k_pp_fold<FT / 2, 2, false>))
-                              : (star_aggs ? reinterpret_cast<const void *>(k_pp_fold<FT, 1, true>)
-                                           : reinterpret_cast<const void *>(k_pp_fold<FT, 1, false>));
+    const void *kfold = fold2 ? (star_aggs ? reinterpret_cast<const void *>(k_pp_fold<FT / 2, 2, true, 1>)
+                                           : reinterpret_cast<const void *>(k_pp_fold<FT / 2, 2, false, 1>))
+                              : (star_aggs ? reinterpret_cast<const void *>(k_pp_fold<FT, 1, true, FOLD_FI>)
+                                           : reinterpret_cast<const void *>(k_pp_fold<FT, 1, false, FOLD_FI>));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(kfold, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm_fold));
     if (e == cudaSuccess && P.n > 0) {
