@@ -875,7 +875,9 @@ __global__ void k_part_two_pass_tables(const uint32_t *hist, const int64_t *off,
 // (measured on GB300).  Up to 32 digits, two blocks of 256 threads x 8 rows
 // per SM: at 600M pairs and fan-out 1024 it beat one block of 512 x 8 (9.3 ms
 // against 9.9 ms for the two passes), 512 x 4 and 1024 x 4 at 32 warps per
-// SM (10.0 / 10.9 ms; 64 registers with spills) and 256 x 6 (10.1 ms).  From
+// SM (10.0 / 10.9 ms; 64 registers with spills), 256 x 6 (10.1 ms), and three
+// blocks of 256 x 8 per SM with no register prefetch (80 registers; 9.7 ms,
+// 9.8 ms with two such blocks).  From
 // 64 digits a chunk of 256 x 8 rows gives each digit runs too short for the
 // per-digit work, so one block of 512 runs per SM; and every block writes
 // one output page per destination and column at a time, so beyond a few
