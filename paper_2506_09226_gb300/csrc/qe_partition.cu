@@ -16,9 +16,9 @@
 //                      offset per destination so rows keep their input order.
 //                      Three kernels:
 //                      k_part_scatter_sf (one int64 payload or none, at most
-//                        64 digits: F <= 64 in one pass, F = 1024 .. 4096 in
+//                        64 digits: F <= 64 in one pass, F = 512 .. 4096 in
 //                        two passes) and k_part_scatter_wc (the same inputs,
-//                        F = 128 .. 512 in one pass): register-prefetched
+//                        F = 128 or 256 in one pass): register-prefetched
 //                        chunks, one-pass ranking with per-warp counters, and
 //                        write-combining of 32-byte sectors (see below);
 //                      k_part_scatter (qe_part_general.cuh; any payloads, any
@@ -154,8 +154,8 @@ __global__ void __launch_bounds__(1024) k_part_basescan(const int64_t *tot, int6
 
 // ---------------------------------------------------------------------------
 // Write-combining scatter: int64 keys with no payload or one int64 payload,
-// 128 .. 512 digits (k_part_scatter_sf below takes up to 64 digits, with the
-// same chunk walk and sector rule).  A block walks its rows in chunks of T * IT;
+// 128 or 256 digits in one pass (k_part_scatter_sf below takes up to 64
+// digits, with the same chunk walk and sector rule).  A block walks its rows in chunks of T * IT;
 // the next chunk is loaded into registers while the current one is ranked.
 //
 // Ranking is one pass: each warp counts destinations in its own row of the
@@ -172,7 +172,11 @@ __global__ void __launch_bounds__(1024) k_part_basescan(const int64_t *tot, int6
 // most three) until a later chunk fills the sector; only whole sectors are
 // written, except the first and last sector of the block's range, which it
 // shares with the neighbouring blocks.
-constexpr int WC_MAX_LOG2F = 9;
+// Fan-outs up to 2^WC_MAX_LOG2F take one pass; above, two passes of at most
+// 64 digits (600M pairs at fan-out 512: 11.5 ms in one pass of
+// k_part_scatter_wc, against the two passes of 32 and 16 digits; at 256 the
+// one pass and two passes of 16 measured about equal).
+constexpr int WC_MAX_LOG2F = 8;
 
 // Shared-memory layout of a block of T threads (chunks of T * IT rows).
 struct WcLayout {
@@ -902,7 +906,7 @@ static WcShape wc_shape(int log2f)
     if (log2f <= 8)
         return {512, 8, reinterpret_cast<const void *>(k_part_scatter_wc<PAY, 8, 512, 8, 1>),
                 WcLayout(F, PAY, 512, 8).total};
-    return {512, 8, reinterpret_cast<const void *>(k_part_scatter_wc<PAY, 10, 512, 8, 1>), WcLayout(F, PAY, 512, 8).total};
+    return {0, 0, nullptr, 0};   // beyond one write-combining pass: not taken
 }
 
 // General scatter (any payload columns, any fan-out up to 4096), at 1024
