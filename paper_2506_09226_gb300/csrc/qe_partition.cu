@@ -313,36 +313,15 @@ __global__ void __launch_bounds__(T, MINB) k_part_scatter_wc(PartArgs A)
     const int aoff = static_cast<int>((reinterpret_cast<uintptr_t>(outK) >> 3) & 3);
     for (int i = threadIdx.x; i < NWARP * FC / 8; i += T) reinterpret_cast<uint4 *>(cnt)[i] = make_uint4(0, 0, 0, 0);
 
+    // one pass only (WC_SINGLE): item b is input range b
     for (int64_t item = blockIdx.x; item < A.nitems; item += gridDim.x) {
-        int64_t lo, hi;
-        int b = static_cast<int>(item), qhi = 0;
-        if (A.omode == WC_PASS2) {
-            // ranges [b, b1) of high digit q: their scratch rows are one run
-            // (t1[b + 1][q] = t1[b][q] + h1[b][q]), and so are their output
-            // rows of each destination (q, r), in range order
-            const int nspan = (A.g1 + A.span - 1) / A.span;
-            qhi = static_cast<int>(item / nspan);
-            b = static_cast<int>(item % nspan) * A.span;
-            const int b1 = b + A.span < A.g1 ? b + A.span : A.g1;
-            const int64_t F1 = Ffull >> A.sub_bits;
-            lo = A.t1[static_cast<int64_t>(b) * F1 + qhi];
-            hi = A.t1[static_cast<int64_t>(b1 - 1) * F1 + qhi] + A.h1[static_cast<int64_t>(b1 - 1) * F1 + qhi];
-        } else {
-            lo = static_cast<int64_t>(b) * A.rows_per_block;
-            hi = min(A.n, lo + A.rows_per_block);
-        }
+        const int b = static_cast<int>(item);
+        const int64_t lo = static_cast<int64_t>(b) * A.rows_per_block;
+        const int64_t hi = min(A.n, lo + A.rows_per_block);
         const int64_t nch = (hi - lo + CH - 1) / CH;
         __syncthreads();                              // the previous item's tables are done with
         for (int p = threadIdx.x; p < F; p += T) {
-            int64_t g;
-            if (A.omode == WC_SINGLE) {
-                g = A.base[p] + A.off[static_cast<int64_t>(b) * Ffull + p];
-            } else if (A.omode == WC_PASS1) {
-                g = A.t1[static_cast<int64_t>(b) * F + p];
-            } else {
-                const int dst = (qhi << A.sub_bits) | p;
-                g = A.base[dst] + A.off[static_cast<int64_t>(b) * Ffull + dst];
-            }
+            const int64_t g = A.base[p] + A.off[static_cast<int64_t>(b) * Ffull + p];
             const int hl = static_cast<int>((4 - ((g + aoff) & 3)) & 3);
             ob[p] = outK + g + hl;
             rq[p] = -hl;
