@@ -445,7 +445,7 @@ __global__ void __launch_bounds__(T, MINB) k_part_scatter_wc(PartArgs A)
 
 // ---------------------------------------------------------------------------
 // Small fan-out scatter: at most 64 digits per launch (fan-out <= 64 in one
-// pass, and both passes of fan-out 1024 .. 4096).  Same work items, output
+// pass, and both passes of fan-out 512 .. 4096).  Same work items, output
 // offsets and write-combining rule as k_part_scatter_wc, with the work per
 // row cut down:
 //   * a chunk whose rows all lie inside the item is loaded and ranked
