@@ -36,13 +36,25 @@ namespace {
 __global__ void __launch_bounds__(256) k_minmax(const int32_t *keys, const int32_t *pay, int64_t n, int32_t *mm)
 {
     int32_t lo = INT_MAX, hi = INT_MIN, plo = INT_MAX, phi = INT_MIN;
-    for (int64_t i = blockIdx.x * 256ll + threadIdx.x; i < n; i += static_cast<int64_t>(gridDim.x) * 256) {
-        const int32_t k = __ldcs(keys + i);
-        const int32_t p = pay ? __ldcs(pay + i) : INT_MAX;
-        lo = min(lo, k);
-        hi = max(hi, k);
-        plo = min(plo, p);
-        phi = pay ? max(phi, p) : phi;
+    // four rows per thread and step, their loads in flight together
+    constexpr int MR = 4;
+    const int64_t step = static_cast<int64_t>(gridDim.x) * 256 * MR;
+    for (int64_t i0 = blockIdx.x * 256ll * MR + threadIdx.x; i0 < n; i0 += step) {
+        int32_t k[MR], p[MR];
+#pragma unroll
+        for (int j = 0; j < MR; j++) {
+            const int64_t i = i0 + j * 256;
+            k[j] = i < n ? __ldcs(keys + i) : INT_MAX;
+            p[j] = i < n && pay ? __ldcs(pay + i) : INT_MAX;
+        }
+#pragma unroll
+        for (int j = 0; j < MR; j++) {
+            if (i0 + j * 256 >= n) continue;
+            lo = min(lo, k[j]);
+            hi = max(hi, k[j]);
+            plo = min(plo, p[j]);
+            phi = pay ? max(phi, p[j]) : phi;
+        }
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {

@@ -106,17 +106,23 @@ __global__ void __launch_bounds__(HT) k_part_hist(PartArgs A)
     }
 }
 
-// One thread per destination p: prefix of hist[.][p] over blocks.
+// One thread per destination p: prefix of hist[.][p] over blocks, sixteen
+// blocks' counts loaded at a time so that their loads overlap.
 __global__ void k_part_colscan(const uint32_t *hist, int64_t *off, int64_t *tot, int G, int F)
 {
+    constexpr int B = 16;
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= F) return;
     int64_t run = 0;
-    for (int b = 0; b < G; b++) {
-        int64_t idx = static_cast<int64_t>(b) * F + p;
-        uint32_t h = hist[idx];
-        off[idx] = run;
-        run += h;
+    for (int b0 = 0; b0 < G; b0 += B) {
+        uint32_t h[B];
+#pragma unroll
+        for (int j = 0; j < B; j++) h[j] = b0 + j < G ? hist[static_cast<int64_t>(b0 + j) * F + p] : 0u;
+#pragma unroll
+        for (int j = 0; j < B; j++) {
+            if (b0 + j < G) off[static_cast<int64_t>(b0 + j) * F + p] = run;
+            run += h[j];
+        }
     }
     tot[p] = run;
 }
