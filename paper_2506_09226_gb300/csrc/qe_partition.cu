@@ -588,6 +588,10 @@ __device__ __forceinline__ void sf_chunk(const PartArgs &A, unsigned char *smem,
     using L = SfLayout<PAY, BITS, T, IT>;
     constexpr int NWARP = L::NWARP, NCL = L::NCL, FMAX = L::FMAX, SROW = L::SROW;
     constexpr int NJ = FMAX / NWARP, LPD = 32 / NJ;      // digits per warp, lanes per digit
+    // whole sectors as bulk stores for up to 32 digits (at 600M pairs: fan-out
+    // 1024 in 8.73 against 8.97 ms); with 64 digits a launch the per-lane
+    // copy measured faster (fan-out 64: 5.98 against 6.06 ms)
+    constexpr bool SF_BULK = BITS <= 5;
     static_assert(LPD >= 8, "a digit's partial sectors take up to seven lanes");
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *sb = smem + L::sb + static_cast<size_t>(buf) * SROW * L::ES;
@@ -599,6 +603,10 @@ __device__ __forceinline__ void sf_chunk(const PartArgs &A, unsigned char *smem,
 #pragma unroll
     for (int k = 0; k < NCL; k++) cl[k] = 0;
     sf_rank<BITS, IT, FULL, NCL>(A, kv, vlo, vhi, dg, rk, cl);
+    // this buffer's bulk stores of two chunks ago have read it (the previous
+    // chunk's, from the other buffer, may still be running); the barrier
+    // below orders the wait before anyone writes the buffer
+    if (SF_BULK && lane < NJ) tma_store_wait_read<1>();
 #pragma unroll
     for (int k = 0; k < NCL; k++)
         if (lane + 32 * k < F) cnt[warp * FMAX + lane + 32 * k] = cl[k];
@@ -648,6 +656,7 @@ __device__ __forceinline__ void sf_chunk(const PartArgs &A, unsigned char *smem,
             if (FULL || dg[i] != 0xffffffffu) sf_put<PAY, SROW>(sb, static_cast<int>(pos + rk[i]), kv[i]);
         }
     }
+    if (SF_BULK) fence_proxy_async_smem();   // the sorted rows, visible to the bulk stores below
     __syncthreads();
     // the rows of every owned digit's partial sectors: lanes LPD j .. LPD j + 6
     // of digit p = warp + NWARP j; roles 0..3 write rows now, roles 4..6 keep
@@ -697,33 +706,59 @@ __device__ __forceinline__ void sf_chunk(const PartArgs &A, unsigned char *smem,
         }
         if (slot >= 0) sf_put<PAY, FMAX * 4>(pend, slot, v);
     }
-    // whole sectors, two rows per lane
-#pragma unroll
-    for (int j = 0; j < NJ; j++) {
+    // whole sectors: lane j of the warp stores digit warp + NWARP j's run
+    // [a, lim) of keys (and of payloads) with one bulk copy each, from the
+    // sorted buffer (16-byte aligned: q - x is even) to its 32-byte-aligned
+    // output rows; payload columns not 16-byte aligned beside the keys take
+    // two rows per lane instead (SF_BULK), as every column does without bulk
+    // stores
+    if (SF_BULK) {
+        const int j = lane < NJ ? lane : 0;
         const int p = warp + NWARP * j;
-        if (p >= F) break;
-        const int kk = p >> 5, src = p & 31;
-        const int r = __shfl_sync(QE_FULL_MASK, kk ? rr[NCL - 1] : rr[0], src);
-        const int h = static_cast<int>(__shfl_sync(QE_FULL_MASK, kk ? tot[NCL - 1] : tot[0], src));
-        const int s = static_cast<int>(__shfl_sync(QE_FULL_MASK, kk ? s0[NCL - 1] : s0[0], src));
-        long long *o = ob[p];
-        const int e = r + h;
-        const int x = r - s;
-        const int lim = e > 0 ? (e & ~3) : 0;
-        const int a = r > 0 ? ((r + 3) & ~3) : 0;
-        for (int q = a + 2 * lane; q < lim; q += 64) {
-            if (!QE_DCHECK(A.st, o + q >= outK && o + q + 1 < outK + A.n, (o + q) - outK)) continue;
-            // rows q - x and q - x + 1 (q - x even): one 16-byte load of
-            // their keys and one of their payloads
-            const longlong2 k2 = reinterpret_cast<const longlong2 *>(sb)[(q - x) >> 1];
-            __stcs(reinterpret_cast<longlong2 *>(o + q), k2);
-            if (PAY) {
-                const longlong2 v2 = reinterpret_cast<const longlong2 *>(sb)[(SROW + q - x) >> 1];
-                if (vecP) {
-                    __stcs(reinterpret_cast<longlong2 *>(o + q + dP), v2);
-                } else {
-                    __stcs(o + q + dP, v2.x);
-                    __stcs(o + q + 1 + dP, v2.y);
+        const int r = sf_get<NCL>(rr, p < F ? p : 0);
+        const int h = static_cast<int>(sf_get<NCL>(tot, p < F ? p : 0));
+        const int s = static_cast<int>(sf_get<NCL>(s0, p < F ? p : 0));
+        if (lane < NJ && p < F) {
+            long long *o = ob[p];
+            const int e = r + h;
+            const int x = r - s;
+            const int lim = e > 0 ? (e & ~3) : 0;
+            const int a = r > 0 ? ((r + 3) & ~3) : 0;
+            if (lim > a && QE_DCHECK(A.st, o + a >= outK && o + lim <= outK + A.n, (o + a) - outK)) {
+                const int t = a - x;
+                const uint32_t bytes = static_cast<uint32_t>(lim - a) * 8u;
+                tma_store_1d(o + a, reinterpret_cast<const long long *>(sb) + t, bytes);
+                if (PAY && vecP) tma_store_1d(o + a + dP, reinterpret_cast<const long long *>(sb) + SROW + t, bytes);
+            }
+        }
+        if (lane < NJ) tma_store_commit();
+    }
+    if (!SF_BULK || (PAY && !vecP)) {
+#pragma unroll
+        for (int j = 0; j < NJ; j++) {
+            const int p = warp + NWARP * j;
+            if (p >= F) break;
+            const int kk = p >> 5, src = p & 31;
+            const int r = __shfl_sync(QE_FULL_MASK, kk ? rr[NCL - 1] : rr[0], src);
+            const int h = static_cast<int>(__shfl_sync(QE_FULL_MASK, kk ? tot[NCL - 1] : tot[0], src));
+            const int s = static_cast<int>(__shfl_sync(QE_FULL_MASK, kk ? s0[NCL - 1] : s0[0], src));
+            long long *o = ob[p];
+            const int e = r + h;
+            const int x = r - s;
+            const int lim = e > 0 ? (e & ~3) : 0;
+            const int a = r > 0 ? ((r + 3) & ~3) : 0;
+            for (int q = a + 2 * lane; q < lim; q += 64) {
+                if (!QE_DCHECK(A.st, o + q >= outK && o + q + 1 < outK + A.n, (o + q) - outK)) continue;
+                if (!SF_BULK)
+                    __stcs(reinterpret_cast<longlong2 *>(o + q), reinterpret_cast<const longlong2 *>(sb)[(q - x) >> 1]);
+                if (PAY) {
+                    const longlong2 v2 = reinterpret_cast<const longlong2 *>(sb)[(SROW + q - x) >> 1];
+                    if (vecP) {
+                        __stcs(reinterpret_cast<longlong2 *>(o + q + dP), v2);
+                    } else {
+                        __stcs(o + q + dP, v2.x);
+                        __stcs(o + q + 1 + dP, v2.y);
+                    }
                 }
             }
         }
@@ -769,6 +804,7 @@ __global__ void __launch_bounds__(T, MINB) k_part_scatter_sf(PartArgs A)
         // rows fill the key sector the digit's output run starts in); the
         // owner warp keeps the key address of q = 0
         int rr[NCL];
+        if (BITS <= 5 && lane < L::FMAX / NWARP) tma_store_wait_read<0>();   // the previous item's bulk stores have read their rows
         __syncthreads();                              // the previous item's pending rows are written
 #pragma unroll
         for (int k = 0; k < NCL; k++) {
@@ -836,6 +872,7 @@ __global__ void __launch_bounds__(T, MINB) k_part_scatter_sf(PartArgs A)
             }
         }
     }
+    if (BITS <= 5 && lane < L::FMAX / NWARP) tma_store_wait_all();   // every bulk store done before the block's memory is released
 }
 
 // Two passes: per first-pass range b and high digit q, the rows and the

@@ -84,3 +84,28 @@ __device__ __forceinline__ void fence_proxy_async_smem()
 {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
+
+// One bulk copy shared -> global in the calling thread's current bulk group.
+// Addresses and size must be multiples of 16 bytes; the shared source must be
+// made visible to the async proxy first (fence_proxy_async_smem by every
+// thread that wrote it, then a barrier).
+__device__ __forceinline__ void tma_store_1d(void *dst, const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Close the calling thread's current bulk group (an empty group is allowed).
+__device__ __forceinline__ void tma_store_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+// Wait until at most N of the calling thread's bulk groups still read their
+// shared source (their sources before that may be overwritten).
+template <int N>
+__device__ __forceinline__ void tma_store_wait_read()
+{
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+
+// Wait until all of the calling thread's bulk groups have completed.
+__device__ __forceinline__ void tma_store_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
