@@ -15,6 +15,8 @@ order, either as separate operator calls or as one fused call each.
 from __future__ import annotations
 
 import collections
+import contextlib
+import gc
 import math
 import time
 from dataclasses import dataclass, field
@@ -340,12 +342,29 @@ def default_shapes(scale: float = 1.0):
             {"n_fact": n, "n_dim": 50_000_000, "n_attr": 1000, "zipf": 1.1}]
 
 
+@contextlib.contextmanager
+def gc_paused():
+    """The cyclic garbage collector frozen and off for a latency-timed loop,
+    so that a full collection of the process's heap (tens of milliseconds
+    with PyTorch loaded) cannot land inside it; per-round objects are still
+    freed by reference counting."""
+    gc.collect()
+    gc.freeze()
+    gc.disable()
+    try:
+        yield
+    finally:
+        gc.enable()
+        gc.unfreeze()
+
+
 def bench_serve(ctx, device, stream, peak_gbs: float, duration_s: float = 10.0, rate: float = 2000.0,
                 scale: float = 1.0, serial_s: float = 1.0, log=print, seed: int = 5,
                 sat_rates=(1000.0, 2000.0, 4000.0, 8000.0), sat_seconds: float = 1.0) -> dict:
     """Served form on a Poisson trace against serial per-request replays, then
     a saturation sweep over rising arrival rates (each a trace of
-    sat_seconds) against serial fused replay."""
+    sat_seconds) against serial fused replay.  Every timed loop, served or
+    serial, runs with the garbage collector paused (gc_paused)."""
     torch.cuda.empty_cache()
     tables = ResidentTables(ctx, default_shapes(scale), device, log=log)
     resident = tables.bytes()
@@ -359,26 +378,30 @@ def bench_serve(ctx, device, stream, peak_gbs: float, duration_s: float = 10.0, 
     warm = serve_loop(trace[:8], ex, Admission(slots * REQ_BYTES, slots), row_cap=ROW_CAP)
     torch.cuda.synchronize()
     log(f"serve: {len(trace)} requests over {duration_s}s, resident {resident / 1e9:.1f} GB")
-    st = serve_loop(trace, ex, adm, row_cap=ROW_CAP)
+    with gc_paused():
+        st = serve_loop(trace, ex, adm, row_cap=ROW_CAP)
     ctx.sync_status()
     served = st.summary()
     del warm
     # serial replays on the first serial_s seconds of the same trace
     prefix = [a for a in trace if a.t < serial_s]
-    st_pre = serve_loop(prefix, ex, Admission(slots * REQ_BYTES, slots), row_cap=ROW_CAP).summary()
+    with gc_paused():
+        st_pre = serve_loop(prefix, ex, Admission(slots * REQ_BYTES, slots), row_cap=ROW_CAP).summary()
     mx = max(a.n for a in prefix) if prefix else 1
     scratch = {"sel": torch.empty(mx, dtype=torch.int32, device=device),
                "cnt": torch.empty(1, dtype=torch.int64, device=device),
                "rows": torch.empty(mx, dtype=torch.int32, device=device),
                "attr": torch.empty(mx, dtype=torch.int32, device=device),
                "jc": torch.empty(1, dtype=torch.int64, device=device)}
-    per_op = serial_replay(prefix, lambda r: per_operator_request(ctx, tables, r, scratch)).summary()
+    with gc_paused():
+        per_op = serial_replay(prefix, lambda r: per_operator_request(ctx, tables, r, scratch)).summary()
     g1, o1 = qe.alloc_groups(CAPACITY, 4, device)
 
     def fused(r):
         qe.qe_pipeline(ctx, tables.desc(r), CAPACITY, check=False, out=(g1, o1))
         torch.cuda.current_stream().synchronize()
-    fused_serial = serial_replay(prefix, fused).summary()
+    with gc_paused():
+        fused_serial = serial_replay(prefix, fused).summary()
     ctx.sync_status()
     # saturation sweep: the arrival rate rising past what serial fused
     # execution sustains, served (continuous batching) against serial fused
@@ -387,8 +410,10 @@ def bench_serve(ctx, device, stream, peak_gbs: float, duration_s: float = 10.0, 
     for lam in sat_rates:
         tr = datagen.poisson_trace(sat_seconds, lam, tables.rows, seed=seed + int(lam), n_lo=1e4,
                                    n_hi=min(5e8, min(tables.rows)))
-        sv = serve_loop(tr, ex, Admission(slots * REQ_BYTES, slots), row_cap=ROW_CAP).summary()
-        sf = serial_replay(tr, fused).summary()
+        with gc_paused():
+            sv = serve_loop(tr, ex, Admission(slots * REQ_BYTES, slots), row_cap=ROW_CAP).summary()
+        with gc_paused():
+            sf = serial_replay(tr, fused).summary()
         ctx.sync_status()
         sweep[str(int(lam))] = {"requests": len(tr), "served": {k: sv[k] for k in ("p50_ms", "p99_ms", "rows_per_s")},
                                 "serial_fused": {k: sf[k] for k in ("p50_ms", "p99_ms", "rows_per_s")}}

@@ -150,3 +150,17 @@ def test_cancel_unknown_or_finished_is_ignored():
     st = serve.serve_loop(trace, ex, adm, clock=clock, idle_sleep=0, cancel_at={2: 5.0})
     assert st.cancelled == 0 and len(st.latencies_ms) == 3
     assert adm.used == 0 and adm.busy == 0
+
+
+def test_gc_paused_restores_the_collector():
+    import gc
+    assert gc.isenabled()
+    with serve.gc_paused():
+        assert not gc.isenabled()
+    assert gc.isenabled() and gc.get_freeze_count() == 0
+    try:
+        with serve.gc_paused():
+            raise RuntimeError("leaves the loop")
+    except RuntimeError:
+        pass
+    assert gc.isenabled() and gc.get_freeze_count() == 0
