@@ -19,7 +19,8 @@
 //                        64 digits: F <= 64 in one pass, F = 512 .. 4096 in
 //                        two passes) and k_part_scatter_wc (the same inputs,
 //                        F = 128 or 256 in one pass): register-prefetched
-//                        chunks, one-pass ranking with per-warp counters, and
+//                        chunks (in the former, the chunk after them fetched
+//                        into L2), one-pass ranking with per-warp counters, and
 //                        write-combining of 32-byte sectors (see below);
 //                      k_part_scatter (qe_part_general.cuh; any payloads, any
 //                        fan-out): bulk-copy (TMA) double-buffered chunks and
@@ -282,6 +283,29 @@ __device__ __forceinline__ void wc_block_scan(const uint32_t *a, uint32_t *out, 
     }
 }
 
+// Rows [r0, min(r0 + CH, hi)) of the keys and of the int64 payloads fetched
+// into L2 (a hint: every address lies inside those rows).  Half the threads
+// take the keys' 128-byte lines, half the payloads'.  The small fan-out
+// scatter fetches the chunk after the one it is about to load, so that load
+// hits L2.  At 600M pairs with two blocks per SM and the next chunk already
+// loaded into registers, fetching the one after it took fan-out 1024 from
+// 8.74 to 8.13 ms and fan-out 32 from 4.71 to 4.31 ms (three chunks ahead:
+// 8.29 / 4.46 ms); up to 32 digits, three blocks that load each chunk at its
+// start from L2 are faster still (the block shapes below).  The one-pass
+// kernel for 128 / 256 digits measured slower with the fetch (7.35 -> 7.53 /
+// 7.87 -> 8.01 ms) and does without.
+template <bool PAY, int T, int CH>
+__device__ __forceinline__ void part_prefetch_l2(const PartArgs &A, int64_t r0, int64_t hi)
+{
+    if (r0 >= hi) return;
+    const int64_t nbytes = ((r0 + CH < hi ? r0 + CH : hi) - r0) * 8;
+    constexpr int H = PAY ? T / 2 : T;
+    const int t = static_cast<int>(threadIdx.x);
+    const char *col = (t < H ? reinterpret_cast<const char *>(A.keys) : static_cast<const char *>(A.pay[0])) + r0 * 8;
+    for (int64_t o = static_cast<int64_t>(t < H ? t : t - H) * 128; o < nbytes; o += H * 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(col + o));
+}
+
 template <bool PAY, int BITS, int T, int IT, int MINB>
 __global__ void __launch_bounds__(T, MINB) k_part_scatter_wc(PartArgs A)
 {
@@ -455,7 +479,8 @@ __global__ void __launch_bounds__(T, MINB) k_part_scatter_wc(PartArgs A)
 // offsets and write-combining rule as k_part_scatter_wc, with the work per
 // row cut down:
 //   * a chunk whose rows all lie inside the item is loaded and ranked
-//     without per-row bounds tests (FULL);
+//     without per-row bounds tests (FULL); the next chunk is loaded into
+//     registers meanwhile and the one after it fetched into L2;
 //   * digit state lives in registers: lane d of every warp keeps the q of
 //     digit d's next row (r, the same in every warp), so the digits' sorted
 //     starts and the write-out need no shared-memory tables;
@@ -469,7 +494,8 @@ __global__ void __launch_bounds__(T, MINB) k_part_scatter_wc(PartArgs A)
 // (rows completing the digit's pending sector, rows before the item's first
 // sector boundary, and rows of the last incomplete sector, which stay in
 // shared memory until a later chunk or the end of the item completes them),
-// then the whole sectors digit by digit, two rows per lane.
+// then the whole sectors: with up to 32 digits one bulk store of keys and
+// one of payloads per digit, else two rows per lane.
 template <bool PAY, int BITS, int T, int IT>
 struct SfLayout {
     static constexpr int NWARP = T / 32, CH = T * IT, NCL = BITS > 5 ? 2 : 1, FMAX = 32 * NCL;
@@ -804,7 +830,8 @@ __global__ void __launch_bounds__(T, MINB) k_part_scatter_sf(PartArgs A)
         // rows fill the key sector the digit's output run starts in); the
         // owner warp keeps the key address of q = 0
         int rr[NCL];
-        if (BITS <= 5 && lane < L::FMAX / NWARP) tma_store_wait_read<0>();   // the previous item's bulk stores have read their rows
+        // the previous item's bulk stores have read their rows
+        if (BITS <= 5 && lane < L::FMAX / NWARP) tma_store_wait_read<0>();
         __syncthreads();                              // the previous item's pending rows are written
 #pragma unroll
         for (int k = 0; k < NCL; k++) {
@@ -826,33 +853,54 @@ __global__ void __launch_bounds__(T, MINB) k_part_scatter_sf(PartArgs A)
             }
         }
         const int64_t nch = (hi - lo + CH - 1) / CH;
-        longlong2 kv[IT], nkv[IT];
-        if (hi - lo >= CH) sf_load_full<PAY, IT>(A, lo, kv);
-        else wc_load<PAY, IT>(A, lo, hi, kv);
-        // chunks in pairs, so that the prefetched rows alternate between kv
-        // and nkv without register copies
-        for (int64_t c = 0; c < nch; c += 2) {
-            {
+        if constexpr (MINB >= 3) {
+            // three blocks per SM: each chunk loaded at its start, from L2,
+            // where the previous chunk's step fetched it
+            longlong2 kv[IT];
+            for (int64_t c = 0; c < nch; c++) {
                 const int64_t r0 = lo + c * CH;
-                const int64_t nx = r0 + CH;
-                if (nx + CH <= hi) sf_load_full<PAY, IT>(A, nx, nkv);
-                else if (nx < hi) wc_load<PAY, IT>(A, nx, hi, nkv);
-                if (r0 + CH <= hi)
-                    sf_chunk<PAY, BITS, T, IT, true>(A, smem, 0, kv, 0, CH, F, rr, outK, dP, vecP);
-                else
-                    sf_chunk<PAY, BITS, T, IT, false>(A, smem, 0, kv, 0, static_cast<int>(hi - r0), F, rr, outK, dP,
+                const int buf = static_cast<int>(c & 1);
+                part_prefetch_l2<PAY, T, CH>(A, r0 + CH, hi);
+                if (r0 + CH <= hi) {
+                    sf_load_full<PAY, IT>(A, r0, kv);
+                    sf_chunk<PAY, BITS, T, IT, true>(A, smem, buf, kv, 0, CH, F, rr, outK, dP, vecP);
+                } else {
+                    wc_load<PAY, IT>(A, r0, hi, kv);
+                    sf_chunk<PAY, BITS, T, IT, false>(A, smem, buf, kv, 0, static_cast<int>(hi - r0), F, rr, outK, dP,
                                                       vecP);
+                }
             }
-            if (c + 1 < nch) {
-                const int64_t r0 = lo + (c + 1) * CH;
-                const int64_t nx = r0 + CH;
-                if (nx + CH <= hi) sf_load_full<PAY, IT>(A, nx, kv);
-                else if (nx < hi) wc_load<PAY, IT>(A, nx, hi, kv);
-                if (r0 + CH <= hi)
-                    sf_chunk<PAY, BITS, T, IT, true>(A, smem, 1, nkv, 0, CH, F, rr, outK, dP, vecP);
-                else
-                    sf_chunk<PAY, BITS, T, IT, false>(A, smem, 1, nkv, 0, static_cast<int>(hi - r0), F, rr, outK, dP,
-                                                      vecP);
+        } else {
+            longlong2 kv[IT], nkv[IT];
+            if (hi - lo >= CH) sf_load_full<PAY, IT>(A, lo, kv);
+            else wc_load<PAY, IT>(A, lo, hi, kv);
+            // chunks in pairs, so that the prefetched rows alternate between kv
+            // and nkv without register copies
+            for (int64_t c = 0; c < nch; c += 2) {
+                {
+                    const int64_t r0 = lo + c * CH;
+                    const int64_t nx = r0 + CH;
+                    if (nx + CH <= hi) sf_load_full<PAY, IT>(A, nx, nkv);
+                    else if (nx < hi) wc_load<PAY, IT>(A, nx, hi, nkv);
+                    part_prefetch_l2<PAY, T, CH>(A, nx + CH, hi);
+                    if (r0 + CH <= hi)
+                        sf_chunk<PAY, BITS, T, IT, true>(A, smem, 0, kv, 0, CH, F, rr, outK, dP, vecP);
+                    else
+                        sf_chunk<PAY, BITS, T, IT, false>(A, smem, 0, kv, 0, static_cast<int>(hi - r0), F, rr, outK, dP,
+                                                          vecP);
+                }
+                if (c + 1 < nch) {
+                    const int64_t r0 = lo + (c + 1) * CH;
+                    const int64_t nx = r0 + CH;
+                    if (nx + CH <= hi) sf_load_full<PAY, IT>(A, nx, kv);
+                    else if (nx < hi) wc_load<PAY, IT>(A, nx, hi, kv);
+                    part_prefetch_l2<PAY, T, CH>(A, nx + CH, hi);
+                    if (r0 + CH <= hi)
+                        sf_chunk<PAY, BITS, T, IT, true>(A, smem, 1, nkv, 0, CH, F, rr, outK, dP, vecP);
+                    else
+                        sf_chunk<PAY, BITS, T, IT, false>(A, smem, 1, nkv, 0, static_cast<int>(hi - r0), F, rr, outK,
+                                                          dP, vecP);
+                }
             }
         }
         __syncwarp();
@@ -872,7 +920,8 @@ __global__ void __launch_bounds__(T, MINB) k_part_scatter_sf(PartArgs A)
             }
         }
     }
-    if (BITS <= 5 && lane < L::FMAX / NWARP) tma_store_wait_all();   // every bulk store done before the block's memory is released
+    // every bulk store done before the block's memory is released
+    if (BITS <= 5 && lane < L::FMAX / NWARP) tma_store_wait_all();
 }
 
 // Two passes: per first-pass range b and high digit q, the rows and the
@@ -898,12 +947,15 @@ __global__ void k_part_two_pass_tables(const uint32_t *hist, const int64_t *off,
 }
 
 // Block shapes of the write-combining scatters, by digits per launch
-// (measured on GB300).  Up to 32 digits, two blocks of 256 threads x 8 rows
-// per SM: at 600M pairs and fan-out 1024 it beat one block of 512 x 8 (9.3 ms
-// against 9.9 ms for the two passes), 512 x 4 and 1024 x 4 at 32 warps per
-// SM (10.0 / 10.9 ms; 64 registers with spills), 256 x 6 (10.1 ms), and three
-// blocks of 256 x 8 per SM with no register prefetch (80 registers; 9.7 ms,
-// 9.8 ms with two such blocks).  From
+// (measured on GB300).  Up to 32 digits, three blocks of 256 threads x 8
+// rows per SM (79 registers), each chunk loaded at its start after the
+// previous step fetched it into L2: at 600M pairs, fan-out 1024 in 8.00 ms
+// against 8.14 ms for two blocks that also load the next chunk into
+// registers, and 8.45 ms for two blocks without that.  Before the L2
+// fetches, two blocks with the register prefetch (9.3 ms) beat one block of
+// 512 x 8 (9.9 ms), 512 x 4 and 1024 x 4 at 32 warps per SM (10.0 / 10.9 ms;
+// 64 registers with spills), 256 x 6 (10.1 ms), and three blocks without the
+// register prefetch (9.7 ms).  From
 // 64 digits a chunk of 256 x 8 rows gives each digit runs too short for the
 // per-digit work, so one block of 512 runs per SM; and every block writes
 // one output page per destination and column at a time, so beyond a few
@@ -920,7 +972,7 @@ static WcShape wc_shape(int log2f)
 {
     const int F = 1 << log2f;
     if (log2f <= 5)
-        return {256, 8, reinterpret_cast<const void *>(k_part_scatter_sf<PAY, 5, 256, 8, 2>),
+        return {256, 8, reinterpret_cast<const void *>(k_part_scatter_sf<PAY, 5, 256, 8, 3>),
                 SfLayout<PAY, 5, 256, 8>::total};
     if (log2f <= 6)
         return {512, 8, reinterpret_cast<const void *>(k_part_scatter_sf<PAY, 6, 512, 8, 1>),
