@@ -18,10 +18,11 @@
 //                      k_part_scatter_sf (one int64 payload or none, at most
 //                        64 digits: F <= 64 in one pass, F = 512 .. 4096 in
 //                        two passes) and k_part_scatter_wc (the same inputs,
-//                        F = 128 or 256 in one pass): register-prefetched
-//                        chunks (in the former, the chunk after them fetched
-//                        into L2), one-pass ranking with per-warp counters, and
-//                        write-combining of 32-byte sectors (see below);
+//                        F = 128 or 256 in one pass): each chunk's successor
+//                        loaded into registers while the chunk is processed
+//                        (in the former, after an L2 fetch), one-pass ranking
+//                        with per-warp counters, and write-combining of
+//                        32-byte sectors (see below);
 //                      k_part_scatter (qe_part_general.cuh; any payloads, any
 //                        fan-out): bulk-copy (TMA) double-buffered chunks and
 //                        a one- or two-digit LSD ranking.
@@ -286,14 +287,16 @@ __device__ __forceinline__ void wc_block_scan(const uint32_t *a, uint32_t *out, 
 // Rows [r0, min(r0 + CH, hi)) of the keys and of the int64 payloads fetched
 // into L2 (a hint: every address lies inside those rows).  Half the threads
 // take the keys' 128-byte lines, half the payloads'.  The small fan-out
-// scatter fetches the chunk after the one it is about to load, so that load
-// hits L2.  At 600M pairs with two blocks per SM and the next chunk already
-// loaded into registers, fetching the one after it took fan-out 1024 from
-// 8.74 to 8.13 ms and fan-out 32 from 4.71 to 4.31 ms (three chunks ahead:
-// 8.29 / 4.46 ms); up to 32 digits, three blocks that load each chunk at its
-// start from L2 are faster still (the block shapes below).  The one-pass
-// kernel for 128 / 256 digits measured slower with the fetch (7.35 -> 7.53 /
-// 7.87 -> 8.01 ms) and does without.
+// scatter fetches the next chunk at the start of every step and loads it
+// into registers halfway through, so that load hits L2.  Measured at 600M
+// pairs, fan-out 1024 (whole call, 256 x 8 rows a chunk): 8.74 ms with two
+// blocks per SM loading the next chunk into a second register set and no
+// fetch; 8.13 ms with the fetch of the chunk after that (8.29 ms three chunks
+// ahead); 7.99 ms with three blocks per SM, one register set, each chunk
+// loaded at its step's start after a fetch one step ahead; 7.69 ms with the
+// load moved halfway (kept); 9.18 ms for the same without the fetch.  The one-pass kernel for
+// 128 / 256 digits measured slower with the fetch (7.35 -> 7.53 / 7.87 ->
+// 8.01 ms) and does without.
 template <bool PAY, int T, int CH>
 __device__ __forceinline__ void part_prefetch_l2(const PartArgs &A, int64_t r0, int64_t hi)
 {
@@ -479,8 +482,9 @@ __global__ void __launch_bounds__(T, MINB) k_part_scatter_wc(PartArgs A)
 // offsets and write-combining rule as k_part_scatter_wc, with the work per
 // row cut down:
 //   * a chunk whose rows all lie inside the item is loaded and ranked
-//     without per-row bounds tests (FULL); the next chunk is loaded into
-//     registers meanwhile and the one after it fetched into L2;
+//     without per-row bounds tests (FULL); a step fetches the next chunk
+//     into L2 first and loads it into the one register set as soon as its
+//     own rows are in shared memory, so the loads overlap the write-out;
 //   * digit state lives in registers: lane d of every warp keeps the q of
 //     digit d's next row (r, the same in every warp), so the digits' sorted
 //     starts and the write-out need no shared-memory tables;
@@ -605,11 +609,13 @@ __device__ __forceinline__ V sf_get(const V (&v)[NCL], int p)
 }
 
 // One chunk: rank, place in sorted buffer `buf`, write out.  rr (q of every
-// lane digit's next row) advances by the chunk's rows.
+// lane digit's next row) advances by the chunk's rows.  kv then takes the
+// rows of the next chunk, at nx (up to hi), as soon as its own rows are in
+// shared memory, so those loads overlap the write-out.
 template <bool PAY, int BITS, int T, int IT, bool FULL>
-__device__ __forceinline__ void sf_chunk(const PartArgs &A, unsigned char *smem, int buf, const longlong2 (&kv)[IT],
+__device__ __forceinline__ void sf_chunk(const PartArgs &A, unsigned char *smem, int buf, longlong2 (&kv)[IT],
                                          int vlo, int vhi, int F, int (&rr)[SfLayout<PAY, BITS, T, IT>::NCL],
-                                         long long *outK, int64_t dP, bool vecP)
+                                         long long *outK, int64_t dP, bool vecP, int64_t nx, int64_t hi)
 {
     using L = SfLayout<PAY, BITS, T, IT>;
     constexpr int NWARP = L::NWARP, NCL = L::NCL, FMAX = L::FMAX, SROW = L::SROW;
@@ -682,6 +688,8 @@ __device__ __forceinline__ void sf_chunk(const PartArgs &A, unsigned char *smem,
             if (FULL || dg[i] != 0xffffffffu) sf_put<PAY, SROW>(sb, static_cast<int>(pos + rk[i]), kv[i]);
         }
     }
+    if (nx + T * IT <= hi) sf_load_full<PAY, IT>(A, nx, kv);
+    else if (nx < hi) wc_load<PAY, IT>(A, nx, hi, kv);
     if (SF_BULK) fence_proxy_async_smem();   // the sorted rows, visible to the bulk stores below
     __syncthreads();
     // the rows of every owned digit's partial sectors: lanes LPD j .. LPD j + 6
@@ -853,55 +861,20 @@ __global__ void __launch_bounds__(T, MINB) k_part_scatter_sf(PartArgs A)
             }
         }
         const int64_t nch = (hi - lo + CH - 1) / CH;
-        if constexpr (MINB >= 3) {
-            // three blocks per SM: each chunk loaded at its start, from L2,
-            // where the previous chunk's step fetched it
-            longlong2 kv[IT];
-            for (int64_t c = 0; c < nch; c++) {
-                const int64_t r0 = lo + c * CH;
-                const int buf = static_cast<int>(c & 1);
-                part_prefetch_l2<PAY, T, CH>(A, r0 + CH, hi);
-                if (r0 + CH <= hi) {
-                    sf_load_full<PAY, IT>(A, r0, kv);
-                    sf_chunk<PAY, BITS, T, IT, true>(A, smem, buf, kv, 0, CH, F, rr, outK, dP, vecP);
-                } else {
-                    wc_load<PAY, IT>(A, r0, hi, kv);
-                    sf_chunk<PAY, BITS, T, IT, false>(A, smem, buf, kv, 0, static_cast<int>(hi - r0), F, rr, outK, dP,
-                                                      vecP);
-                }
-            }
-        } else {
-            longlong2 kv[IT], nkv[IT];
-            if (hi - lo >= CH) sf_load_full<PAY, IT>(A, lo, kv);
-            else wc_load<PAY, IT>(A, lo, hi, kv);
-            // chunks in pairs, so that the prefetched rows alternate between kv
-            // and nkv without register copies
-            for (int64_t c = 0; c < nch; c += 2) {
-                {
-                    const int64_t r0 = lo + c * CH;
-                    const int64_t nx = r0 + CH;
-                    if (nx + CH <= hi) sf_load_full<PAY, IT>(A, nx, nkv);
-                    else if (nx < hi) wc_load<PAY, IT>(A, nx, hi, nkv);
-                    part_prefetch_l2<PAY, T, CH>(A, nx + CH, hi);
-                    if (r0 + CH <= hi)
-                        sf_chunk<PAY, BITS, T, IT, true>(A, smem, 0, kv, 0, CH, F, rr, outK, dP, vecP);
-                    else
-                        sf_chunk<PAY, BITS, T, IT, false>(A, smem, 0, kv, 0, static_cast<int>(hi - r0), F, rr, outK, dP,
-                                                          vecP);
-                }
-                if (c + 1 < nch) {
-                    const int64_t r0 = lo + (c + 1) * CH;
-                    const int64_t nx = r0 + CH;
-                    if (nx + CH <= hi) sf_load_full<PAY, IT>(A, nx, kv);
-                    else if (nx < hi) wc_load<PAY, IT>(A, nx, hi, kv);
-                    part_prefetch_l2<PAY, T, CH>(A, nx + CH, hi);
-                    if (r0 + CH <= hi)
-                        sf_chunk<PAY, BITS, T, IT, true>(A, smem, 1, nkv, 0, CH, F, rr, outK, dP, vecP);
-                    else
-                        sf_chunk<PAY, BITS, T, IT, false>(A, smem, 1, nkv, 0, static_cast<int>(hi - r0), F, rr, outK,
-                                                          dP, vecP);
-                }
-            }
+        // one register set: every step fetches the next chunk into L2 first
+        // and loads it into kv once this chunk's rows are in shared memory
+        longlong2 kv[IT];
+        if (hi - lo >= CH) sf_load_full<PAY, IT>(A, lo, kv);
+        else wc_load<PAY, IT>(A, lo, hi, kv);
+        for (int64_t c = 0; c < nch; c++) {
+            const int64_t r0 = lo + c * CH;
+            const int buf = static_cast<int>(c & 1);
+            part_prefetch_l2<PAY, T, CH>(A, r0 + CH, hi);
+            if (r0 + CH <= hi)
+                sf_chunk<PAY, BITS, T, IT, true>(A, smem, buf, kv, 0, CH, F, rr, outK, dP, vecP, r0 + CH, hi);
+            else
+                sf_chunk<PAY, BITS, T, IT, false>(A, smem, buf, kv, 0, static_cast<int>(hi - r0), F, rr, outK, dP, vecP,
+                                                  r0 + CH, hi);
         }
         __syncwarp();
         // rows still pending at the end of the item (owner lanes)
@@ -947,17 +920,19 @@ __global__ void k_part_two_pass_tables(const uint32_t *hist, const int64_t *off,
 }
 
 // Block shapes of the write-combining scatters, by digits per launch
-// (measured on GB300).  Up to 32 digits, three blocks of 256 threads x 8
-// rows per SM (79 registers), each chunk loaded at its start after the
-// previous step fetched it into L2: at 600M pairs, fan-out 1024 in 8.00 ms
-// against 8.14 ms for two blocks that also load the next chunk into
-// registers, and 8.45 ms for two blocks without that.  Before the L2
-// fetches, two blocks with the register prefetch (9.3 ms) beat one block of
-// 512 x 8 (9.9 ms), 512 x 4 and 1024 x 4 at 32 warps per SM (10.0 / 10.9 ms;
-// 64 registers with spills), 256 x 6 (10.1 ms), and three blocks without the
-// register prefetch (9.7 ms).  From
-// 64 digits a chunk of 256 x 8 rows gives each digit runs too short for the
-// per-digit work, so one block of 512 runs per SM; and every block writes
+// (measured on GB300).  Up to 32 digits, two blocks of 256 threads x 11 rows
+// per SM (125 registers, one register set).  At 600M pairs, fan-out 1024,
+// whole call: 9, 10, 11 and 12 rows per thread with two blocks per SM took
+// 7.41, 7.27, 7.11 and 7.56 ms; 8 rows with three blocks 7.68 ms, 6 rows with
+// four 7.86 ms.  Before the L2 fetches, two blocks of 256 x 8 with a second
+// register set for the next chunk (9.3 ms) beat one block of 512 x 8
+// (9.9 ms), 512 x 4 and 1024 x 4 at 32 warps per SM (10.0 / 10.9 ms; 64
+// registers with spills), 256 x 6 (10.1 ms), and three blocks of 256 x 8
+// without the second set (9.7 ms).  From 64 digits a chunk of 256 threads
+// gives each digit runs too short for the per-digit work, so one block of
+// 512 x 8 runs per SM (its one register set measured faster than two:
+// fan-out 4096 in 10.46 against 11.02 ms, fan-out 64 in 5.57 against
+// 5.82 ms; 10 and 12 rows per thread 10.55 / 11.21 ms); and every block writes
 // one output page per destination and column at a time, so beyond a few
 // hundred pages per SM (two blocks at 256 digits) the address translation
 // caches miss.
@@ -972,8 +947,8 @@ static WcShape wc_shape(int log2f)
 {
     const int F = 1 << log2f;
     if (log2f <= 5)
-        return {256, 8, reinterpret_cast<const void *>(k_part_scatter_sf<PAY, 5, 256, 8, 3>),
-                SfLayout<PAY, 5, 256, 8>::total};
+        return {256, 11, reinterpret_cast<const void *>(k_part_scatter_sf<PAY, 5, 256, 11, 2>),
+                SfLayout<PAY, 5, 256, 11>::total};
     if (log2f <= 6)
         return {512, 8, reinterpret_cast<const void *>(k_part_scatter_sf<PAY, 6, 512, 8, 1>),
                 SfLayout<PAY, 6, 512, 8>::total};
@@ -1072,7 +1047,7 @@ extern "C" qe_status qe_partition(qe_ctx *ctx, const int64_t *keys, const qe_col
     int64_t G = static_cast<int64_t>(ctx->num_sms) * per_sm;
     int64_t need = qe_ceil_div(nrows, chunk);
     if (G > need) G = need;
-    // whole chunks per block, so every chunk but the last starts 16 KB-aligned
+    // whole chunks per block
     A.rows_per_block = qe_ceil_div(qe_ceil_div(nrows, G), chunk) * chunk;
     G = qe_ceil_div(nrows, A.rows_per_block);
     A.tma = !wc && qe_aligned(keys, 16) && (!fast || qe_aligned(A.pay[0], 16));
