@@ -14,15 +14,14 @@
 //                      chunk stably by destination in shared memory and writes
 //                      the rows in destination order, keeping a running output
 //                      offset per destination so rows keep their input order.
-//                      Three kernels:
+//                      Two kernels:
 //                      k_part_scatter_sf (one int64 payload or none, at most
-//                        64 digits: F <= 64 in one pass, F = 512 .. 4096 in
-//                        two passes) and k_part_scatter_wc (the same inputs,
-//                        F = 128 or 256 in one pass): each chunk's successor
-//                        loaded into registers while the chunk is processed
-//                        (in the former, after an L2 fetch), one-pass ranking
-//                        with per-warp counters, and write-combining of
-//                        32-byte sectors (see below);
+//                        64 digits a launch: F <= 64 in one pass, F = 128 ..
+//                        4096 in two passes): each chunk's successor fetched
+//                        into L2 and loaded into registers while the chunk is
+//                        processed, one-pass ranking with ballots and
+//                        per-warp counts, and write-combining of 32-byte
+//                        sectors (see below);
 //                      k_part_scatter (qe_part_general.cuh; any payloads, any
 //                        fan-out): bulk-copy (TMA) double-buffered chunks and
 //                        a one- or two-digit LSD ranking.
@@ -161,16 +160,13 @@ __global__ void __launch_bounds__(1024) k_part_basescan(const int64_t *tot, int6
 }
 
 // ---------------------------------------------------------------------------
-// Write-combining scatter: int64 keys with no payload or one int64 payload,
-// 128 or 256 digits in one pass (k_part_scatter_sf below takes up to 64
-// digits, with the same chunk walk and sector rule).  A block walks its rows in chunks of T * IT;
-// the next chunk is loaded into registers while the current one is ranked.
+// Write-combining scatter (k_part_scatter_sf below): int64 keys with no
+// payload or one int64 payload.  A block walks its rows in chunks of T * IT.
 //
-// Ranking is one pass: each warp counts destinations in its own row of the
-// counter matrix cnt[warp][p] (equal destinations within a warp found with
-// bit-wise ballots, in lane order), the matrix is scanned over warps per
-// destination and then over destinations, and every row moves to its stable
-// sorted position in shared memory.
+// Ranking is one pass: each warp counts destinations (equal destinations
+// within a warp found with bit-wise ballots, in lane order), the counts are
+// scanned over warps per destination and then over destinations, and every
+// row moves to its stable sorted position in shared memory.
 //
 // A DRAM sector is 32 bytes (four 8-byte rows).  With F destinations a chunk
 // adds only CHUNK/F rows to each, so writing every chunk's rows at once would
@@ -181,33 +177,11 @@ __global__ void __launch_bounds__(1024) k_part_basescan(const int64_t *tot, int6
 // written, except the first and last sector of the block's range, which it
 // shares with the neighbouring blocks.
 // Fan-outs up to 2^WC_MAX_LOG2F take one pass; above, two passes of at most
-// 64 digits (600M pairs at fan-out 512: 11.5 ms in one pass of
-// k_part_scatter_wc, against the two passes of 32 and 16 digits; at 256 the
-// one pass and two passes of 16 measured about equal).
-constexpr int WC_MAX_LOG2F = 8;
-
-// Shared-memory layout of a block of T threads (chunks of T * IT rows).
-struct WcLayout {
-    size_t sK, sP, pK, pP, ob, qt, rq, hist, start, cnt, sD, total;
-    int FC;                                       // counter row width (even)
-    __host__ __device__ WcLayout(int F, bool pay, int T, int IT)
-    {
-        const size_t f = static_cast<size_t>(F), ch = static_cast<size_t>(T) * IT;
-        FC = F < 2 ? 2 : F;
-        sK = 0;
-        sP = sK + ch * 8;
-        pK = sP + (pay ? ch * 8 : 0);
-        pP = pK + 24 * f;
-        ob = pP + (pay ? 24 * f : 0);
-        qt = ob + 8 * f;
-        rq = qt + 8 * f;
-        hist = rq + 4 * f;
-        start = hist + 4 * f;
-        cnt = (start + 4 * f + 15) & ~size_t(15);
-        sD = cnt + 2 * static_cast<size_t>(T / 32) * FC;
-        total = sD + 2 * ch;
-    }
-};
+// 64 digits.  At 600M pairs, fan-out 128 / 256 took 6.89 / 7.00 ms in two
+// passes against 7.35 / 7.87 ms in one pass of a 512-thread kernel for up to
+// 256 digits (since removed); fan-out 64 takes 5.57 ms in one pass against
+// 6.78 ms in two.
+constexpr int WC_MAX_LOG2F = 6;
 
 // Rows r0 + (warp-striped positions) into registers, key in .x and payload
 // in .y, so that a row moves to shared memory as one 16-byte element.
@@ -223,67 +197,6 @@ __device__ __forceinline__ void wc_load(const PartArgs &A, int64_t r0, int64_t h
     }
 }
 
-// Lanes holding the same BITS-bit label d, among the lanes in `valid`.
-template <int BITS>
-__device__ __forceinline__ unsigned match_label(uint32_t d, unsigned valid)
-{
-#ifdef QE_WC_MATCH_ANY
-    return __match_any_sync(QE_FULL_MASK, d) & valid;
-#endif
-    unsigned peers = valid;
-#pragma unroll
-    for (int bit = 0; bit < BITS; bit++) {
-        const bool on = (d >> bit) & 1u;
-        const unsigned set = __ballot_sync(QE_FULL_MASK, on);
-        peers &= on ? set : ~set;
-    }
-    return peers;
-}
-
-// Exclusive scan of a[0..N) into out[0..N) by a block of T threads.
-template <int T>
-__device__ __forceinline__ void wc_block_scan(const uint32_t *a, uint32_t *out, int N, int *s_w)
-{
-    constexpr int NWARP = T / 32;
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int per = (N + T - 1) / T;
-    uint32_t local = 0;
-    for (int j = 0; j < per; j++) {
-        const int i = t * per + j;
-        if (i < N) local += a[i];
-    }
-    const uint32_t inc = warp_incl_scan(local);
-    if (N <= 32 * per) {                          // one warp holds everything
-        if (warp == 0) {
-            uint32_t run = inc - local;
-            for (int j = 0; j < per; j++) {
-                const int i = t * per + j;
-                if (i < N) {
-                    out[i] = run;
-                    run += a[i];
-                }
-            }
-        }
-        return;
-    }
-    if (lane == 31) s_w[warp] = static_cast<int>(inc);
-    __syncthreads();
-    if (warp == 0) {
-        const int w = lane < NWARP ? s_w[lane] : 0;
-        const int wi = warp_incl_scan(w);
-        if (lane < NWARP) s_w[lane] = wi - w;
-    }
-    __syncthreads();
-    uint32_t run = static_cast<uint32_t>(s_w[warp]) + inc - local;
-    for (int j = 0; j < per; j++) {
-        const int i = t * per + j;
-        if (i < N) {
-            out[i] = run;
-            run += a[i];
-        }
-    }
-}
-
 // Rows [r0, min(r0 + CH, hi)) of the keys and of the int64 payloads fetched
 // into L2 (a hint: every address lies inside those rows).  Half the threads
 // take the keys' 128-byte lines, half the payloads'.  The small fan-out
@@ -294,9 +207,7 @@ __device__ __forceinline__ void wc_block_scan(const uint32_t *a, uint32_t *out, 
 // fetch; 8.13 ms with the fetch of the chunk after that (8.29 ms three chunks
 // ahead); 7.99 ms with three blocks per SM, one register set, each chunk
 // loaded at its step's start after a fetch one step ahead; 7.69 ms with the
-// load moved halfway (kept); 9.18 ms for the same without the fetch.  The one-pass kernel for
-// 128 / 256 digits measured slower with the fetch (7.35 -> 7.53 / 7.87 ->
-// 8.01 ms) and does without.
+// load moved halfway (kept); 9.18 ms for the same without the fetch.
 template <bool PAY, int T, int CH>
 __device__ __forceinline__ void part_prefetch_l2(const PartArgs &A, int64_t r0, int64_t hi)
 {
@@ -309,178 +220,10 @@ __device__ __forceinline__ void part_prefetch_l2(const PartArgs &A, int64_t r0, 
         asm volatile("prefetch.global.L2 [%0];" ::"l"(col + o));
 }
 
-template <bool PAY, int BITS, int T, int IT, int MINB>
-__global__ void __launch_bounds__(T, MINB) k_part_scatter_wc(PartArgs A)
-{
-    constexpr int NWARP = T / 32;
-    constexpr int CH = T * IT;
-    static_assert(CH < 65536, "counters are 16-bit");
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ int s_w[NWARP];
-    const int F = static_cast<int>(A.dmask) + 1;            // digits sorted by this launch
-    const WcLayout L(F, PAY, T, IT);
-    const int FC = L.FC;
-    long long *sK = reinterpret_cast<long long *>(smem + L.sK);     // sorted chunk keys
-    long long *sP = reinterpret_cast<long long *>(smem + L.sP);     // sorted chunk payloads
-    long long *pK = reinterpret_cast<long long *>(smem + L.pK);     // pending keys [F][3]
-    long long *pP = reinterpret_cast<long long *>(smem + L.pP);     // pending payloads [F][3]
-    long long **ob = reinterpret_cast<long long **>(smem + L.ob);   // key output address of q = 0
-    int2 *qt = reinterpret_cast<int2 *>(smem + L.qt);               // {q of sorted row 0, rows t < y written now}
-    int32_t *rq = reinterpret_cast<int32_t *>(smem + L.rq);         // q of the next row
-    uint32_t *hist = reinterpret_cast<uint32_t *>(smem + L.hist);
-    uint32_t *start = reinterpret_cast<uint32_t *>(smem + L.start);
-    uint16_t *cnt = reinterpret_cast<uint16_t *>(smem + L.cnt);     // [NWARP][FC]
-    uint16_t *sD = reinterpret_cast<uint16_t *>(smem + L.sD);       // sorted chunk destinations
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1;
-    const int Ffull = 1 << A.log2f;
-    long long *outK = reinterpret_cast<long long *>(A.out_keys);
-    // payload address = key address + dP elements
-    const int64_t dP = PAY ? static_cast<long long *>(A.out_pay[0]) - outK : 0;
-    // A work item's rows for digit p go to the output rows [g, g + n_p).  A
-    // row is numbered q = (its rank among them) - hl, where hl rows fill the
-    // key sector that g starts in (0 if g starts one); q = 0 then starts a
-    // sector and the sectors are q in [4j, 4j + 4).  Rows with q < 0 share
-    // their sector with the previous item and are written at once.
-    const int aoff = static_cast<int>((reinterpret_cast<uintptr_t>(outK) >> 3) & 3);
-    for (int i = threadIdx.x; i < NWARP * FC / 8; i += T) reinterpret_cast<uint4 *>(cnt)[i] = make_uint4(0, 0, 0, 0);
-
-    // one pass only (WC_SINGLE): item b is input range b
-    for (int64_t item = blockIdx.x; item < A.nitems; item += gridDim.x) {
-        const int b = static_cast<int>(item);
-        const int64_t lo = static_cast<int64_t>(b) * A.rows_per_block;
-        const int64_t hi = min(A.n, lo + A.rows_per_block);
-        const int64_t nch = (hi - lo + CH - 1) / CH;
-        __syncthreads();                              // the previous item's tables are done with
-        for (int p = threadIdx.x; p < F; p += T) {
-            const int64_t g = A.base[p] + A.off[static_cast<int64_t>(b) * Ffull + p];
-            const int hl = static_cast<int>((4 - ((g + aoff) & 3)) & 3);
-            ob[p] = outK + g + hl;
-            rq[p] = -hl;
-        }
-        longlong2 kv[IT];
-        wc_load<PAY, IT>(A, lo, hi, kv);
-        __syncthreads();
-
-        for (int64_t c = 0; c < nch; c++) {
-            const int64_t r0 = lo + c * CH;
-            const int m = static_cast<int>(hi - r0 < CH ? hi - r0 : CH);
-            longlong2 nkv[IT];
-            wc_load<PAY, IT>(A, r0 + CH, hi, nkv);       // rows past hi are not read
-
-            uint32_t dg[IT], rk[IT];
-            {
-                // shared-memory counters per warp
-#pragma unroll
-                for (int i = 0; i < IT; i++) {
-                    const bool valid = warp * 32 * IT + i * 32 + lane < m;
-                    const uint32_t d =
-                        valid ? (dev_part_id(kv[i].x, A.log2f, A.mode, A.shift) >> A.dshift) & A.dmask : 0u;
-                    const unsigned peers = match_label<BITS>(d, __ballot_sync(QE_FULL_MASK, valid));
-                    uint16_t *cp = cnt + warp * FC + d;
-                    uint32_t basec = 0;
-                    if (valid) basec = *cp;
-                    __syncwarp();
-                    if (valid && lane == __ffs(peers) - 1) *cp = static_cast<uint16_t>(basec + __popc(peers));
-                    __syncwarp();
-                    dg[i] = valid ? d : 0xffffffffu;
-                    rk[i] = basec + __popc(peers & lt);
-                }
-                __syncthreads();
-                // per digit pair (two 16-bit counters in a word): prefix over
-                // warps and totals; both halves stay below 2^16
-                {
-                    uint32_t *cw = reinterpret_cast<uint32_t *>(cnt);
-                    const int FW = FC / 2;
-                    for (int j = threadIdx.x; j < FW; j += T) {
-                        uint32_t tot = 0;
-#pragma unroll
-                        for (int w = 0; w < NWARP; w++) {
-                            const uint32_t x = cw[w * FW + j];
-                            cw[w * FW + j] = tot;
-                            tot += x;
-                        }
-                        if (2 * j < F) hist[2 * j] = tot & 0xffffu;
-                        if (2 * j + 1 < F) hist[2 * j + 1] = tot >> 16;
-                    }
-                }
-                __syncthreads();
-                wc_block_scan<T>(hist, start, F, s_w);
-                __syncthreads();
-                for (int p = threadIdx.x; p < F; p += T) {
-                    const int r = rq[p];
-                    const int h = static_cast<int>(hist[p]);
-                    const int e = r + h;
-                    const int r4 = r & ~3, e4 = e & ~3;
-                    const int np = r > 0 ? (r & 3) : 0;
-                    if (np && e4 > r4) {
-                        // this chunk completes the pending sector: write its earlier rows
-                        long long *o = ob[p] + r4;
-                        for (int j = 0; j < np; j++) {
-                            if (!QE_DCHECK(A.st, o + j >= outK && o + j < outK + A.n, (o + j) - outK)) continue;
-                            __stcs(o + j, pK[p * 3 + j]);
-                            if (PAY) __stcs(o + dP + j, pP[p * 3 + j]);
-                        }
-                    }
-                    const int lim = e4 > 0 ? e4 : 0;          // rows with q < lim are written now
-                    const int k = lim - r;                    // of this chunk's h rows, the first k
-                    const int s0 = static_cast<int>(start[p]);
-                    qt[p] = make_int2(r - s0, s0 + (k < 0 ? 0 : (k > h ? h : k)));
-                    rq[p] = e;
-                }
-#pragma unroll
-                for (int i = 0; i < IT; i++) {
-                    if (dg[i] != 0xffffffffu) {
-                        const uint32_t pos = start[dg[i]] + cnt[warp * FC + dg[i]] + rk[i];
-                        sK[pos] = kv[i].x;
-                        if (PAY) sP[pos] = kv[i].y;
-                        sD[pos] = static_cast<uint16_t>(dg[i]);
-                    }
-                }
-                __syncthreads();
-                for (int t = threadIdx.x; t < m; t += T) {
-                    const int p = sD[t];
-                    const int2 x = qt[p];
-                    const int q = x.x + t;
-                    if (t < x.y) {
-                        long long *o = ob[p] + q;
-                        if (!QE_DCHECK(A.st, o >= outK && o < outK + A.n, o - outK)) continue;
-                        __stcs(o, sK[t]);
-                        if (PAY) __stcs(o + dP, sP[t]);
-                    } else {
-                        pK[p * 3 + (q & 3)] = sK[t];
-                        if (PAY) pP[p * 3 + (q & 3)] = sP[t];
-                    }
-                }
-                for (int i = threadIdx.x; i < NWARP * FC / 8; i += T)
-                    reinterpret_cast<uint4 *>(cnt)[i] = make_uint4(0, 0, 0, 0);
-                __syncthreads();
-            }
-#pragma unroll
-            for (int i = 0; i < IT; i++) {
-                kv[i] = nkv[i];
-            }
-        }
-        // rows still pending at the end of the item
-        for (int p = threadIdx.x; p < F; p += T) {
-            const int r = rq[p];
-            const int np = r > 0 ? (r & 3) : 0;
-            long long *o = ob[p] + (r & ~3);
-            for (int j = 0; j < np; j++) {
-                if (!QE_DCHECK(A.st, o + j >= outK && o + j < outK + A.n, (o + j) - outK)) continue;
-                __stcs(o + j, pK[p * 3 + j]);
-                if (PAY) __stcs(o + dP + j, pP[p * 3 + j]);
-            }
-        }
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Small fan-out scatter: at most 64 digits per launch (fan-out <= 64 in one
-// pass, and both passes of fan-out 512 .. 4096).  Same work items, output
-// offsets and write-combining rule as k_part_scatter_wc, with the work per
-// row cut down:
+// pass, and both passes of fan-out 128 .. 4096), with the work per row cut
+// down:
 //   * a chunk whose rows all lie inside the item is loaded and ranked
 //     without per-row bounds tests (FULL); a step fetches the next chunk
 //     into L2 first and loads it into the one register set as soon as its
@@ -934,7 +677,7 @@ __global__ void k_part_two_pass_tables(const uint32_t *hist, const int64_t *off,
 // fan-out 4096 in 10.46 against 11.02 ms, fan-out 64 in 5.57 against
 // 5.82 ms; 10 and 12 rows per thread 10.55 / 11.21 ms); and every block writes
 // one output page per destination and column at a time, so beyond a few
-// hundred pages per SM (two blocks at 256 digits) the address translation
+// hundred pages per SM (measured at 256 digits) the address translation
 // caches miss.
 struct WcShape {
     int threads, items;
@@ -945,16 +688,12 @@ struct WcShape {
 template <bool PAY>
 static WcShape wc_shape(int log2f)
 {
-    const int F = 1 << log2f;
     if (log2f <= 5)
         return {256, 11, reinterpret_cast<const void *>(k_part_scatter_sf<PAY, 5, 256, 11, 2>),
                 SfLayout<PAY, 5, 256, 11>::total};
     if (log2f <= 6)
         return {512, 8, reinterpret_cast<const void *>(k_part_scatter_sf<PAY, 6, 512, 8, 1>),
                 SfLayout<PAY, 6, 512, 8>::total};
-    if (log2f <= 8)
-        return {512, 8, reinterpret_cast<const void *>(k_part_scatter_wc<PAY, 8, 512, 8, 1>),
-                WcLayout(F, PAY, 512, 8).total};
     return {0, 0, nullptr, 0};   // beyond one write-combining pass: not taken
 }
 
