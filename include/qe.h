@@ -264,7 +264,7 @@ typedef enum {
  * log2_fanout in [0, 12]; shift in [0, 63] (radix mode).
  * Scratch, taken from the context's HBM budget for the duration of the call:
  * per-block histograms and offsets (about 12 bytes x F x 304), and, when the
- * rows are int64 keys with one int64 payload or none and F > 512, a copy of
+ * rows are int64 keys with one int64 payload or none and F > 64, a copy of
  * the keys and payload (16 bytes per row), because such fan-outs run as two
  * passes of at most 64 destinations each.  QE_ERR_OOM when the budget does
  * not hold it. */

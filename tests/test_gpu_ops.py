@@ -162,7 +162,7 @@ def test_partition_radix_generic_payloads(ctx, log2f, shift):
 def test_partition_many_chunks_per_block(ctx, log2f):
     """Several chunks per block, so the rows a block holds back for an
     incomplete output sector are carried across chunks; keys only and with
-    one payload.  Fan-outs above 512 take two passes."""
+    one payload.  Fan-outs above 64 take two passes."""
     n = 3_000_001
     k, p = datagen.key_payload_pairs(n, seed=77)
     _check_partition(ctx, k.numpy(), [p.numpy()], log2f)
